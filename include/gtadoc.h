@@ -1,0 +1,173 @@
+/*
+ * gtadoc.h - C ABI of libgtadoc.so: text analytics run directly on
+ * Sequitur grammar-compressed corpora (G-TADOC, arXiv 2106.06889) on one
+ * NVIDIA GB300 GPU (sm_103a).
+ *
+ * Input model (Section II-A and Fig. 1 of the paper): words are dictionary-
+ * converted to integer IDs; a context-free grammar of rules R0..Rn encodes
+ * every file; the root R0 holds the files one after another, separated by
+ * unique splitter symbols; every other rule stands for a repeated phrase.
+ * Here the splitters are removed from the root body and their positions are
+ * given as file offsets instead.
+ *
+ * Conventions shared by every call:
+ *   - A `stream` argument is a cudaStream_t passed as void*; NULL means the
+ *     legacy default stream.  Calls that take a stream only enqueue work on it
+ *     and return without waiting for the GPU, unless stated otherwise.
+ *   - Pointers named d_* are device pointers on the context's device;
+ *     everything else is a host pointer.
+ *   - Inputs stay owned by the caller.  The grammar is copied into library-
+ *     owned device memory at load time.  Results (gt_result) are library-owned
+ *     device buffers released with gt_free_result.
+ *   - Every output is canonical (sorted as each call states), so equal inputs
+ *     give byte-identical outputs whatever the grammar that encodes them.
+ *   - Counts are exact unsigned 64-bit integers.
+ *   - Errors: a call returns a gt_status; GT_OK is 0.  A human-readable
+ *     message for the last failure on a context is available from
+ *     gt_last_error.  Failures that only the GPU can detect (a full hash
+ *     table, a timed-out wait) are recorded in a device status word and
+ *     reported by gt_sync / gt_result_view.
+ *   - There is no CPU fallback: if no usable sm_103a device is present,
+ *     gt_create fails with GT_ECUDA.
+ */
+#ifndef GTADOC_H
+#define GTADOC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int gt_status;
+#define GT_OK 0
+#define GT_EINVAL 1       /* malformed argument or grammar                      */
+#define GT_ENOMEM 2       /* device or pool allocation failed                   */
+#define GT_ECUDA 3        /* a CUDA runtime call failed                         */
+#define GT_ETIMEOUT 4     /* a bounded device-side wait gave up                 */
+#define GT_ETABLE_FULL 5  /* a device hash table ran out of slots               */
+#define GT_EOVERFLOW 6    /* a size exceeds what the encoding supports          */
+#define GT_EBUSY 7        /* admission refused: not enough free memory / slots  */
+#define GT_ENOTFOUND 8    /* unknown result field or ticket                     */
+
+typedef struct gt_ctx gt_ctx;
+typedef struct gt_grammar gt_grammar;
+typedef struct gt_result gt_result;
+
+/* Grammar description (Section II-A).  num_rules counts the root.
+ *   rule_off [num_rules+1] int64: body of rule r is sym[rule_off[r] .. rule_off[r+1]).
+ *                          rule_off[0] must be 0; rule 0 is the root.
+ *   sym      [rule_off[num_rules]] int32: s < num_words is a word ID,
+ *                          s >= num_words references rule s - num_words (never 0).
+ *   file_off [num_files+1] int64: file f is root body positions
+ *                          file_off[f] .. file_off[f+1]; file_off[0] = 0 and
+ *                          file_off[num_files] = root body length.
+ *   on_device: 0 if the three arrays are host memory, 1 if device memory.
+ * Every non-root body must be non-empty and the rule graph must be acyclic. */
+typedef struct {
+  int32_t num_words;
+  int32_t num_rules;
+  int32_t num_files;
+  const int64_t* rule_off;
+  const int32_t* sym;
+  const int64_t* file_off;
+  int32_t on_device;
+} gt_grammar_desc;
+
+/* Facts about a loaded grammar, filled by gt_grammar_info. */
+typedef struct {
+  int64_t num_words, num_rules, num_files;
+  int64_t num_syms;        /* G: total body symbols                              */
+  int64_t num_edges;       /* E: distinct (parent, child) rule pairs             */
+  int64_t num_root_edges;  /* distinct (file, child) pairs in the root           */
+  int64_t depth;           /* number of DAG levels (root = level 0)              */
+  int64_t num_tokens;      /* N: length of the fully expanded corpus             */
+  int64_t owned_windows;   /* sum over rules of the owned 3-word windows (Eq. 1) */
+  int64_t device_bytes;    /* device memory held by the loaded grammar           */
+} gt_grammar_info;
+
+/* ---- context ---------------------------------------------------------- */
+
+/* Create a context on CUDA device `device`.  pool_bytes > 0 reserves that
+ * much device memory for the stream-ordered pool that backs per-query scratch
+ * and results (0 = grow on demand).  Fails with GT_ECUDA when the device is
+ * absent or is not compute capability 10.3. */
+gt_status gt_create(gt_ctx** ctx, int device, size_t pool_bytes);
+gt_status gt_destroy(gt_ctx* ctx);
+/* Message for the last failure on ctx (never NULL; "" when none). */
+const char* gt_last_error(const gt_ctx* ctx);
+/* Wait for `stream`, then return and clear the device status word. */
+gt_status gt_sync(gt_ctx* ctx, void* stream);
+
+/* ---- grammar ---------------------------------------------------------- */
+
+/* Load a grammar (the initialisation phase of Section IV-A): copy it to the
+ * device and build the rule DAG used by every traversal - deduplicated child
+ * lists with multiplicities (the subRules of Algorithm 1), the parent lists
+ * (genRuleParentsKernel, Algorithm 2), per-file root edges, the DAG levels
+ * that order top-down and bottom-up passes, per-rule word/rule counts and
+ * expansion lengths.  Synchronises `stream` before returning (it validates
+ * the grammar on the device).  GT_EINVAL for a malformed or cyclic grammar. */
+gt_status gt_load_grammar(gt_ctx* ctx, const gt_grammar_desc* desc, void* stream, gt_grammar** out);
+gt_status gt_free_grammar(gt_grammar* g);
+gt_status gt_grammar_info_get(const gt_grammar* g, gt_grammar_info* info);
+
+/* ---- analytics (Section VI: the six CompressDirect applications) ------- */
+
+/* Top-down rule weights (Algorithm 1): d_weights[r] = number of times rule r
+ * occurs in the full expansion of the corpus; d_weights[0] = 1.
+ * d_weights: device uint64[num_rules], written entirely. */
+gt_status gt_rule_weights(gt_grammar* g, uint64_t* d_weights, void* stream);
+
+/* Word count (Fig. 2): d_counts[w] = occurrences of word w in all files.
+ * d_counts: device uint64[num_words], written entirely. */
+gt_status gt_word_count(gt_grammar* g, uint64_t* d_counts, void* stream);
+
+/* Sort: the distinct words with their counts.  order 0: ascending word ID;
+ * order 1: descending count, ties by ascending word ID.
+ * Result fields: "word" int32[n], "count" uint64[n]. */
+gt_status gt_sort(gt_grammar* g, int order, void* stream, gt_result** out);
+
+/* Inverted index: for each word, the ascending list of files containing it.
+ * Result fields: "offsets" int64[num_words+1], "file" int32[offsets[V]]. */
+gt_status gt_inverted_index(gt_grammar* g, void* stream, gt_result** out);
+
+/* Term vector: for each file, its distinct words with their in-file counts.
+ * top_k == 0: all words, ascending word ID.  top_k > 0: the top_k largest
+ * counts of each file, by descending count then ascending word ID.
+ * Result fields: "offsets" int64[num_files+1], "word" int32[], "count" uint64[]. */
+gt_status gt_term_vector(gt_grammar* g, int top_k, void* stream, gt_result** out);
+
+/* Sequence count for l = 3 (Section IV-D): every window of three consecutive
+ * words inside one file (windows never cross a file boundary), keyed as
+ * key = w1 << 42 | w2 << 21 | w3 (requires num_words <= 2^21).
+ * per_file == 0: fields "key" uint64[n], "count" uint64[n], ascending key.
+ * per_file == 1: fields "file" int32[n], "key" uint64[n], "count" uint64[n],
+ *                ascending (file, key). */
+gt_status gt_sequence_count(gt_grammar* g, int per_file, void* stream, gt_result** out);
+
+/* Ranked inverted index.  n == 3: keys are 3-word windows as in
+ * gt_sequence_count; n == 1: keys are words.  For each key (ascending), the
+ * files containing it with the in-file count, by descending count then
+ * ascending file.  Fields: "offsets" int64[nkeys+1], "key" uint64[nkeys],
+ * "file" int32[m], "count" uint64[m]. */
+gt_status gt_ranked_index(gt_grammar* g, int n, void* stream, gt_result** out);
+
+/* Head and tail buffers (Section IV-C): for every rule, the first two and
+ * the last two words of its expansion (word IDs; -1 pads a rule whose
+ * expansion has a single word).  d_head, d_tail: device int32[2*num_rules]. */
+gt_status gt_head_tail(gt_grammar* g, int32_t* d_head, int32_t* d_tail, void* stream);
+
+/* ---- results ---------------------------------------------------------- */
+
+/* Device pointer and element count of one field of a result.  Waits for the
+ * work that produced the result; returns the device status if that work
+ * failed (e.g. GT_ETABLE_FULL) and GT_ENOTFOUND for an unknown field. */
+gt_status gt_result_view(gt_result* r, const char* field, const void** d_ptr, int64_t* len);
+gt_status gt_free_result(gt_result* r);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GTADOC_H */

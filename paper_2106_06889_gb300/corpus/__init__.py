@@ -1,0 +1,277 @@
+"""Seeded synthetic corpora and their TADOC compressed form.
+
+This module prepares inputs only.  It draws Zipf-distributed word-ID streams
+with injected repeated passages (stand-ins for the paper's datasets A-E of
+Section V-A, which are not available here) and compresses them with the
+Sequitur compressor in ``sequitur.cpp`` into the rule-grammar form of
+Section II-A: a root rule holding every file with unique splitters between
+files, plus one rule per repeated phrase.
+
+It contains none of the analytics: both the CUDA engine and the CPU oracle
+consume the :class:`Grammar` it returns.
+"""
+from __future__ import annotations
+
+import ctypes
+import hashlib
+import json
+import os
+from dataclasses import dataclass, field
+from pathlib import Path
+
+import numpy as np
+
+from .._build import build_corpus, CORPUS_SO, ROOT
+
+__all__ = ["Grammar", "sequitur", "zipf_tokens", "Corpus", "make_corpus", "CONFIGS", "load_config",
+           "root_only_grammar", "refactor_grammar"]
+
+
+@dataclass
+class Grammar:
+    """A compressed corpus.
+
+    ``sym`` holds every rule body back to back (``rule_off[r]:rule_off[r+1]``);
+    rule 0 is the root, whose body is all files concatenated without
+    splitters, file ``f`` being ``file_off[f]:file_off[f+1]`` of that body.
+    A symbol ``s < num_words`` is a word; ``s >= num_words`` refers to rule
+    ``s - num_words``.
+    """
+
+    num_words: int
+    rule_off: np.ndarray  # int64 [R+1]
+    sym: np.ndarray  # int32 [G]
+    file_off: np.ndarray  # int64 [F+1]
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def num_rules(self) -> int:
+        return int(self.rule_off.shape[0] - 1)
+
+    @property
+    def num_files(self) -> int:
+        return int(self.file_off.shape[0] - 1)
+
+    @property
+    def num_syms(self) -> int:
+        return int(self.sym.shape[0])
+
+    def body(self, r: int) -> np.ndarray:
+        return self.sym[self.rule_off[r]:self.rule_off[r + 1]]
+
+    def save(self, path: Path) -> None:
+        np.savez(path, num_words=np.int64(self.num_words), rule_off=self.rule_off, sym=self.sym,
+                 file_off=self.file_off, meta=np.array(json.dumps(self.meta)))
+
+    @staticmethod
+    def load(path: Path) -> "Grammar":
+        z = np.load(path)
+        return Grammar(int(z["num_words"]), z["rule_off"], z["sym"], z["file_off"], json.loads(str(z["meta"])))
+
+
+_lib = None
+
+
+def _corpus_lib():
+    global _lib
+    if _lib is None:
+        so = build_corpus()
+        lib = ctypes.CDLL(str(so))
+        lib.gtc_sequitur_build.restype = ctypes.c_void_p
+        lib.gtc_sequitur_build.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                           ctypes.c_void_p]
+        lib.gtc_grammar_sizes.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64),
+                                          ctypes.POINTER(ctypes.c_int64)]
+        lib.gtc_grammar_export.argtypes = [ctypes.c_void_p] * 4
+        lib.gtc_grammar_free.argtypes = [ctypes.c_void_p]
+        _lib = lib
+    return _lib
+
+
+def sequitur(tokens: np.ndarray, file_lens, num_words: int) -> Grammar:
+    """Compress ``tokens`` (the files back to back) into a Sequitur grammar."""
+    tokens = np.ascontiguousarray(tokens, dtype=np.int32)
+    file_lens = np.ascontiguousarray(file_lens, dtype=np.int64)
+    lib = _corpus_lib()
+    h = lib.gtc_sequitur_build(tokens.ctypes.data, tokens.shape[0], num_words, file_lens.shape[0],
+                               file_lens.ctypes.data)
+    if not h:
+        raise ValueError("Sequitur rejected the input (bad token, size mismatch or out of memory)")
+    try:
+        nr, ns = ctypes.c_int64(), ctypes.c_int64()
+        lib.gtc_grammar_sizes(h, ctypes.byref(nr), ctypes.byref(ns))
+        rule_off = np.empty(nr.value + 1, np.int64)
+        sym = np.empty(ns.value, np.int32)
+        file_off = np.empty(file_lens.shape[0] + 1, np.int64)
+        lib.gtc_grammar_export(h, rule_off.ctypes.data, sym.ctypes.data, file_off.ctypes.data)
+    finally:
+        lib.gtc_grammar_free(h)
+    return Grammar(int(num_words), rule_off, sym, file_off)
+
+
+def root_only_grammar(tokens: np.ndarray, file_lens, num_words: int) -> Grammar:
+    """The trivial encoding: no rules, the root is the raw text."""
+    tokens = np.ascontiguousarray(tokens, dtype=np.int32)
+    file_off = np.concatenate([[0], np.cumsum(np.asarray(file_lens, np.int64))]).astype(np.int64)
+    return Grammar(int(num_words), np.array([0, tokens.shape[0]], np.int64), tokens.copy(), file_off)
+
+
+def refactor_grammar(g: Grammar, rng: np.random.Generator, rounds: int = 3, frac: float = 0.2) -> Grammar:
+    """Re-encode ``g`` with extra random rules (same expansion, other DAG).
+
+    Each round picks random adjacent symbol pairs inside bodies (never across
+    a file boundary of the root) and moves each pair into a fresh rule used
+    once.  Rule utility is deliberately not kept: the result is a valid but
+    non-Sequitur grammar, which the analytics must handle identically.
+    """
+    bodies = [list(g.body(r)) for r in range(g.num_rules)]
+    V = g.num_words
+    root_files = [list(g.body(0)[g.file_off[f]:g.file_off[f + 1]]) for f in range(g.num_files)]
+    for _ in range(rounds):
+        new_rules = []
+
+        def fold(seq):
+            out, i = [], 0
+            while i < len(seq):
+                if i + 1 < len(seq) and rng.random() < frac:
+                    rid = len(bodies) + len(new_rules)
+                    new_rules.append([seq[i], seq[i + 1]])
+                    out.append(V + rid)
+                    i += 2
+                else:
+                    out.append(seq[i])
+                    i += 1
+            return out
+
+        root_files = [fold(s) for s in root_files]
+        for r in range(1, len(bodies)):
+            bodies[r] = fold(bodies[r])
+        bodies.extend(new_rules)
+    bodies[0] = [x for s in root_files for x in s]
+    lens = [len(b) for b in bodies]
+    rule_off = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    sym = np.array([x for b in bodies for x in b], np.int32)
+    file_off = np.concatenate([[0], np.cumsum([len(s) for s in root_files])]).astype(np.int64)
+    return Grammar(V, rule_off, sym, file_off)
+
+
+# ---------------------------------------------------------------------------
+# Synthetic Zipf corpora
+# ---------------------------------------------------------------------------
+
+def zipf_cdf(V: int, s: float) -> np.ndarray:
+    w = np.arange(1, V + 1, dtype=np.float64) ** (-s)
+    c = np.cumsum(w)
+    return c / c[-1]
+
+
+def zipf_tokens(rng: np.random.Generator, n: int, cdf: np.ndarray, perm: np.ndarray) -> np.ndarray:
+    """n word IDs: Zipf ranks by inverse CDF, mapped to IDs by ``perm``."""
+    u = rng.random(n)
+    rank = np.searchsorted(cdf, u, side="right")
+    np.minimum(rank, cdf.shape[0] - 1, out=rank)
+    return perm[rank].astype(np.int32)
+
+
+def inject(rng: np.random.Generator, base: np.ndarray, pieces) -> np.ndarray:
+    """Insert each piece into ``base`` at independent uniform positions."""
+    if not pieces:
+        return base
+    pos = np.sort(rng.integers(0, base.shape[0] + 1, size=len(pieces)))
+    order = rng.permutation(len(pieces))
+    out, last = [], 0
+    for p, k in zip(pos, order):
+        out.append(base[last:p])
+        out.append(pieces[k])
+        last = p
+    out.append(base[last:])
+    return np.concatenate(out).astype(np.int32)
+
+
+@dataclass
+class Corpus:
+    tokens: np.ndarray
+    file_lens: np.ndarray
+    num_words: int
+    meta: dict
+
+
+def make_corpus(name: str, seed: int | None = None, scale: float = 1.0) -> Corpus:
+    """Build one of the named synthetic corpora.
+
+    ``scale`` shrinks token counts (not vocabulary) for quick tests.
+    """
+    spec = CONFIGS[name]
+    seed = spec["seed"] if seed is None else seed
+    rng = np.random.default_rng(seed)
+    V, s = spec["V"], spec["s"]
+    cdf = zipf_cdf(V, s)
+    perm = rng.permutation(V).astype(np.int32)
+    kind = spec["kind"]
+    if kind == "single_passages":
+        N = max(int(spec["N"] * scale), 1000)
+        plen = spec["passage_len"]
+        npass = max(1, int(round(spec["passages"] * min(1.0, scale * 4))))
+        pool = [zipf_tokens(rng, plen, cdf, perm) for _ in range(npass)]
+        pieces = [p for p in pool for _ in range(spec["copies"])]
+        base = zipf_tokens(rng, N - sum(len(p) for p in pieces), cdf, perm)
+        toks = inject(rng, base, pieces)
+        lens = np.array([toks.shape[0]], np.int64)
+    elif kind == "files_passages":
+        F = spec["F"]
+        lo, hi = spec["len_range"]
+        raw = np.exp(rng.uniform(np.log(lo), np.log(hi), size=F))
+        lens_t = np.maximum(np.round(raw / raw.sum() * spec["N"] * scale), 0).astype(np.int64)
+        plen = spec["passage_len"]
+        pool = [zipf_tokens(rng, plen, cdf, perm) for _ in range(spec["passages"])]
+        files = []
+        for f in range(F):
+            target = int(lens_t[f])
+            want = int(round(target * spec["passage_frac"] / plen))
+            pieces = [pool[i] for i in rng.integers(0, len(pool), size=want)]
+            base = zipf_tokens(rng, max(target - want * plen, 0), cdf, perm)
+            files.append(inject(rng, base, pieces))
+        toks = np.concatenate(files).astype(np.int32)
+        lens = np.array([f.shape[0] for f in files], np.int64)
+    else:
+        raise ValueError(f"unknown corpus kind {kind}")
+    meta = {"name": name, "seed": int(seed), "scale": scale, "V": V, "s": s, "N": int(toks.shape[0]),
+            "F": int(lens.shape[0])}
+    return Corpus(toks, lens, V, meta)
+
+
+# Shapes follow the paper's workloads (Section V-A): one small file (like
+# dataset D), a few large files sharing one grammar (like dataset B).
+CONFIGS = {
+    "wc_single_200k": dict(kind="single_passages", seed=20210613, N=200_000, V=20_000, s=1.1,
+                           passages=50, passage_len=200, copies=4),
+    "multi64_50m": dict(kind="files_passages", seed=20210614, N=50_000_000, F=64, len_range=(10_000, 2_000_000),
+                        V=500_000, s=1.0, passages=500, passage_len=200, passage_frac=0.05),
+}
+
+
+def cache_dir() -> Path:
+    d = Path(os.environ.get("GT_CACHE_DIR", ROOT / ".gtcache"))
+    d.mkdir(parents=True, exist_ok=True)
+    return d
+
+
+def load_config(name: str, scale: float = 1.0, keep_tokens: bool = False):
+    """Corpus + Sequitur grammar for a named config, cached on disk.
+
+    Returns ``(grammar, corpus_or_None)``.
+    """
+    tag = hashlib.sha1(json.dumps([name, CONFIGS[name], scale, "v1"], sort_keys=True).encode()).hexdigest()[:12]
+    path = cache_dir() / f"{name}_{tag}.npz"
+    if path.exists() and not keep_tokens:
+        return Grammar.load(path), None
+    corpus = make_corpus(name, scale=scale)
+    if path.exists():
+        g = Grammar.load(path)
+    else:
+        g = sequitur(corpus.tokens, corpus.file_lens, corpus.num_words)
+        g.meta = dict(corpus.meta)
+        tmp = path.with_suffix(f".tmp{os.getpid()}.npz")
+        g.save(tmp)
+        os.replace(tmp, path)
+    return g, (corpus if keep_tokens else None)
