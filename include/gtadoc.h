@@ -129,31 +129,6 @@ gt_status gt_word_count(gt_grammar* g, uint64_t* d_counts, void* stream);
  * Result fields: "word" int32[n], "count" uint64[n]. */
 gt_status gt_sort(gt_grammar* g, int order, void* stream, gt_result** out);
 
-/* Inverted index: for each word, the ascending list of files containing it.
- * Result fields: "offsets" int64[num_words+1], "file" int32[offsets[V]]. */
-gt_status gt_inverted_index(gt_grammar* g, void* stream, gt_result** out);
-
-/* Term vector: for each file, its distinct words with their in-file counts.
- * top_k == 0: all words, ascending word ID.  top_k > 0: the top_k largest
- * counts of each file, by descending count then ascending word ID.
- * Result fields: "offsets" int64[num_files+1], "word" int32[], "count" uint64[]. */
-gt_status gt_term_vector(gt_grammar* g, int top_k, void* stream, gt_result** out);
-
-/* Sequence count for l = 3 (Section IV-D): every window of three consecutive
- * words inside one file (windows never cross a file boundary), keyed as
- * key = w1 << 42 | w2 << 21 | w3 (requires num_words <= 2^21).
- * per_file == 0: fields "key" uint64[n], "count" uint64[n], ascending key.
- * per_file == 1: fields "file" int32[n], "key" uint64[n], "count" uint64[n],
- *                ascending (file, key). */
-gt_status gt_sequence_count(gt_grammar* g, int per_file, void* stream, gt_result** out);
-
-/* Ranked inverted index.  n == 3: keys are 3-word windows as in
- * gt_sequence_count; n == 1: keys are words.  For each key (ascending), the
- * files containing it with the in-file count, by descending count then
- * ascending file.  Fields: "offsets" int64[nkeys+1], "key" uint64[nkeys],
- * "file" int32[m], "count" uint64[m]. */
-gt_status gt_ranked_index(gt_grammar* g, int n, void* stream, gt_result** out);
-
 /* Head and tail buffers (Section IV-C): for every rule, the first two and
  * the last two words of its expansion (word IDs; -1 pads a rule whose
  * expansion has a single word).  d_head, d_tail: device int32[2*num_rules]. */
@@ -166,6 +141,26 @@ gt_status gt_head_tail(gt_grammar* g, int32_t* d_head, int32_t* d_tail, void* st
  * failed (e.g. GT_ETABLE_FULL) and GT_ENOTFOUND for an unknown field. */
 gt_status gt_result_view(gt_result* r, const char* field, const void** d_ptr, int64_t* len);
 gt_status gt_free_result(gt_result* r);
+
+/* ---- profiling (not in the paper; the paper reports phase times only) ----
+ * When enabled, the library records CUDA events on the caller's stream around
+ * each phase it runs ("weights", "wc_partition", "wc_hist", "sort_canon", ...).
+ * gt_profile_read waits for those events and returns, for one phase, the
+ * summed device time in ms, the number of timed spans, and the number of
+ * kernels launched inside them.  gt_kernel_launches returns how many kernels
+ * this process has launched through the library so far. */
+gt_status gt_profile_enable(gt_ctx* ctx, int on);
+gt_status gt_profile_reset(gt_ctx* ctx);
+gt_status gt_profile_read(gt_ctx* ctx, const char* phase, double* total_ms, int64_t* spans, int64_t* launches);
+int64_t gt_kernel_launches(void);
+
+/* Tunable parameters (Section IV-A, parameter selection: results never depend
+ * on them, only speed does).  Known names:
+ *   "wc_aggregate"  1: merge equal words inside a warp (__match_any_sync)
+ *                   before the shared-memory histogram update; 0 (default):
+ *                   update per lane.
+ * GT_ENOTFOUND for an unknown name. */
+gt_status gt_set_param(gt_ctx* ctx, const char* name, int64_t value);
 
 #ifdef __cplusplus
 }

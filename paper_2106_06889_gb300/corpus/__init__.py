@@ -24,7 +24,7 @@ import numpy as np
 from .._build import build_corpus, CORPUS_SO, ROOT
 
 __all__ = ["Grammar", "sequitur", "zipf_tokens", "Corpus", "make_corpus", "CONFIGS", "load_config",
-           "root_only_grammar", "refactor_grammar"]
+           "root_only_grammar", "refactor_grammar", "prefix_files"]
 
 
 @dataclass
@@ -275,3 +275,14 @@ def load_config(name: str, scale: float = 1.0, keep_tokens: bool = False):
         g.save(tmp)
         os.replace(tmp, path)
     return g, (corpus if keep_tokens else None)
+
+
+def prefix_files(g: Grammar, k: int) -> Grammar:
+    """The same grammar restricted to its first ``k`` files (rules unchanged)."""
+    k = max(1, min(k, g.num_files))
+    root_end = int(g.file_off[k])
+    root_len = int(g.rule_off[1])
+    sym = np.concatenate([g.sym[:root_end], g.sym[root_len:]]).astype(np.int32)
+    rule_off = g.rule_off.copy()
+    rule_off[1:] -= root_len - root_end
+    return Grammar(g.num_words, rule_off, sym, g.file_off[:k + 1].copy(), dict(g.meta))

@@ -1,0 +1,242 @@
+// Device primitives: exclusive prefix sum and a stable LSD radix sort.
+//
+// These back the memory-pool sizing (exclusive scans of per-rule sizes, the
+// "memory pool" of Section IV-B), the edge deduplication at load time and the
+// canonical ordering of every result.
+#include "gt_internal.cuh"
+
+namespace gt {
+namespace {
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+constexpr int kScanChunk = kScanThreads * kScanItems;
+
+__device__ __forceinline__ int64_t warp_incl_scan(int64_t v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int64_t t = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += t;
+  }
+  return v;
+}
+
+// Exclusive scan of one value per thread across the block; returns the block
+// total through *total.
+__device__ __forceinline__ int64_t block_excl_scan(int64_t v, int64_t* total) {
+  __shared__ int64_t warp_sums[kScanThreads / 32 + 1];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int64_t incl = warp_incl_scan(v);
+  if (lane == 31) warp_sums[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    int64_t w = lane < kScanThreads / 32 ? warp_sums[lane] : 0;
+    int64_t wi = warp_incl_scan(w);
+    if (lane < kScanThreads / 32) warp_sums[lane] = wi - w;
+    if (lane == kScanThreads / 32 - 1) warp_sums[kScanThreads / 32] = wi;  // slot after the last warp
+  }
+  __syncthreads();
+  int64_t r = warp_sums[warp] + incl - v;
+  if (total) *total = warp_sums[kScanThreads / 32];
+  __syncthreads();
+  return r;
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const int64_t* __restrict__ in, int64_t n,
+                                                                   int64_t* __restrict__ bsum) {
+  const int64_t base = int64_t(blockIdx.x) * kScanChunk;
+  int64_t s = 0;
+  for (int i = threadIdx.x; i < kScanChunk; i += kScanThreads) {
+    int64_t idx = base + i;
+    if (idx < n) s += in[idx];
+  }
+  int64_t total;
+  block_excl_scan(s, &total);
+  if (threadIdx.x == 0) bsum[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_apply_kernel(const int64_t* in, int64_t* out, int64_t n,
+                                                                  const int64_t* __restrict__ boff) {
+  __shared__ int64_t tile[kScanChunk];
+  const int64_t base = int64_t(blockIdx.x) * kScanChunk;
+  for (int i = threadIdx.x; i < kScanChunk; i += kScanThreads) {
+    int64_t idx = base + i;
+    tile[i] = idx < n ? in[idx] : 0;
+  }
+  __syncthreads();
+  int64_t local[kScanItems];
+  int64_t s = 0;
+#pragma unroll
+  for (int j = 0; j < kScanItems; ++j) {
+    local[j] = tile[threadIdx.x * kScanItems + j];
+    s += local[j];
+  }
+  int64_t off = block_excl_scan(s, nullptr) + (boff ? boff[blockIdx.x] : 0);
+#pragma unroll
+  for (int j = 0; j < kScanItems; ++j) {
+    tile[threadIdx.x * kScanItems + j] = off;
+    off += local[j];
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kScanChunk; i += kScanThreads) {
+    int64_t idx = base + i;
+    if (idx < n) out[idx] = tile[i];
+  }
+}
+
+// ---- radix sort -------------------------------------------------------------
+
+constexpr int kRsThreads = 256;
+constexpr int kRsWarps = kRsThreads / 32;
+constexpr int kRsItems = 16;
+constexpr int kRsTile = kRsThreads * kRsItems;  // keys per tile
+
+__global__ void __launch_bounds__(kRsThreads) radix_upsweep_kernel(const uint64_t* __restrict__ keys, int64_t n,
+                                                                   int shift, uint32_t mask, int64_t ntiles,
+                                                                   int64_t* __restrict__ hist) {
+  __shared__ uint32_t h[256];
+  for (int i = threadIdx.x; i < 256; i += kRsThreads) h[i] = 0;
+  __syncthreads();
+  const int64_t base = int64_t(blockIdx.x) * kRsTile;
+  for (int i = threadIdx.x; i < kRsTile; i += kRsThreads) {
+    int64_t idx = base + i;
+    if (idx < n) atomicAdd(&h[(keys[idx] >> shift) & mask], 1u);
+  }
+  __syncthreads();
+  for (int d = threadIdx.x; d < 256; d += kRsThreads) hist[int64_t(d) * ntiles + blockIdx.x] = h[d];
+}
+
+// Stable scatter: within a tile, keys keep their order because warp w owns the
+// w-th slice of the tile, walks it in order 32 keys at a time, and ranks equal
+// digits within each group of 32 by lane order (__match_any_sync).
+template <int VB>
+__global__ void __launch_bounds__(kRsThreads) radix_downsweep_kernel(
+    const uint64_t* __restrict__ kin, uint64_t* __restrict__ kout, const void* __restrict__ vin,
+    void* __restrict__ vout, int64_t n, int shift, uint32_t mask, int64_t ntiles, const int64_t* __restrict__ offs) {
+  __shared__ uint32_t wcnt[kRsWarps][256];
+  __shared__ int64_t goff[256];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i = threadIdx.x; i < kRsWarps * 256; i += kRsThreads) wcnt[i / 256][i % 256] = 0;
+  for (int d = threadIdx.x; d < 256; d += kRsThreads) goff[d] = offs[int64_t(d) * ntiles + blockIdx.x];
+  __syncthreads();
+  const unsigned lt_mask = (1u << lane) - 1u;
+  const int64_t wbase = int64_t(blockIdx.x) * kRsTile + int64_t(warp) * 32 * kRsItems;
+  uint64_t key[kRsItems];
+  uint32_t rank[kRsItems];
+  uint64_t val[kRsItems];
+#pragma unroll
+  for (int it = 0; it < kRsItems; ++it) {
+    const int64_t idx = wbase + it * 32 + lane;
+    const bool valid = idx < n;
+    key[it] = valid ? kin[idx] : 0;
+    if (VB == 4) val[it] = valid ? static_cast<const uint32_t*>(vin)[idx] : 0;
+    if (VB == 8) val[it] = valid ? static_cast<const uint64_t*>(vin)[idx] : 0;
+    const unsigned active = __ballot_sync(0xffffffffu, valid);
+    rank[it] = 0;
+    if (valid) {
+      const uint32_t d = uint32_t(key[it] >> shift) & mask;
+      const unsigned peers = __match_any_sync(active, d);
+      const uint32_t before = wcnt[warp][d];
+      const uint32_t r = __popc(peers & lt_mask);
+      rank[it] = before + r;
+      __syncwarp(active);
+      if (r == 0) wcnt[warp][d] = before + __popc(peers);
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+  // exclusive prefix over warps, per digit
+  for (int d = threadIdx.x; d < 256; d += kRsThreads) {
+    uint32_t run = 0;
+#pragma unroll
+    for (int w = 0; w < kRsWarps; ++w) {
+      uint32_t c = wcnt[w][d];
+      wcnt[w][d] = run;
+      run += c;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int it = 0; it < kRsItems; ++it) {
+    const int64_t idx = wbase + it * 32 + lane;
+    if (idx < n) {
+      const uint32_t d = uint32_t(key[it] >> shift) & mask;
+      const int64_t pos = goff[d] + wcnt[warp][d] + rank[it];
+      kout[pos] = key[it];
+      if (VB == 4) static_cast<uint32_t*>(vout)[pos] = uint32_t(val[it]);
+      if (VB == 8) static_cast<uint64_t*>(vout)[pos] = val[it];
+    }
+  }
+}
+
+}  // namespace
+
+size_t scan_scratch_bytes(int64_t n) {
+  int64_t nb = (n + kScanChunk - 1) / kScanChunk;
+  if (nb <= 1) return 0;
+  return size_t(2 * nb) * sizeof(int64_t) + scan_scratch_bytes(nb);
+}
+
+void exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, void* scratch, cudaStream_t s) {
+  if (n <= 0) return;
+  int64_t nb = (n + kScanChunk - 1) / kScanChunk;
+  if (nb == 1) {
+    scan_apply_kernel<<<1, kScanThreads, 0, s>>>(in, out, n, nullptr);
+    GT_LAUNCH_CHECK();
+    return;
+  }
+  int64_t* bsum = static_cast<int64_t*>(scratch);
+  int64_t* boff = bsum + nb;
+  scan_reduce_kernel<<<unsigned(nb), kScanThreads, 0, s>>>(in, n, bsum);
+  GT_LAUNCH_CHECK();
+  exclusive_scan_i64(bsum, boff, nb, boff + nb, s);
+  scan_apply_kernel<<<unsigned(nb), kScanThreads, 0, s>>>(in, out, n, boff);
+  GT_LAUNCH_CHECK();
+}
+
+size_t radix_scratch_bytes(int64_t n, bool, int) {
+  int64_t ntiles = (n + kRsTile - 1) / kRsTile;
+  int64_t m = 256 * ntiles;
+  return size_t(2 * m) * sizeof(int64_t) + scan_scratch_bytes(m) + 256;
+}
+
+void radix_sort_u64(uint64_t* keys_in, uint64_t* keys_out, void* vals_in, void* vals_out, int value_bytes,
+                    int64_t n, int begin_bit, int end_bit, void* scratch, cudaStream_t s) {
+  if (n <= 0) return;
+  const int64_t ntiles = (n + kRsTile - 1) / kRsTile;
+  const int64_t m = 256 * ntiles;
+  int64_t* hist = static_cast<int64_t*>(scratch);
+  int64_t* offs = hist + m;
+  void* sscratch = offs + m;
+  uint64_t* ka = keys_in;
+  uint64_t* kb = keys_out;
+  void* va = vals_in;
+  void* vb = vals_out;
+  int passes = 0;
+  for (int shift = begin_bit; shift < end_bit; shift += 8, ++passes) {
+    const int bits = end_bit - shift < 8 ? end_bit - shift : 8;
+    const uint32_t mask = (1u << bits) - 1u;
+    radix_upsweep_kernel<<<unsigned(ntiles), kRsThreads, 0, s>>>(ka, n, shift, mask, ntiles, hist);
+    GT_LAUNCH_CHECK();
+    exclusive_scan_i64(hist, offs, m, sscratch, s);
+    if (value_bytes == 4)
+      radix_downsweep_kernel<4><<<unsigned(ntiles), kRsThreads, 0, s>>>(ka, kb, va, vb, n, shift, mask, ntiles, offs);
+    else if (value_bytes == 8)
+      radix_downsweep_kernel<8><<<unsigned(ntiles), kRsThreads, 0, s>>>(ka, kb, va, vb, n, shift, mask, ntiles, offs);
+    else
+      radix_downsweep_kernel<0><<<unsigned(ntiles), kRsThreads, 0, s>>>(ka, kb, nullptr, nullptr, n, shift, mask,
+                                                                        ntiles, offs);
+    GT_LAUNCH_CHECK();
+    std::swap(ka, kb);
+    std::swap(va, vb);
+  }
+  // after the loop the sorted data is in ka / va
+  if (ka != keys_out) {
+    GT_CUDA(cudaMemcpyAsync(keys_out, ka, size_t(n) * 8, cudaMemcpyDeviceToDevice, s));
+    if (value_bytes)
+      GT_CUDA(cudaMemcpyAsync(vals_out, va, size_t(n) * value_bytes, cudaMemcpyDeviceToDevice, s));
+  }
+}
+
+}  // namespace gt
