@@ -25,7 +25,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOADS = {
-    "multi64_50m": {"analytics": ["word_count"],
+    "multi64_50m": {"analytics": ["word_count", "inverted_index", "term_vector"],
                     "desc": "64 files, log-uniform 10k-2M tokens (~50M), Zipf s=1.0, V=500k, 5% repeated "
                             "passages, one Sequitur grammar"},
 }
@@ -104,10 +104,14 @@ def algorithmic_bytes(info: dict) -> dict:
     return {"wc_partition": 4 * G, "weights": 8 * E + 16 * R, "total": 4 * G + 8 * E + 8 * R + 8 * V}
 
 
-def run_step(B, gh, bufs, analytics, stream):
-    for a in analytics:
-        if a == "word_count":
-            B.gt_word_count(gh, bufs["counts"], stream)
+def run_step(B, gh, bufs, analytics, stream, keep):
+    """One pass of the workload's analytics as one batch (one traversal per
+    grammar); result handles go to ``keep`` and are released after the timed
+    region (freeing waits for the GPU)."""
+    kinds = {"word_count": B.GT_Q_WORD_COUNT, "inverted_index": B.GT_Q_INVERTED_INDEX,
+             "term_vector": B.GT_Q_TERM_VECTOR, "sort": B.GT_Q_SORT}
+    qs = [(gh, kinds[a], 0, bufs["counts"] if a == "word_count" else None) for a in analytics]
+    keep.extend(r for r in B.gt_run_batch(gh.ctx, qs, stream) if r is not None)
 
 
 def oracle_sample(g, budget_s: float = 20.0):
@@ -195,10 +199,14 @@ def main():
             dist.barrier()
 
     # ---- device-timed steps (inputs resident; the 148 MB symbol array exceeds L2) ----
+    keep = []
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
-            run_step(B, gh, bufs, wl["analytics"], stream)
+            run_step(B, gh, bufs, wl["analytics"], stream, keep)
         torch.cuda.synchronize()
+        for r in keep:
+            B.gt_free_result(r)
+        keep.clear()
         B.gt_profile_reset(ctx)
         B.gt_profile_enable(ctx, True)
         launches0 = B.gt_kernel_launches()
@@ -208,11 +216,14 @@ def main():
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
         for _ in range(args.steps):
-            run_step(B, gh, bufs, wl["analytics"], stream)
+            run_step(B, gh, bufs, wl["analytics"], stream, keep)
         ev1.record(stream)
         torch.cuda.synchronize()
         barrier()
         clk = clocks.stop()
+        for r in keep:
+            B.gt_free_result(r)
+        keep.clear()
         launches = B.gt_kernel_launches() - launches0
         B.gt_profile_enable(ctx, False)
     ms = ev0.elapsed_time(ev1)
@@ -225,7 +236,7 @@ def main():
 
     # ---- dominant kernel: live CUDA-event time of its phase ----
     phases = {}
-    for ph in ("weights", "wc_partition", "wc_hist", "sort_canon"):
+    for ph in ("weights", "wc_partition", "wc_hist", "sort_canon", "file_weights", "tv_hist", "tv_out", "ii_out"):
         tot, spans, la = B.gt_profile_read(ctx, ph)
         if spans:
             phases[ph] = {"ms_per_launch": tot / spans, "spans": spans, "launches": la}
@@ -251,6 +262,7 @@ def main():
 
     out_host = torch.empty(g.num_words, dtype=torch.int64).pin_memory()
     e2e_steps = 0 if args.no_e2e else max(2, min(args.steps, 5))
+    d2h_res = [0]
     h2d = sum(int(v.numel() * v.element_size()) for v in pinned.values())
     d2h = int(out_host.numel() * out_host.element_size())
     with torch.cuda.stream(stream):
@@ -258,12 +270,24 @@ def main():
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
             gh2 = B.gt_load_grammar(ctx, HostG, stream)
-            run_step(B, gh2, bufs, wl["analytics"], stream)
+            run_step(B, gh2, bufs, wl["analytics"], stream, keep)
             out_host.copy_(bufs["counts"], non_blocking=True)
+            for r in keep:  # copy every result field back to host memory
+                for fld in ("offsets", "word", "count", "file"):
+                    try:
+                        t = B.result_tensor(r, fld)
+                    except B.GtError:
+                        continue
+                    d2h_res[0] += t.numel() * t.element_size()
+                    t.to("cpu", non_blocking=True)
             stream.synchronize()
+            for r in keep:
+                B.gt_free_result(r)
+            keep.clear()
             B.gt_free_grammar(gh2)
         e2e_s = (time.perf_counter() - t0) / max(e2e_steps, 1)
     if e2e_steps:
+        d2h += d2h_res[0] // e2e_steps
         e2e = {"value": world * N / e2e_s, "unit": "tokens/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h,
                "note": "gt_load_grammar from pinned host arrays + analytics + result copy back, per step"}

@@ -129,10 +129,46 @@ gt_status gt_word_count(gt_grammar* g, uint64_t* d_counts, void* stream);
  * Result fields: "word" int32[n], "count" uint64[n]. */
 gt_status gt_sort(gt_grammar* g, int order, void* stream, gt_result** out);
 
+/* Inverted index: for each word, the ascending list of files containing it.
+ * Result fields: "offsets" int64[num_words+1], "file" int32[offsets[V]].
+ * Top-down strategy (Section IV-A), currently for at most 64 files;
+ * GT_EOVERFLOW beyond that. */
+gt_status gt_inverted_index(gt_grammar* g, void* stream, gt_result** out);
+
+/* Term vector: for each file, its distinct words with their in-file counts.
+ * top_k == 0: all words, ascending word ID.  top_k > 0: the top_k largest
+ * counts of each file, by descending count then ascending word ID.
+ * Result fields: "offsets" int64[num_files+1], "word" int32[], "count" uint64[].
+ * Same strategy and file limit as gt_inverted_index. */
+gt_status gt_term_vector(gt_grammar* g, int top_k, void* stream, gt_result** out);
+
 /* Head and tail buffers (Section IV-C): for every rule, the first two and
  * the last two words of its expansion (word IDs; -1 pads a rule whose
  * expansion has a single word).  d_head, d_tail: device int32[2*num_rules]. */
 gt_status gt_head_tail(gt_grammar* g, int32_t* d_head, int32_t* d_tail, void* stream);
+
+/* ---- batches ------------------------------------------------------------
+ * Several analytics over one or more grammars in one call.  Queries on the
+ * same grammar share one traversal: word count and sort share the rule
+ * weights and the counts; term vectors and the inverted index share the
+ * per-file weights and (file, word) histograms.  out[i] receives query i's
+ * result (NULL for a word count, which writes into its d_counts).  On failure
+ * no result is returned.  (Not in the paper: it serves one query at a time.) */
+typedef enum {
+  GT_Q_WORD_COUNT = 0,     /* d_counts: device uint64[num_words]                */
+  GT_Q_SORT = 1,           /* param: order (0 or 1)                             */
+  GT_Q_INVERTED_INDEX = 2,
+  GT_Q_TERM_VECTOR = 3     /* param: top_k (0 = all)                            */
+} gt_query_kind;
+
+typedef struct {
+  gt_grammar* grammar;
+  int32_t kind;       /* gt_query_kind */
+  int32_t param;
+  uint64_t* d_counts; /* word count only */
+} gt_query;
+
+gt_status gt_run_batch(gt_ctx* ctx, const gt_query* q, int nq, void* stream, gt_result** out);
 
 /* ---- results ---------------------------------------------------------- */
 

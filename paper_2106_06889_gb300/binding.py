@@ -32,6 +32,14 @@ class gt_grammar_desc(ctypes.Structure):
                 ("on_device", ctypes.c_int32)]
 
 
+class gt_query(ctypes.Structure):
+    _fields_ = [("grammar", ctypes.c_void_p), ("kind", ctypes.c_int32), ("param", ctypes.c_int32),
+                ("d_counts", ctypes.c_void_p)]
+
+
+GT_Q_WORD_COUNT, GT_Q_SORT, GT_Q_INVERTED_INDEX, GT_Q_TERM_VECTOR = 0, 1, 2, 3
+
+
 class gt_grammar_info(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in ("num_words", "num_rules", "num_files", "num_syms", "num_edges",
                                               "num_root_edges", "depth", "num_tokens", "owned_windows",
@@ -68,6 +76,7 @@ def lib() -> ctypes.CDLL:
             "gt_free_result": [_P],
             "gt_profile_enable": [_P, ctypes.c_int],
             "gt_set_param": [_P, ctypes.c_char_p, ctypes.c_int64],
+            "gt_run_batch": [_P, _P, ctypes.c_int, _P, _P],
             "gt_profile_reset": [_P],
             "gt_profile_read": [_P, ctypes.c_char_p, ctypes.POINTER(ctypes.c_double),
                                 ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)],
@@ -289,3 +298,19 @@ def gt_kernel_launches() -> int:
 
 def gt_set_param(ctx: Context, name: str, value: int) -> None:
     _check(lib().gt_set_param(ctx.handle, name.encode(), int(value)), ctx.handle)
+
+
+def gt_run_batch(ctx: Context, queries, stream=None):
+    """queries: list of (GrammarHandle, kind, param, counts_tensor_or_None).
+    Returns a list with a ResultHandle (or None for word counts) per query."""
+    n = len(queries)
+    arr = (gt_query * max(n, 1))()
+    for i, (gh, kind, param, counts) in enumerate(queries):
+        arr[i].grammar = gh.handle.value if isinstance(gh.handle, ctypes.c_void_p) else gh.handle
+        arr[i].kind = int(kind)
+        arr[i].param = int(param)
+        arr[i].d_counts = _dptr(counts).value if counts is not None else None
+    outs = (ctypes.c_void_p * max(n, 1))()
+    _check(lib().gt_run_batch(ctx.handle, ctypes.cast(arr, ctypes.c_void_p), n, _stream(stream),
+                              ctypes.cast(outs, ctypes.c_void_p)), ctx.handle)
+    return [ResultHandle(ctypes.c_void_p(outs[i]), ctx) if outs[i] else None for i in range(n)]

@@ -54,58 +54,6 @@ const char* status_text(uint32_t st) {
   return "";
 }
 
-// ---- result construction ----------------------------------------------------
-
-// A result under construction: buffers are allocated from the pool on the
-// query's stream; data-dependent lengths are written by kernels into a small
-// device array and copied to pinned host memory when the query ends.
-struct ResultBuilder {
-  gt_result* r;
-  cudaStream_t s;
-  int64_t* d_lens = nullptr;  // device slots for data-dependent lengths; slot 0 holds the status word
-  int nslots = 0;
-  static constexpr int kMaxSlots = 8;
-
-  ResultBuilder(gt_ctx* ctx, cudaStream_t st) : s(st) {
-    r = new gt_result();
-    r->ctx = ctx;
-    GT_CUDA(cudaMallocHost(&r->h_lens, kMaxSlots * sizeof(int64_t)));
-    void* p = nullptr;
-    GT_CUDA(cudaMallocFromPoolAsync(&p, kMaxSlots * sizeof(int64_t), ctx->pool, s));
-    r->owned.push_back(p);
-    d_lens = static_cast<int64_t*>(p);
-    GT_CUDA(cudaMemsetAsync(d_lens, 0, kMaxSlots * sizeof(int64_t), s));
-    nslots = 1;
-  }
-  uint32_t* status() { return reinterpret_cast<uint32_t*>(d_lens); }
-  int64_t* new_len_slot() {
-    if (nslots >= kMaxSlots) fail(GT_EINVAL, "too many result fields");
-    return d_lens + nslots++;
-  }
-  void* alloc(size_t bytes) {
-    void* p = nullptr;
-    GT_CUDA(cudaMallocFromPoolAsync(&p, bytes ? bytes : 16, r->ctx->pool, s));
-    r->owned.push_back(p);
-    return p;
-  }
-  void field(const char* name, void* ptr, int64_t len) { r->fields.push_back({name, ptr, len, nullptr}); }
-  void field_dyn(const char* name, void* ptr, int64_t* d_len_slot) {
-    const int64_t idx = d_len_slot - d_lens;
-    r->fields.push_back({name, ptr, -1, r->h_lens + idx});
-  }
-  gt_result* finish() {
-    GT_CUDA(cudaMemcpyAsync(r->h_lens, d_lens, kMaxSlots * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    GT_CUDA(cudaEventCreateWithFlags(&r->done, cudaEventDisableTiming));
-    GT_CUDA(cudaEventRecord(r->done, s));
-    gt_result* out = r;
-    r = nullptr;
-    return out;
-  }
-  ~ResultBuilder() {
-    if (r) gt_free_result(r);
-  }
-};
-
 __global__ void nonzero_flags_kernel(const uint64_t* __restrict__ c, int64_t n, int64_t* __restrict__ flag) {
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
     flag[i] = c[i] != 0;
@@ -196,6 +144,9 @@ GT_API gt_status gt_create(gt_ctx** out, int device, size_t pool_bytes) {
 GT_API gt_status gt_destroy(gt_ctx* ctx) {
   if (!ctx) return GT_EINVAL;
   cudaSetDevice(ctx->device);
+  for (cudaEvent_t e : ctx->free_events) cudaEventDestroy(e);
+  for (void* p : ctx->pinned_chunks) cudaFreeHost(p);
+  gt_profile_reset(ctx);
   if (ctx->d_status) cudaFree(ctx->d_status);
   if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
   delete ctx;
@@ -276,6 +227,36 @@ GT_API gt_status gt_load_grammar(gt_ctx* ctx, const gt_grammar_desc* desc, void*
     GT_CUDA(cudaMemcpyAsync(p, foff.data(), foff.size() * 8, cudaMemcpyHostToDevice, s));
     d.file_off = static_cast<int64_t*>(p);
     g->info.device_bytes = Gp * 4 + int64_t(roff.size() + foff.size()) * 8;
+    {
+      // file-pure chunks of the root (per-file analytics)
+      std::vector<int64_t> cs, cf(size_t(F) + 1);
+      std::vector<int32_t> cl;
+      for (int32_t f = 0; f < F; ++f) {
+        cf[f] = int64_t(cs.size());
+        for (int64_t q = foff[f]; q < foff[f + 1]; q += gt::kFileChunk) {
+          cs.push_back(q);
+          cl.push_back(int32_t(std::min<int64_t>(gt::kFileChunk, foff[f + 1] - q)));
+        }
+      }
+      cf[F] = int64_t(cs.size());
+      const int64_t nc = int64_t(cs.size());
+      g->root_chunks = nc;
+      void* q;
+      GT_CUDA(cudaMalloc(&q, size_t(nc + 1) * 8));
+      g->owned.push_back(q);
+      if (nc) GT_CUDA(cudaMemcpy(q, cs.data(), size_t(nc) * 8, cudaMemcpyHostToDevice));
+      d.rch_start = static_cast<int64_t*>(q);
+      GT_CUDA(cudaMalloc(&q, size_t(nc + 1) * 4));
+      g->owned.push_back(q);
+      if (nc) GT_CUDA(cudaMemcpy(q, cl.data(), size_t(nc) * 4, cudaMemcpyHostToDevice));
+      d.rch_len = static_cast<int32_t*>(q);
+      GT_CUDA(cudaMalloc(&q, size_t(F + 2) * 8));
+      g->owned.push_back(q);
+      GT_CUDA(cudaMemcpy(q, cf.data(), size_t(F + 1) * 8, cudaMemcpyHostToDevice));
+      GT_CUDA(cudaMemcpy(static_cast<int64_t*>(q) + F + 1, &nc, 8, cudaMemcpyHostToDevice));
+      d.rch_foff = static_cast<int64_t*>(q);
+      d.rch_count = static_cast<int64_t*>(q) + F + 1;
+    }
     gt::load_build_dag(g, s);
     g->info.num_words = V;
     g->info.num_rules = R;
@@ -336,51 +317,158 @@ GT_API gt_status gt_head_tail(gt_grammar* g, int32_t* d_head, int32_t* d_tail, v
   });
 }
 
+namespace {
+
+// Sort result from already computed word counts.
+gt_result* sort_from_counts(gt_grammar* g, const uint64_t* wc, int order, cudaStream_t s) {
+  gt_ctx* ctx = g->ctx;
+  const int64_t V = g->d.V;
+  const int threads = 256, cap = ctx->num_sms * 8;
+  gt::ResultBuilder rb(ctx, s);
+  auto* words = static_cast<int32_t*>(rb.alloc(size_t(V) * 4));
+  auto* counts = static_cast<uint64_t*>(rb.alloc(size_t(V) * 8));
+  int64_t* nlen = rb.new_len_slot();
+  gt::Phase ph(ctx, "sort_canon", s);
+  if (order == 0) {
+    Buf flag(ctx, size_t(V) * 8, s), pos(ctx, size_t(V) * 8, s), sc(ctx, gt::scan_scratch_bytes(V), s);
+    nonzero_flags_kernel<<<gt::grid_for(V, threads, cap), threads, 0, s>>>(wc, V, flag.as<int64_t>());
+    GT_LAUNCH_CHECK();
+    gt::exclusive_scan_i64(flag.as<int64_t>(), pos.as<int64_t>(), V, sc.p, s);
+    compact_words_kernel<<<gt::grid_for(V, threads, cap), threads, 0, s>>>(wc, V, pos.as<int64_t>(), words, counts,
+                                                                            nlen);
+    GT_LAUNCH_CHECK();
+  } else {
+    const uint64_t N = g->d.N;
+    Buf k0(ctx, size_t(V) * 8, s), k1(ctx, size_t(V) * 8, s), v0(ctx, size_t(V) * 4, s), v1(ctx, size_t(V) * 4, s);
+    Buf rs(ctx, gt::radix_scratch_bytes(V, true, 4), s);
+    count_keys_kernel<<<gt::grid_for(V, threads, cap), threads, 0, s>>>(wc, V, N, k0.as<uint64_t>(),
+                                                                        v0.as<uint32_t>());
+    GT_LAUNCH_CHECK();
+    gt::radix_sort_u64(k0.as<uint64_t>(), k1.as<uint64_t>(), v0.p, v1.p, 4, V, 0, bits_for(N), rs.p, s);
+    count_unkey_kernel<<<gt::grid_for(V, threads, cap), threads, 0, s>>>(k1.as<uint64_t>(), v1.as<uint32_t>(), V, N,
+                                                                         words, counts, nlen);
+    GT_LAUNCH_CHECK();
+  }
+  rb.field_dyn("word", words, nlen);
+  rb.field_dyn("count", counts, nlen);
+  GT_CUDA(cudaMemcpyAsync(rb.status(), ctx->d_status, 4, cudaMemcpyDeviceToDevice, s));
+  return rb.finish();
+}
+
+}  // namespace
+
 GT_API gt_status gt_sort(gt_grammar* g, int order, void* stream, gt_result** out) {
   if (!g || !out || (order != 0 && order != 1)) return GT_EINVAL;
   *out = nullptr;
   return guard(g->ctx, [&] {
-    gt_ctx* ctx = g->ctx;
-    use_device(ctx);
+    use_device(g->ctx);
     cudaStream_t s = as_stream(stream);
-    const int64_t V = g->d.V;
-    const int threads = 256, cap = ctx->num_sms * 8;
-    ResultBuilder rb(ctx, s);
-    auto* words = static_cast<int32_t*>(rb.alloc(size_t(V) * 4));
-    auto* counts = static_cast<uint64_t*>(rb.alloc(size_t(V) * 8));
-    int64_t* nlen = rb.new_len_slot();
-    Buf wc(ctx, size_t(V) * 8, s);
+    Buf wc(g->ctx, size_t(g->d.V) * 8, s);
     {
-      Buf wt(ctx, size_t(g->d.R) * 8, s);
+      Buf wt(g->ctx, size_t(g->d.R) * 8, s);
       gt::run_rule_weights(g, wt.as<uint64_t>(), s);
       gt::run_word_count(g, wt.as<uint64_t>(), wc.as<uint64_t>(), s);
     }
-    gt::Phase ph(ctx, "sort_canon", s);
-    if (order == 0) {
-      Buf flag(ctx, size_t(V) * 8, s), pos(ctx, size_t(V) * 8, s), sc(ctx, gt::scan_scratch_bytes(V), s);
-      nonzero_flags_kernel<<<gt::grid_for(V, threads, cap), threads, 0, s>>>(wc.as<uint64_t>(), V, flag.as<int64_t>());
-      GT_LAUNCH_CHECK();
-      gt::exclusive_scan_i64(flag.as<int64_t>(), pos.as<int64_t>(), V, sc.p, s);
-      compact_words_kernel<<<gt::grid_for(V, threads, cap), threads, 0, s>>>(wc.as<uint64_t>(), V, pos.as<int64_t>(),
-                                                                              words, counts, nlen);
-      GT_LAUNCH_CHECK();
-    } else {
-      const uint64_t N = g->d.N;
-      Buf k0(ctx, size_t(V) * 8, s), k1(ctx, size_t(V) * 8, s), v0(ctx, size_t(V) * 4, s), v1(ctx, size_t(V) * 4, s);
-      Buf rs(ctx, gt::radix_scratch_bytes(V, true, 4), s);
-      count_keys_kernel<<<gt::grid_for(V, threads, cap), threads, 0, s>>>(wc.as<uint64_t>(), V, N, k0.as<uint64_t>(),
-                                                                          v0.as<uint32_t>());
-      GT_LAUNCH_CHECK();
-      gt::radix_sort_u64(k0.as<uint64_t>(), k1.as<uint64_t>(), v0.p, v1.p, 4, V, 0, bits_for(N), rs.p, s);
-      count_unkey_kernel<<<gt::grid_for(V, threads, cap), threads, 0, s>>>(k1.as<uint64_t>(), v1.as<uint32_t>(), V, N,
-                                                                           words, counts, nlen);
-      GT_LAUNCH_CHECK();
-    }
-    rb.field_dyn("word", words, nlen);
-    rb.field_dyn("count", counts, nlen);
-    GT_CUDA(cudaMemcpyAsync(rb.status(), ctx->d_status, 4, cudaMemcpyDeviceToDevice, s));
-    *out = rb.finish();
+    *out = sort_from_counts(g, wc.as<uint64_t>(), order, s);
   });
+}
+
+GT_API gt_status gt_term_vector(gt_grammar* g, int top_k, void* stream, gt_result** out) {
+  if (!g || !out || top_k < 0) return GT_EINVAL;
+  *out = nullptr;
+  return guard(g->ctx, [&] {
+    use_device(g->ctx);
+    *out = gt::run_term_vector(g, top_k, as_stream(stream));
+  });
+}
+
+GT_API gt_status gt_inverted_index(gt_grammar* g, void* stream, gt_result** out) {
+  if (!g || !out) return GT_EINVAL;
+  *out = nullptr;
+  return guard(g->ctx, [&] {
+    use_device(g->ctx);
+    *out = gt::run_inverted_index(g, as_stream(stream));
+  });
+}
+
+// ============================================================================
+// batches: several analytics over one or more grammars, one traversal each
+// ============================================================================
+
+GT_API gt_status gt_run_batch(gt_ctx* ctx, const gt_query* q, int nq, void* stream, gt_result** out) {
+  if (!ctx || (nq > 0 && (!q || !out)) || nq < 0) return GT_EINVAL;
+  for (int i = 0; i < nq; ++i) {
+    out[i] = nullptr;
+    if (!q[i].grammar || q[i].grammar->ctx != ctx) return GT_EINVAL;
+    if (q[i].kind < GT_Q_WORD_COUNT || q[i].kind > GT_Q_TERM_VECTOR) return GT_EINVAL;
+    if (q[i].kind == GT_Q_WORD_COUNT && !q[i].d_counts) return GT_EINVAL;
+    if (q[i].kind == GT_Q_SORT && q[i].param != 0 && q[i].param != 1) return GT_EINVAL;
+    if (q[i].kind == GT_Q_TERM_VECTOR && q[i].param < 0) return GT_EINVAL;
+  }
+  gt_status st = guard(ctx, [&] {
+    use_device(ctx);
+    cudaStream_t s = as_stream(stream);
+    std::vector<bool> done(size_t(nq), false);
+    for (int i = 0; i < nq; ++i) {
+      if (done[i]) continue;
+      gt_grammar* g = q[i].grammar;
+      std::vector<int> same;
+      for (int j = i; j < nq; ++j)
+        if (!done[j] && q[j].grammar == g) same.push_back(j);
+      // word count and sort share the weights and the counts
+      int first_wc = -1;
+      bool need_counts = false;
+      for (int j : same) {
+        if (q[j].kind == GT_Q_WORD_COUNT && first_wc < 0) first_wc = j;
+        if (q[j].kind == GT_Q_WORD_COUNT || q[j].kind == GT_Q_SORT) need_counts = true;
+      }
+      if (need_counts) {
+        Buf scratch;
+        uint64_t* counts = first_wc >= 0 ? q[first_wc].d_counts : nullptr;
+        if (!counts) {
+          scratch = Buf(ctx, size_t(g->d.V) * 8, s);
+          counts = scratch.as<uint64_t>();
+        }
+        {
+          Buf wt(ctx, size_t(g->d.R) * 8, s);
+          gt::run_rule_weights(g, wt.as<uint64_t>(), s);
+          gt::run_word_count(g, wt.as<uint64_t>(), counts, s);
+        }
+        for (int j : same) {
+          if (q[j].kind == GT_Q_WORD_COUNT && q[j].d_counts != counts)
+            GT_CUDA(cudaMemcpyAsync(q[j].d_counts, counts, size_t(g->d.V) * 8, cudaMemcpyDeviceToDevice, s));
+          if (q[j].kind == GT_Q_SORT) out[j] = sort_from_counts(g, counts, q[j].param, s);
+        }
+      }
+      // term vectors and inverted index share the per-file traversal
+      std::vector<int> tv_idx, tv_k;
+      int ii = -1;
+      for (int j : same) {
+        if (q[j].kind == GT_Q_TERM_VECTOR) {
+          tv_idx.push_back(j);
+          tv_k.push_back(q[j].param);
+        }
+        if (q[j].kind == GT_Q_INVERTED_INDEX && ii < 0) ii = j;
+      }
+      if (!tv_idx.empty() || ii >= 0) {
+        std::vector<gt_result*> tvr(tv_idx.size(), nullptr);
+        gt_result* iir = nullptr;
+        gt::run_file_batch(g, tv_k.data(), int(tv_k.size()), tvr.data(), ii >= 0 ? &iir : nullptr, s);
+        for (size_t k = 0; k < tv_idx.size(); ++k) out[tv_idx[k]] = tvr[k];
+        if (ii >= 0) out[ii] = iir;
+        for (int j : same)  // a second inverted-index query on the same grammar gets its own copy
+          if (q[j].kind == GT_Q_INVERTED_INDEX && j != ii) out[j] = gt::run_inverted_index(g, s);
+      }
+      for (int j : same) done[j] = true;
+    }
+  });
+  if (st != GT_OK)
+    for (int i = 0; i < nq; ++i)
+      if (out[i]) {
+        gt_free_result(out[i]);
+        out[i] = nullptr;
+      }
+  return st;
 }
 
 // ============================================================================
@@ -417,12 +505,9 @@ GT_API gt_status gt_result_view(gt_result* r, const char* field, const void** d_
 GT_API gt_status gt_free_result(gt_result* r) {
   if (!r) return GT_EINVAL;
   cudaSetDevice(r->ctx->device);
-  if (r->done) {
-    cudaEventSynchronize(r->done);
-    cudaEventDestroy(r->done);
-  }
+  if (r->done) cudaEventSynchronize(r->done);
   for (void* p : r->owned) cudaFreeAsync(p, nullptr);
-  if (r->h_lens) cudaFreeHost(r->h_lens);
+  r->ctx->give_back(r->h_lens, r->done);
   delete r;
   return GT_OK;
 }

@@ -1,0 +1,697 @@
+// Per-file analytics: term vector and inverted index (Section VI), with the
+// top-down traversal of Section IV-A carrying file information from the root
+// to every rule ("a small buffer ... in each rule indicating its file
+// information", the strategy the paper picks when there are few files).
+//
+// GB300 form, for up to 64 files:
+//   1. file masks, top-down: mask[r] = files whose expansion contains rule r,
+//      a 64-bit set per rule, ORed over parents level by level;
+//   2. memory pool: popcount(mask) slots per rule, placed by an exclusive scan;
+//   3. per-file weights, top-down: slot (r, f) = occurrences of r in file f,
+//      from the root's per-file references plus mult * parent weight;
+//   4. rule words per file: every (file, rule) pair emits the rule's own words
+//      with that weight, grouped by file (radix sort by file, then a scan);
+//   5. one CTA per (file, 2^14-word bucket) builds a dense shared-memory
+//      histogram from the file's root segment and emitted rule words - the
+//      CTAs of one file run together, so the file's data is read from HBM once
+//      and from L2 by the others - and writes the bucket's nonzero counts in
+//      word order plus a bit per word for the inverted index;
+//   6. the (file, bucket) pieces are concatenated into the term vector and
+//      the bits are turned into ascending file lists for the inverted index.
+#include <algorithm>
+
+#include "gt_device.cuh"
+
+namespace gt {
+namespace {
+
+constexpr int kFBLog2 = 14;
+constexpr int kFBucket = 1 << kFBLog2;
+constexpr int kTvThreads = 512;
+constexpr int kBinsPerThread = kFBucket / kTvThreads;  // 32: one mask word per thread
+static_assert(kBinsPerThread == 32, "one 32-bit mask word per thread");
+
+__global__ void fmask_root_kernel(const int64_t* __restrict__ rfile_off, const int32_t* __restrict__ rfile_f,
+                                  int32_t R, unsigned long long* __restrict__ mask) {
+  for (int64_t c = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; c < R; c += int64_t(gridDim.x) * blockDim.x) {
+    unsigned long long m = 0;
+    for (int64_t e = rfile_off[c]; e < rfile_off[c + 1]; ++e) m |= 1ull << rfile_f[e];
+    mask[c] = m;
+  }
+}
+
+// OR of the parents' masks for the children on one level (edges grouped by
+// child; the root's own mask is 0, its references came from fmask_root).
+__global__ void fmask_edges_kernel(const int32_t* __restrict__ lchild, const int32_t* __restrict__ lpar, int64_t a,
+                                   int64_t b, unsigned long long* __restrict__ mask) {
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t i = a + blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i - lane < b; i += stride) {
+    const bool in = i < b;
+    const int32_t c = in ? lchild[i] : -1;
+    unsigned long long v = in ? mask[lpar[i]] : 0ull;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long u = __shfl_down_sync(0xffffffffu, v, o);
+      const int32_t c2 = __shfl_down_sync(0xffffffffu, c, o);
+      if (lane + o < 32 && c2 == c) v |= u;
+    }
+    const int32_t cp = __shfl_up_sync(0xffffffffu, c, 1);
+    if (in && (lane == 0 || cp != c) && v) atomicOr(&mask[c], v);
+  }
+}
+
+__global__ void popc_kernel(const unsigned long long* __restrict__ mask, int32_t R, int64_t* __restrict__ cnt) {
+  for (int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; r < R; r += int64_t(gridDim.x) * blockDim.x)
+    cnt[r] = r == 0 ? 0 : __popcll(mask[r]);
+}
+
+__device__ __forceinline__ int64_t slot_of(const int64_t* off, const unsigned long long* mask, int32_t r, int f) {
+  return off[r] + __popcll(mask[r] & ((1ull << f) - 1ull));
+}
+
+// The root's per-file references give the first part of every weight.
+__global__ void fweight_root_kernel(const int64_t* __restrict__ rfile_off, const int32_t* __restrict__ rfile_f,
+                                    const uint32_t* __restrict__ rfile_m, int32_t R, const int64_t* __restrict__ off,
+                                    const unsigned long long* __restrict__ mask, uint32_t* __restrict__ w) {
+  for (int64_t c = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; c < R; c += int64_t(gridDim.x) * blockDim.x)
+    for (int64_t e = rfile_off[c]; e < rfile_off[c + 1]; ++e) w[slot_of(off, mask, int32_t(c), rfile_f[e])] = rfile_m[e];
+}
+
+// One level: every non-root parent edge adds mult * (parent's weight in file f)
+// to the child's slot for f.
+__global__ void fweight_edges_kernel(const int32_t* __restrict__ lchild, const int32_t* __restrict__ lpar,
+                                     const uint32_t* __restrict__ lmult, int64_t a, int64_t b,
+                                     const int64_t* __restrict__ off, const unsigned long long* __restrict__ mask,
+                                     uint32_t* __restrict__ w) {
+  for (int64_t i = a + blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < b; i += int64_t(gridDim.x) * blockDim.x) {
+    const int32_t p = lpar[i];
+    if (p == 0) continue;
+    const int32_t c = lchild[i];
+    const uint32_t m = lmult[i];
+    unsigned long long pm = mask[p];
+    const unsigned long long cm = mask[c];
+    const int64_t po = off[p], co = off[c];
+    int k = 0;
+    while (pm) {
+      const int f = __ffsll(pm) - 1;
+      pm &= pm - 1;
+      atomicAdd(&w[co + __popcll(cm & ((1ull << f) - 1ull))], m * w[po + k]);
+      ++k;
+    }
+  }
+}
+
+// (file << 32 | rule) keys of every (rule, file) slot, rule-major.
+__global__ void fentry_keys_kernel(const unsigned long long* __restrict__ mask, const int64_t* __restrict__ off,
+                                   int32_t R, uint64_t* __restrict__ keys) {
+  for (int64_t r = 1 + blockIdx.x * int64_t(blockDim.x) + threadIdx.x; r < R; r += int64_t(gridDim.x) * blockDim.x) {
+    unsigned long long m = mask[r];
+    int64_t o = off[r];
+    while (m) {
+      const int f = __ffsll(m) - 1;
+      m &= m - 1;
+      keys[o++] = (uint64_t(f) << 32) | uint64_t(r);
+    }
+  }
+}
+
+// Keys past the real entries (n_dev) carry file F so they sort last.
+__global__ void pad_keys_kernel(uint64_t* __restrict__ keys, const int64_t* __restrict__ n_dev, int64_t bound,
+                                int32_t F) {
+  const int64_t n = *n_dev;
+  for (int64_t i = n + blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < bound; i += int64_t(gridDim.x) * blockDim.x)
+    keys[i] = uint64_t(uint32_t(F)) << 32;
+}
+
+__global__ void entry_words_kernel(const uint64_t* __restrict__ keys, int64_t n, const int32_t* __restrict__ W,
+                                   int32_t F, int64_t* __restrict__ cnt) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    cnt[i] = int32_t(keys[i] >> 32) < F ? W[uint32_t(keys[i])] : 0;
+}
+
+// Each (file, rule) entry writes the rule's own words with the entry's weight.
+__global__ void expand_words_kernel(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ wts, int64_t n,
+                                    const int64_t* __restrict__ pos, DevGrammar d, int32_t* __restrict__ xw,
+                                    uint32_t* __restrict__ xwt) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    if (int32_t(keys[i] >> 32) >= d.F) continue;  // padding
+    const int32_t r = int32_t(uint32_t(keys[i]));
+    const uint32_t wt = wts[i];
+    int64_t o = pos[i];
+    for (int64_t j = d.rule_off[r]; j < d.rule_off[r + 1]; ++j) {
+      const int32_t s = d.sym[j];
+      if (s < d.V) {
+        xw[o] = s;
+        xwt[o] = wt;
+        ++o;
+      }
+    }
+  }
+}
+
+// xoff[f] = position of file f's first emitted word.
+__global__ void file_starts_kernel(const int64_t* __restrict__ fstart, const int64_t* __restrict__ pos,
+                                   const int64_t* __restrict__ wcnt, int64_t n, int32_t F, int64_t* __restrict__ xoff) {
+  for (int32_t f = blockIdx.x * blockDim.x + threadIdx.x; f <= F; f += gridDim.x * blockDim.x) {
+    const int64_t i = fstart[f];
+    xoff[f] = i < n ? pos[i] : (n > 0 ? pos[n - 1] + wcnt[n - 1] : 0);
+  }
+}
+
+struct TvSlots {
+  int32_t* word;   // [F * nb * kFBucket]
+  uint32_t* cnt;   // same
+  int64_t* nnz;    // [F * nb]
+  uint32_t* bits;  // [F * nb * kTvThreads]: bit l of word t = word (bucket base + 32 t + l) occurs
+};
+
+constexpr int kChunk = kFileChunk;  // items per file-pure chunk
+constexpr int kCsThreads = 512;
+constexpr int kCsWarps = kCsThreads / 32;
+constexpr int kCsItems = kChunk / kCsThreads;
+constexpr int kMaxNb = 128;
+
+// A stream of (file-ordered) word items cut into chunks that never cross a
+// file: chunk c covers items [start[c], start[c] + len[c]) of file file_of(c);
+// the chunks of file f are [foff[f], foff[f+1]).
+struct Chunks {
+  const int64_t* start;
+  const int32_t* len;
+  const int64_t* foff;
+  const int64_t* count;  // device: number of chunks
+};
+
+// Counting sort of one chunk by word bucket, in shared memory, written back
+// to the chunk's own item range (one entry per word, so it always fits):
+// root words become their 14-bit index (uint16), rule words (index | weight
+// << 16) as uint64.  runs[c * nb + b] = (start, length) of bucket b's entries.
+template <bool kWeighted>
+__global__ void __launch_bounds__(kCsThreads) chunk_sort_kernel(Chunks ch, const int32_t* __restrict__ items,
+                                                                const uint32_t* __restrict__ wts, int nb, int32_t V,
+                                                                void* __restrict__ out, int64_t* __restrict__ run_start,
+                                                                int32_t* __restrict__ run_len) {
+  __shared__ uint32_t wcnt[kCsWarps][kMaxNb + 1];
+  __shared__ uint32_t bstart[kMaxNb + 1];
+  __shared__ __align__(16) unsigned char stage_raw[kChunk * (kWeighted ? 8 : 2)];
+  const int64_t nch = *ch.count;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int64_t c = blockIdx.x; c < nch; c += gridDim.x) {
+    for (int i = tid; i < kCsWarps * (kMaxNb + 1); i += kCsThreads) (&wcnt[0][0])[i] = 0;
+    __syncthreads();
+    const int64_t base = ch.start[c];
+    const int n = ch.len[c];
+    int32_t w[kCsItems];
+    uint32_t rank[kCsItems];
+#pragma unroll
+    for (int j = 0; j < kCsItems; ++j) {
+      const int i = j * kCsThreads + tid;  // warp-contiguous: item order inside a warp is lane order
+      w[j] = i < n ? items[base + i] : -1;
+      if (uint32_t(w[j]) < uint32_t(V)) rank[j] = atomicAdd(&wcnt[warp][w[j] >> kFBLog2], 1u);
+    }
+    __syncthreads();
+    // exclusive prefix over (bucket, warp): warp b0.. scans bucket b over the 16 warps
+    for (int b = warp; b < nb; b += kCsWarps) {
+      const uint32_t x = lane < kCsWarps ? wcnt[lane][b] : 0u;
+      uint32_t incl = x;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += u;
+      }
+      if (lane < kCsWarps) wcnt[lane][b] = incl - x;
+      if (lane == 31) bstart[b] = incl;  // bucket total, turned into a start below
+    }
+    __syncthreads();
+    if (warp == 0) {
+      uint32_t run = 0;
+      for (int b0 = 0; b0 < nb; b0 += 32) {
+        const int b = b0 + lane;
+        const uint32_t x = b < nb ? bstart[b] : 0u;
+        uint32_t incl = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += u;
+        }
+        if (b < nb) {
+          bstart[b] = run + incl - x;
+          run_start[c * nb + b] = base + run + incl - x;
+          run_len[c * nb + b] = int32_t(x);
+        }
+        run += __shfl_sync(0xffffffffu, incl, 31);
+      }
+      if (lane == 0) bstart[kMaxNb] = run;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kCsItems; ++j) {
+      if (uint32_t(w[j]) >= uint32_t(V)) continue;
+      const int b = w[j] >> kFBLog2;
+      const uint32_t pos = bstart[b] + wcnt[warp][b] + rank[j];
+      const uint32_t local = uint32_t(w[j]) & (kFBucket - 1);
+      if (kWeighted)
+        reinterpret_cast<uint64_t*>(stage_raw)[pos] =
+            (uint64_t(wts[base + j * kCsThreads + tid]) << 16) | local;
+      else
+        reinterpret_cast<uint16_t*>(stage_raw)[pos] = uint16_t(local);
+    }
+    __syncthreads();
+    const uint32_t total = bstart[kMaxNb];
+    if (kWeighted) {
+      uint64_t* o = static_cast<uint64_t*>(out) + base;
+      for (uint32_t i = tid; i < total; i += kCsThreads) o[i] = reinterpret_cast<uint64_t*>(stage_raw)[i];
+    } else {
+      uint16_t* o = static_cast<uint16_t*>(out) + base;
+      for (uint32_t i = tid; i < total; i += kCsThreads) o[i] = reinterpret_cast<uint16_t*>(stage_raw)[i];
+    }
+    __syncthreads();
+  }
+}
+
+// Chunk table of the emitted rule words: file f's words [xoff[f], xoff[f+1]).
+// One block; thread f cuts file f (F <= 64 on this path).
+__global__ void rule_chunks_kernel(const int64_t* __restrict__ xoff, int32_t F, int64_t* __restrict__ start,
+                                   int32_t* __restrict__ len, int64_t* __restrict__ foff, int64_t* __restrict__ count) {
+  __shared__ int64_t nch[65];
+  const int f = threadIdx.x;
+  if (f < F) nch[f] = (xoff[f + 1] - xoff[f] + kChunk - 1) / kChunk;
+  __syncthreads();
+  if (f == 0) {
+    int64_t c = 0;
+    for (int32_t i = 0; i < F; ++i) {
+      const int64_t n = nch[i];
+      nch[i] = c;
+      c += n;
+    }
+    nch[F] = c;
+    *count = c;
+  }
+  __syncthreads();
+  if (f <= F) foff[f] = nch[f];
+  if (f < F) {
+    int64_t c = nch[f];
+    for (int64_t p = xoff[f]; p < xoff[f + 1]; p += kChunk, ++c) {
+      start[c] = p;
+      len[c] = int32_t(min(int64_t(kChunk), xoff[f + 1] - p));
+    }
+  }
+}
+
+// CTA (f, b): dense histogram of file f's words in bucket b, from the bucket-b
+// runs of f's root chunks and rule-word chunks.
+__global__ void __launch_bounds__(kTvThreads) tv_hist_kernel(int32_t F, int nb, Chunks rc, const int64_t* __restrict__ rrs,
+                                                             const int32_t* __restrict__ rrl,
+                                                             const uint16_t* __restrict__ rent, Chunks xc,
+                                                             const int64_t* __restrict__ xrs,
+                                                             const int32_t* __restrict__ xrl,
+                                                             const uint64_t* __restrict__ xent, TvSlots out) {
+  __shared__ uint32_t hist[kFBucket];
+  __shared__ int64_t warp_tot[kTvThreads / 32 + 1];
+  const int f = blockIdx.x / nb, b = blockIdx.x % nb;
+  const int tid = threadIdx.x;
+  for (int i = tid; i < kFBucket; i += kTvThreads) hist[i] = 0;
+  __syncthreads();
+  // one chunk run per warp at a time, so many runs are in flight
+  const int lane0 = tid & 31, warp0 = tid >> 5;
+  for (int64_t c = rc.foff[f] + warp0; c < rc.foff[f + 1]; c += kTvThreads / 32) {
+    const int64_t s0 = rrs[c * nb + b];
+    const int32_t n = rrl[c * nb + b];
+    for (int i = lane0; i < n; i += 32) atomicAdd(&hist[rent[s0 + i]], 1u);
+  }
+  for (int64_t c = xc.foff[f] + warp0; c < xc.foff[f + 1]; c += kTvThreads / 32) {
+    const int64_t s0 = xrs[c * nb + b];
+    const int32_t n = xrl[c * nb + b];
+    for (int i = lane0; i < n; i += 32) {
+      const uint64_t e = xent[s0 + i];
+      atomicAdd(&hist[uint32_t(e) & (kFBucket - 1)], uint32_t(e >> 16));
+    }
+  }
+  __syncthreads();
+  // compaction in word order: thread t owns bins [32 t, 32 t + 32)
+  uint32_t bits = 0;
+#pragma unroll
+  for (int j = 0; j < kBinsPerThread; ++j)
+    if (hist[tid * kBinsPerThread + j]) bits |= 1u << j;
+  const int n = __popc(bits);
+  const int lane = tid & 31, warp = tid >> 5;
+  int incl = n;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int u = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += u;
+  }
+  if (lane == 31) warp_tot[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    int64_t wv = lane < kTvThreads / 32 ? warp_tot[lane] : 0;
+    int64_t wi = wv;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t u = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += u;
+    }
+    if (lane < kTvThreads / 32) warp_tot[lane] = wi - wv;
+    if (lane == kTvThreads / 32 - 1) warp_tot[kTvThreads / 32] = wi;
+  }
+  __syncthreads();
+  int64_t o = warp_tot[warp] + incl - n;
+  const int64_t slot = int64_t(blockIdx.x) * kFBucket;
+  const int32_t wbase = b << kFBLog2;
+#pragma unroll 4
+  for (int j = 0; j < kBinsPerThread; ++j)
+    if (bits >> j & 1u) {
+      out.word[slot + o] = wbase + tid * kBinsPerThread + j;
+      out.cnt[slot + o] = hist[tid * kBinsPerThread + j];
+      ++o;
+    }
+  out.bits[int64_t(blockIdx.x) * kTvThreads + tid] = bits;
+  if (tid == 0) out.nnz[blockIdx.x] = warp_tot[kTvThreads / 32];
+}
+
+// Copy every (file, bucket) piece to its place in the term vector.
+__global__ void tv_gather_kernel(TvSlots in, const int64_t* __restrict__ off, int32_t* __restrict__ word,
+                                 uint64_t* __restrict__ cnt) {
+  const int64_t slot = int64_t(blockIdx.x) * kFBucket;
+  const int64_t n = in.nnz[blockIdx.x], o = off[blockIdx.x];
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    word[o + i] = in.word[slot + i];
+    cnt[o + i] = in.cnt[slot + i];
+  }
+}
+
+__global__ void tv_file_off_kernel(const int64_t* __restrict__ off, int nb, int32_t F,
+                                   const int64_t* __restrict__ total, int64_t* __restrict__ tv_off) {
+  for (int32_t f = blockIdx.x * blockDim.x + threadIdx.x; f <= F; f += gridDim.x * blockDim.x)
+    tv_off[f] = f < F ? off[int64_t(f) * nb] : *total;
+}
+
+// Inverted index: files holding each word (bit set in that file's piece).
+__global__ void ii_count_kernel(const uint32_t* __restrict__ bits, int nb, int32_t F, int32_t V,
+                                int64_t* __restrict__ cnt) {
+  for (int64_t w = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; w < V; w += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t b = w >> kFBLog2, l = w & (kFBucket - 1);
+    int c = 0;
+    for (int32_t f = 0; f < F; ++f) c += (bits[(int64_t(f) * nb + b) * kTvThreads + (l >> 5)] >> (l & 31)) & 1u;
+    cnt[w] = c;
+  }
+}
+
+__global__ void ii_fill_kernel(const uint32_t* __restrict__ bits, int nb, int32_t F, int32_t V,
+                               const int64_t* __restrict__ off, int32_t* __restrict__ files) {
+  for (int64_t w = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; w < V; w += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t b = w >> kFBLog2, l = w & (kFBucket - 1);
+    int64_t o = off[w];
+    for (int32_t f = 0; f < F; ++f)
+      if ((bits[(int64_t(f) * nb + b) * kTvThreads + (l >> 5)] >> (l & 31)) & 1u) files[o++] = f;
+  }
+}
+
+__global__ void last_total_kernel(const int64_t* __restrict__ ex, const int64_t* __restrict__ cnt, int64_t n,
+                                  int64_t* __restrict__ out, int64_t* __restrict__ out2) {
+  const int64_t t = n > 0 ? ex[n - 1] + cnt[n - 1] : 0;
+  *out = t;
+  if (out2) *out2 = t;
+}
+
+// top-k: key = file << 32 | (2^32 - 1 - count), sorted stably over entries that
+// are already in ascending word order inside each file.
+__global__ void topk_keys_kernel(const int32_t* __restrict__ word, const uint64_t* __restrict__ cnt,
+                                 const int64_t* __restrict__ tv_off, int32_t F, int64_t bound,
+                                 uint64_t* __restrict__ keys, uint32_t* __restrict__ idx) {
+  const int64_t n = tv_off[F];
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < bound; i += int64_t(gridDim.x) * blockDim.x) {
+    idx[i] = uint32_t(i);
+    if (i >= n) {
+      keys[i] = uint64_t(uint32_t(F)) << 32;  // padding sorts last
+      continue;
+    }
+    int32_t lo = 0, hi = F;  // file of entry i: last f with tv_off[f] <= i
+    while (hi - lo > 1) {
+      const int32_t mid = (lo + hi) >> 1;
+      if (tv_off[mid] <= i) lo = mid;
+      else hi = mid;
+    }
+    keys[i] = (uint64_t(lo) << 32) | uint64_t(0xffffffffu - uint32_t(cnt[i]));
+  }
+}
+
+__global__ void topk_count_kernel(const int64_t* __restrict__ tv_off, int32_t F, int k, int64_t* __restrict__ cnt) {
+  for (int32_t f = blockIdx.x * blockDim.x + threadIdx.x; f < F; f += gridDim.x * blockDim.x)
+    cnt[f] = min(int64_t(k), tv_off[f + 1] - tv_off[f]);
+}
+
+__global__ void topk_gather_kernel(const uint32_t* __restrict__ idx, const int64_t* __restrict__ tv_off,
+                                   const int64_t* __restrict__ k_off, int32_t F, const int32_t* __restrict__ word,
+                                   const uint64_t* __restrict__ cnt, int32_t* __restrict__ kw,
+                                   uint64_t* __restrict__ kc) {
+  for (int32_t f = blockIdx.x; f < F; f += gridDim.x) {
+    const int64_t n = k_off[f + 1] - k_off[f];
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+      const uint32_t j = idx[tv_off[f] + i];
+      kw[k_off[f] + i] = word[j];
+      kc[k_off[f] + i] = cnt[j];
+    }
+  }
+}
+
+struct FileHist {
+  Buf slot_word, slot_cnt, nnz, bits, off, total;
+  int nb = 0;
+  int64_t bound = 0;  // bound on term-vector entries (= inverted-index postings)
+};
+
+int bits_for(int64_t x) {
+  int b = 1;
+  while ((int64_t(1) << b) <= x) ++b;
+  return b;
+}
+
+// Steps 1-5: the dense (file, bucket) pieces, their sizes and the II bits.
+// Nothing here waits for the GPU: buffers are sized by bounds computed when
+// the grammar was loaded, and sorts run over padded, bound-sized arrays.
+void file_hist(gt_grammar* g, cudaStream_t s, FileHist& fh) {
+  gt_ctx* ctx = g->ctx;
+  const DevGrammar& d = g->d;
+  const int threads = 256, cap = ctx->num_sms * 16;
+  const int32_t R = d.R, F = d.F, V = d.V;
+  if (F > 64) fail(GT_EOVERFLOW, "per-file analytics use the top-down strategy, limited to 64 files");
+  if (d.N >= (uint64_t(1) << 32)) fail(GT_EOVERFLOW, "per-file analytics need fewer than 2^32 tokens per grammar");
+  if (V > (1 << 21)) fail(GT_EOVERFLOW, "per-file analytics support num_words <= 2^21");
+  const int64_t EB = g->fentry_bound, XB = g->fword_bound;
+  Phase ph(ctx, "file_weights", s);
+  Buf mask(ctx, size_t(R) * 8, s), cnt(ctx, size_t(R) * 8, s), off(ctx, size_t(R) * 8, s);
+  Buf sc(ctx, scan_scratch_bytes(R), s), dev(ctx, 8 * 8, s);
+  int64_t* nnz_d = dev.as<int64_t>();      // (rule, file) pairs
+  int64_t* nx_d = dev.as<int64_t>() + 1;   // emitted rule words
+  auto* M = mask.as<unsigned long long>();
+  fmask_root_kernel<<<grid_for(R, threads, cap), threads, 0, s>>>(d.rfile_off, d.rfile_f, R, M);
+  GT_LAUNCH_CHECK();
+  for (int lv = 2; lv < d.depth; ++lv) {
+    const int64_t a = g->ledge_off[lv], b = g->ledge_off[lv + 1];
+    if (b > a) {
+      fmask_edges_kernel<<<grid_for(b - a, threads, cap), threads, 0, s>>>(d.ledge_child, d.ledge_par, a, b, M);
+      GT_LAUNCH_CHECK();
+    }
+  }
+  popc_kernel<<<grid_for(R, threads, cap), threads, 0, s>>>(M, R, cnt.as<int64_t>());
+  GT_LAUNCH_CHECK();
+  exclusive_scan_i64(cnt.as<int64_t>(), off.as<int64_t>(), R, sc.p, s);
+  last_total_kernel<<<1, 1, 0, s>>>(off.as<int64_t>(), cnt.as<int64_t>(), R, nnz_d, nullptr);
+  GT_LAUNCH_CHECK();
+  Buf w(ctx, size_t(EB) * 4, s);
+  if (EB > 0) GT_CUDA(cudaMemsetAsync(w.p, 0, size_t(EB) * 4, s));
+  fweight_root_kernel<<<grid_for(R, threads, cap), threads, 0, s>>>(d.rfile_off, d.rfile_f, d.rfile_m, R,
+                                                                     off.as<int64_t>(), M, w.as<uint32_t>());
+  GT_LAUNCH_CHECK();
+  for (int lv = 2; lv < d.depth; ++lv) {
+    const int64_t a = g->ledge_off[lv], b = g->ledge_off[lv + 1];
+    if (b > a) {
+      fweight_edges_kernel<<<grid_for(b - a, threads, cap), threads, 0, s>>>(
+          d.ledge_child, d.ledge_par, d.ledge_mult, a, b, off.as<int64_t>(), M, w.as<uint32_t>());
+      GT_LAUNCH_CHECK();
+    }
+  }
+  // ---- rule words per file (file-major) ----
+  Buf keys(ctx, size_t(EB) * 8, s), skeys(ctx, size_t(EB) * 8, s), swt(ctx, size_t(EB) * 4, s);
+  Buf rs(ctx, radix_scratch_bytes(EB, true, 4), s);
+  Buf wcnt(ctx, size_t(EB) * 8, s), pos(ctx, size_t(EB) * 8, s), sc2(ctx, scan_scratch_bytes(EB), s);
+  Buf fstart(ctx, size_t(F + 1) * 8, s), xoff(ctx, size_t(F + 1) * 8, s);
+  GT_CUDA(cudaMemsetAsync(nx_d, 0, 8, s));
+  if (EB > 0) {
+    fentry_keys_kernel<<<grid_for(R, threads, cap), threads, 0, s>>>(M, off.as<int64_t>(), R, keys.as<uint64_t>());
+    GT_LAUNCH_CHECK();
+    pad_keys_kernel<<<grid_for(EB, threads, cap), threads, 0, s>>>(keys.as<uint64_t>(), nnz_d, EB, F);
+    GT_LAUNCH_CHECK();
+    radix_sort_u64(keys.as<uint64_t>(), skeys.as<uint64_t>(), w.p, swt.p, 4, EB, 32, 32 + bits_for(F), rs.p, s);
+    entry_words_kernel<<<grid_for(EB, threads, cap), threads, 0, s>>>(skeys.as<uint64_t>(), EB, d.nwords, F,
+                                                                       wcnt.as<int64_t>());
+    GT_LAUNCH_CHECK();
+    exclusive_scan_i64(wcnt.as<int64_t>(), pos.as<int64_t>(), EB, sc2.p, s);
+    last_total_kernel<<<1, 1, 0, s>>>(pos.as<int64_t>(), wcnt.as<int64_t>(), EB, nx_d, nullptr);
+    GT_LAUNCH_CHECK();
+  }
+  csr_offsets_hi(skeys.as<uint64_t>(), EB, F, fstart.as<int64_t>(), s);
+  file_starts_kernel<<<1, 128, 0, s>>>(fstart.as<int64_t>(), pos.as<int64_t>(), wcnt.as<int64_t>(), EB, F,
+                                       xoff.as<int64_t>());
+  GT_LAUNCH_CHECK();
+  Buf xw(ctx, size_t(XB) * 4, s), xwt(ctx, size_t(XB) * 4, s);
+  if (EB > 0) {
+    expand_words_kernel<<<grid_for(EB, threads, cap), threads, 0, s>>>(skeys.as<uint64_t>(), swt.as<uint32_t>(), EB,
+                                                                        pos.as<int64_t>(), d, xw.as<int32_t>(),
+                                                                        xwt.as<uint32_t>());
+    GT_LAUNCH_CHECK();
+  }
+  // ---- bucket-sorted chunks, then dense (file, bucket) histograms ----
+  const int nb = int((V + kFBucket - 1) / kFBucket);
+  const int64_t pieces = int64_t(F) * nb;
+  fh.nb = nb;
+  fh.bound = std::min<int64_t>(int64_t(d.N), pieces * kFBucket);
+  fh.slot_word = Buf(ctx, size_t(pieces) * kFBucket * 4, s);
+  fh.slot_cnt = Buf(ctx, size_t(pieces) * kFBucket * 4, s);
+  fh.nnz = Buf(ctx, size_t(pieces) * 8, s);
+  fh.bits = Buf(ctx, size_t(pieces) * kTvThreads * 4, s);
+  fh.off = Buf(ctx, size_t(pieces) * 8, s);
+  fh.total = Buf(ctx, 8, s);
+  TvSlots ts{fh.slot_word.as<int32_t>(), fh.slot_cnt.as<uint32_t>(), fh.nnz.as<int64_t>(), fh.bits.as<uint32_t>()};
+  {
+    Phase ph2(ctx, "tv_hist", s);
+    const int64_t nrc = g->root_chunks;
+    Chunks rc{d.rch_start, d.rch_len, d.rch_foff, d.rch_count};
+    Buf rent(ctx, size_t(d.root_len) * 2 + 16, s), rrs(ctx, size_t(nrc) * nb * 8, s), rrl(ctx, size_t(nrc) * nb * 4, s);
+    if (nrc > 0) {
+      chunk_sort_kernel<false><<<unsigned(std::min<int64_t>(nrc, 65535)), kCsThreads, 0, s>>>(
+          rc, d.sym, nullptr, nb, V, rent.p, rrs.as<int64_t>(), rrl.as<int32_t>());
+      GT_LAUNCH_CHECK();
+    }
+    const int64_t nxc = XB / kChunk + F + 1;  // bound on the rule-word chunks
+    Buf xcs(ctx, size_t(nxc) * 8, s), xcl(ctx, size_t(nxc) * 4, s), xcf(ctx, size_t(F + 1) * 8, s), xcn(ctx, 8, s);
+    Buf xent(ctx, size_t(XB) * 8 + 16, s), xrs(ctx, size_t(nxc) * nb * 8, s), xrl(ctx, size_t(nxc) * nb * 4, s);
+    rule_chunks_kernel<<<1, 128, 0, s>>>(xoff.as<int64_t>(), F, xcs.as<int64_t>(), xcl.as<int32_t>(), xcf.as<int64_t>(),
+                                        xcn.as<int64_t>());
+    GT_LAUNCH_CHECK();
+    Chunks xc{xcs.as<int64_t>(), xcl.as<int32_t>(), xcf.as<int64_t>(), xcn.as<int64_t>()};
+    chunk_sort_kernel<true><<<unsigned(std::min<int64_t>(nxc, 65535)), kCsThreads, 0, s>>>(
+        xc, xw.as<int32_t>(), xwt.as<uint32_t>(), nb, V, xent.p, xrs.as<int64_t>(), xrl.as<int32_t>());
+    GT_LAUNCH_CHECK();
+    tv_hist_kernel<<<unsigned(pieces), kTvThreads, 0, s>>>(F, nb, rc, rrs.as<int64_t>(), rrl.as<int32_t>(),
+                                                           rent.as<uint16_t>(), xc, xrs.as<int64_t>(),
+                                                           xrl.as<int32_t>(), xent.as<uint64_t>(), ts);
+    GT_LAUNCH_CHECK();
+  }
+  Buf sc3(ctx, scan_scratch_bytes(pieces), s);
+  exclusive_scan_i64(fh.nnz.as<int64_t>(), fh.off.as<int64_t>(), pieces, sc3.p, s);
+  last_total_kernel<<<1, 1, 0, s>>>(fh.off.as<int64_t>(), fh.nnz.as<int64_t>(), pieces, fh.total.as<int64_t>(),
+                                    nullptr);
+  GT_LAUNCH_CHECK();
+}
+
+gt_result* term_vector_from(gt_grammar* g, FileHist& fh, int top_k, cudaStream_t s) {
+  gt_ctx* ctx = g->ctx;
+  const DevGrammar& d = g->d;
+  const int threads = 256, cap = ctx->num_sms * 16;
+  ResultBuilder rb(ctx, s);
+  const int64_t pieces = int64_t(d.F) * fh.nb;
+  const int64_t nb_ = fh.bound;
+  Phase ph(ctx, "tv_out", s);
+  auto* tv_off = static_cast<int64_t*>(rb.alloc(size_t(d.F + 1) * 8));
+  TvSlots ts{fh.slot_word.as<int32_t>(), fh.slot_cnt.as<uint32_t>(), fh.nnz.as<int64_t>(), fh.bits.as<uint32_t>()};
+  if (top_k <= 0) {
+    auto* word = static_cast<int32_t*>(rb.alloc(size_t(nb_) * 4));
+    auto* cnt = static_cast<uint64_t*>(rb.alloc(size_t(nb_) * 8));
+    int64_t* len = rb.new_len_slot();
+    tv_gather_kernel<<<unsigned(pieces), 256, 0, s>>>(ts, fh.off.as<int64_t>(), word, cnt);
+    GT_LAUNCH_CHECK();
+    tv_file_off_kernel<<<1, 256, 0, s>>>(fh.off.as<int64_t>(), fh.nb, d.F, fh.total.as<int64_t>(), tv_off);
+    GT_LAUNCH_CHECK();
+    GT_CUDA(cudaMemcpyAsync(len, fh.total.p, 8, cudaMemcpyDeviceToDevice, s));
+    rb.field("offsets", tv_off, int64_t(d.F) + 1);
+    rb.field_dyn("word", word, len);
+    rb.field_dyn("count", cnt, len);
+  } else {
+    Buf tw(ctx, size_t(nb_) * 4, s), tc(ctx, size_t(nb_) * 8, s), full_off(ctx, size_t(d.F + 1) * 8, s);
+    tv_gather_kernel<<<unsigned(pieces), 256, 0, s>>>(ts, fh.off.as<int64_t>(), tw.as<int32_t>(), tc.as<uint64_t>());
+    GT_LAUNCH_CHECK();
+    tv_file_off_kernel<<<1, 256, 0, s>>>(fh.off.as<int64_t>(), fh.nb, d.F, fh.total.as<int64_t>(),
+                                         full_off.as<int64_t>());
+    GT_LAUNCH_CHECK();
+    Buf k0(ctx, size_t(nb_) * 8, s), k1(ctx, size_t(nb_) * 8, s), i0(ctx, size_t(nb_) * 4, s), i1(ctx, size_t(nb_) * 4, s);
+    Buf rs(ctx, radix_scratch_bytes(nb_, true, 4), s);
+    Buf kc(ctx, size_t(d.F) * 8 + 8, s), sc(ctx, scan_scratch_bytes(d.F + 1), s);
+    if (nb_ > 0) {
+      topk_keys_kernel<<<grid_for(nb_, threads, cap), threads, 0, s>>>(tw.as<int32_t>(), tc.as<uint64_t>(),
+                                                                        full_off.as<int64_t>(), d.F, nb_,
+                                                                        k0.as<uint64_t>(), i0.as<uint32_t>());
+      GT_LAUNCH_CHECK();
+      radix_sort_u64(k0.as<uint64_t>(), k1.as<uint64_t>(), i0.p, i1.p, 4, nb_, 0, 32 + bits_for(d.F), rs.p, s);
+    }
+    topk_count_kernel<<<1, 256, 0, s>>>(full_off.as<int64_t>(), d.F, top_k, kc.as<int64_t>());
+    GT_LAUNCH_CHECK();
+    GT_CUDA(cudaMemsetAsync(kc.as<int64_t>() + d.F, 0, 8, s));
+    exclusive_scan_i64(kc.as<int64_t>(), tv_off, d.F + 1, sc.p, s);
+    const int64_t kb = std::min<int64_t>(int64_t(top_k) * d.F, nb_);
+    auto* kw = static_cast<int32_t*>(rb.alloc(size_t(kb) * 4));
+    auto* kcnt = static_cast<uint64_t*>(rb.alloc(size_t(kb) * 8));
+    int64_t* len = rb.new_len_slot();
+    topk_gather_kernel<<<std::max(1, std::min(d.F, cap)), 256, 0, s>>>(i1.as<uint32_t>(), full_off.as<int64_t>(),
+                                                                       tv_off, d.F, tw.as<int32_t>(),
+                                                                       tc.as<uint64_t>(), kw, kcnt);
+    GT_LAUNCH_CHECK();
+    GT_CUDA(cudaMemcpyAsync(len, tv_off + d.F, 8, cudaMemcpyDeviceToDevice, s));
+    rb.field("offsets", tv_off, int64_t(d.F) + 1);
+    rb.field_dyn("word", kw, len);
+    rb.field_dyn("count", kcnt, len);
+  }
+  GT_CUDA(cudaMemcpyAsync(rb.status(), ctx->d_status, 4, cudaMemcpyDeviceToDevice, s));
+  return rb.finish();
+}
+
+gt_result* inverted_index_from(gt_grammar* g, FileHist& fh, cudaStream_t s) {
+  gt_ctx* ctx = g->ctx;
+  const DevGrammar& d = g->d;
+  ResultBuilder rb(ctx, s);
+  Phase ph(ctx, "ii_out", s);
+  const int threads = 256, cap = ctx->num_sms * 16;
+  const int64_t V = d.V;
+  auto* ii_off = static_cast<int64_t*>(rb.alloc(size_t(V + 1) * 8));
+  auto* files = static_cast<int32_t*>(rb.alloc(size_t(fh.bound) * 4));
+  int64_t* len = rb.new_len_slot();
+  Buf cnt(ctx, size_t(V + 1) * 8, s), sc(ctx, scan_scratch_bytes(V + 1), s);
+  ii_count_kernel<<<grid_for(V, threads, cap), threads, 0, s>>>(fh.bits.as<uint32_t>(), fh.nb, d.F, d.V,
+                                                                 cnt.as<int64_t>());
+  GT_LAUNCH_CHECK();
+  GT_CUDA(cudaMemsetAsync(cnt.as<int64_t>() + V, 0, 8, s));
+  exclusive_scan_i64(cnt.as<int64_t>(), ii_off, V + 1, sc.p, s);
+  ii_fill_kernel<<<grid_for(V, threads, cap), threads, 0, s>>>(fh.bits.as<uint32_t>(), fh.nb, d.F, d.V, ii_off,
+                                                                files);
+  GT_LAUNCH_CHECK();
+  GT_CUDA(cudaMemcpyAsync(len, fh.total.p, 8, cudaMemcpyDeviceToDevice, s));
+  rb.field("offsets", ii_off, V + 1);
+  rb.field_dyn("file", files, len);
+  GT_CUDA(cudaMemcpyAsync(rb.status(), ctx->d_status, 4, cudaMemcpyDeviceToDevice, s));
+  return rb.finish();
+}
+
+}  // namespace
+
+void run_file_batch(gt_grammar* g, const int* tv_topk, int n_tv, gt_result** tv_out, gt_result** ii_out,
+                    cudaStream_t s) {
+  FileHist fh;
+  file_hist(g, s, fh);
+  for (int i = 0; i < n_tv; ++i) tv_out[i] = term_vector_from(g, fh, tv_topk[i], s);
+  if (ii_out) *ii_out = inverted_index_from(g, fh, s);
+}
+
+gt_result* run_term_vector(gt_grammar* g, int top_k, cudaStream_t s) {
+  gt_result* r = nullptr;
+  run_file_batch(g, &top_k, 1, &r, nullptr, s);
+  return r;
+}
+
+gt_result* run_inverted_index(gt_grammar* g, cudaStream_t s) {
+  gt_result* r = nullptr;
+  run_file_batch(g, nullptr, 0, nullptr, &r, s);
+  return r;
+}
+
+}  // namespace gt

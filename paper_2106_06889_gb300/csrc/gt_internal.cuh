@@ -5,6 +5,7 @@
 
 #include <atomic>
 #include <cstdint>
+#include <mutex>
 #include <map>
 #include <string>
 #include <utility>
@@ -48,7 +49,8 @@ enum : uint32_t {
   ST_INVALID = 8u,
 };
 
-constexpr int kTile = 2048;  // symbols per streaming tile (512 threads x int4)
+constexpr int kTile = 2048;        // symbols per streaming tile (512 threads x int4)
+constexpr int kFileChunk = 4096;   // root symbols per file-pure chunk (per-file analytics)
 
 // Device-resident grammar and the DAG built from it at load time.  All
 // arrays are library-owned device memory.
@@ -84,6 +86,10 @@ struct DevGrammar {
   const int64_t* redge_off;  // [F+1]
   const int32_t* redge_child;
   const uint32_t* redge_mult;
+  // the root edges child-major: files referencing each rule from the root
+  const int64_t* rfile_off;  // [R+1]
+  const int32_t* rfile_f;
+  const uint32_t* rfile_m;
   // DAG levels: level(r) = longest path from a source; parents have lower levels
   int32_t depth;
   const int32_t* level;      // [R]
@@ -93,6 +99,12 @@ struct DevGrammar {
   const int32_t* nrefs;    // [R] S_r: rule references in the body
   const uint64_t* exp_len; // [R] L_r: words in the expansion
   const uint64_t* file_len;// [F] words in each file's expansion
+  // the root cut into chunks of at most kFileChunk symbols that never cross a
+  // file: chunk c = [rch_start[c], + rch_len[c]); file f's are [rch_foff[f], rch_foff[f+1])
+  const int64_t* rch_start;
+  const int32_t* rch_len;
+  const int64_t* rch_foff;
+  const int64_t* rch_count;
   uint64_t N;              // tokens in the expanded corpus
 };
 
@@ -115,6 +127,40 @@ struct gt_ctx {
   std::map<std::string, std::vector<Span>> prof;
   // tunable parameters (Section IV-A, parameter selection); see gt_set_param
   std::map<std::string, int64_t> params;
+  // recycled pinned length blocks and events of released results
+  std::mutex res_mu;
+  std::vector<int64_t*> free_lens;
+  std::vector<cudaEvent_t> free_events;
+  std::vector<void*> pinned_chunks;
+  int64_t* take_lens(int slots) {
+    std::lock_guard<std::mutex> lk(res_mu);
+    if (free_lens.empty()) {
+      const int per = 256;
+      void* p = nullptr;
+      if (cudaMallocHost(&p, size_t(per) * slots * sizeof(int64_t)) != cudaSuccess) return nullptr;
+      pinned_chunks.push_back(p);
+      for (int i = 0; i < per; ++i) free_lens.push_back(static_cast<int64_t*>(p) + size_t(i) * slots);
+    }
+    int64_t* q = free_lens.back();
+    free_lens.pop_back();
+    return q;
+  }
+  cudaEvent_t take_event() {
+    std::lock_guard<std::mutex> lk(res_mu);
+    if (free_events.empty()) {
+      cudaEvent_t e = nullptr;
+      if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+      return e;
+    }
+    cudaEvent_t e = free_events.back();
+    free_events.pop_back();
+    return e;
+  }
+  void give_back(int64_t* lens, cudaEvent_t e) {
+    std::lock_guard<std::mutex> lk(res_mu);
+    if (lens) free_lens.push_back(lens);
+    if (e) free_events.push_back(e);
+  }
   int64_t param(const char* name, int64_t dflt) const {
     auto it = params.find(name);
     return it == params.end() ? dflt : it->second;
@@ -127,6 +173,9 @@ struct gt_grammar {
   gt_grammar_info info{};
   std::vector<int64_t> lvl_off;  // host copy: rules of level l are lvl_order[lvl_off[l] .. lvl_off[l+1])
   std::vector<int64_t> ledge_off; // host copy: parent edges of level-l children are ledge_*[ledge_off[l] ..)
+  int64_t root_chunks = 0;        // host copy of *rch_count
+  int64_t fentry_bound = 0;       // bound on (rule, file) pairs with a nonzero per-file weight
+  int64_t fword_bound = 0;        // bound on rule words emitted once per such pair
   std::vector<void*> owned;      // device allocations to free with the grammar
 };
 
@@ -206,6 +255,61 @@ struct Phase {
   }
 };
 
+// ---- result construction ----------------------------------------------------
+
+// A result under construction: buffers are allocated from the pool on the
+// query's stream; data-dependent lengths are written by kernels into a small
+// device array and copied to pinned host memory when the query ends.
+struct ResultBuilder {
+  gt_result* r;
+  cudaStream_t s;
+  int64_t* d_lens = nullptr;  // device slots for data-dependent lengths; slot 0 holds the status word
+  int nslots = 0;
+  static constexpr int kMaxSlots = 8;
+
+  ResultBuilder(gt_ctx* ctx, cudaStream_t st) : s(st) {
+    r = new gt_result();
+    r->ctx = ctx;
+    r->h_lens = ctx->take_lens(kMaxSlots);
+    if (!r->h_lens) fail(GT_ENOMEM, "pinned host allocation failed");
+    void* p = nullptr;
+    GT_CUDA(cudaMallocFromPoolAsync(&p, kMaxSlots * sizeof(int64_t), ctx->pool, s));
+    r->owned.push_back(p);
+    d_lens = static_cast<int64_t*>(p);
+    GT_CUDA(cudaMemsetAsync(d_lens, 0, kMaxSlots * sizeof(int64_t), s));
+    nslots = 1;
+  }
+  uint32_t* status() { return reinterpret_cast<uint32_t*>(d_lens); }
+  int64_t* new_len_slot() {
+    if (nslots >= kMaxSlots) fail(GT_EINVAL, "too many result fields");
+    return d_lens + nslots++;
+  }
+  void* alloc(size_t bytes) {
+    void* p = nullptr;
+    GT_CUDA(cudaMallocFromPoolAsync(&p, bytes ? bytes : 16, r->ctx->pool, s));
+    r->owned.push_back(p);
+    return p;
+  }
+  void field(const char* name, void* ptr, int64_t len) { r->fields.push_back({name, ptr, len, nullptr}); }
+  void field_dyn(const char* name, void* ptr, int64_t* d_len_slot) {
+    const int64_t idx = d_len_slot - d_lens;
+    r->fields.push_back({name, ptr, -1, r->h_lens + idx});
+  }
+  gt_result* finish() {
+    GT_CUDA(cudaMemcpyAsync(r->h_lens, d_lens, kMaxSlots * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    r->done = r->ctx->take_event();
+    if (!r->done) fail(GT_ECUDA, "event creation failed");
+    GT_CUDA(cudaEventRecord(r->done, s));
+    gt_result* out = r;
+    r = nullptr;
+    return out;
+  }
+  ~ResultBuilder() {
+    if (r) gt_free_result(r);
+  }
+};
+
+
 inline int grid_for(int64_t n, int threads, int cap) {
   int64_t b = (n + threads - 1) / threads;
   if (b < 1) b = 1;
@@ -217,11 +321,21 @@ inline int grid_for(int64_t n, int threads, int cap) {
 
 // gt_load.cu
 void load_build_dag(gt_grammar* g, cudaStream_t s);
+// off[h] = first index of the sorted keys whose high 32 bits are >= h, h in [0, nh]
+void csr_offsets_hi(const uint64_t* keys, int64_t n, int64_t nh, int64_t* off, cudaStream_t s);
 
 // gt_wc.cu
 void run_rule_weights(gt_grammar* g, uint64_t* d_wt, cudaStream_t s);
 void run_word_count(gt_grammar* g, const uint64_t* d_wt, uint64_t* d_counts, cudaStream_t s);
 void run_head_tail(gt_grammar* g, int32_t* d_head, int32_t* d_tail, cudaStream_t s);
+
+// gt_file.cu: per-file analytics (top-down strategy, up to 64 files)
+gt_result* run_term_vector(gt_grammar* g, int top_k, cudaStream_t s);
+// One shared traversal for several per-file queries on one grammar: n_tv term
+// vectors (top_k each) and, if ii_out is set, the inverted index.
+void run_file_batch(gt_grammar* g, const int* tv_topk, int n_tv, gt_result** tv_out, gt_result** ii_out,
+                    cudaStream_t s);
+gt_result* run_inverted_index(gt_grammar* g, cudaStream_t s);
 
 // gt_sort.cu: device primitives
 size_t scan_scratch_bytes(int64_t n);

@@ -320,6 +320,52 @@ __global__ void sym_rule_kernel(const int64_t* __restrict__ rule_off, int32_t R,
   }
 }
 
+// Upper bound on the files holding each rule (for sizing per-file buffers
+// without waiting on the GPU): root files referencing it, plus its parents'
+// bounds, each capped at fcap.
+__global__ void fbound_init_kernel(const int64_t* __restrict__ rfile_off, int32_t R, unsigned long long* __restrict__ fb) {
+  for (int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; r < R; r += int64_t(gridDim.x) * blockDim.x)
+    fb[r] = (unsigned long long)(rfile_off[r + 1] - rfile_off[r]);
+}
+
+__global__ void fbound_edges_kernel(const int32_t* __restrict__ lchild, const int32_t* __restrict__ lpar, int64_t a,
+                                    int64_t b, unsigned long long fcap, unsigned long long* __restrict__ fb) {
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t i = a + blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i - lane < b; i += stride) {
+    const bool in = i < b;
+    const int32_t c = in ? lchild[i] : -1;
+    const int32_t p = in ? lpar[i] : 0;
+    unsigned long long v = (in && p != 0) ? min(fb[p], fcap) : 0ull;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long u = __shfl_down_sync(0xffffffffu, v, o);
+      const int32_t c2 = __shfl_down_sync(0xffffffffu, c, o);
+      if (lane + o < 32 && c2 == c) v += u;
+    }
+    const int32_t cp = __shfl_up_sync(0xffffffffu, c, 1);
+    if (in && (lane == 0 || cp != c) && v) atomicAdd(&fb[c], v);
+  }
+}
+
+__global__ void fbound_sum_kernel(const unsigned long long* __restrict__ fb, const int32_t* __restrict__ W, int32_t R,
+                                  unsigned long long fcap, unsigned long long* __restrict__ out) {
+  unsigned long long a = 0, x = 0;
+  for (int64_t r = 1 + blockIdx.x * int64_t(blockDim.x) + threadIdx.x; r < R; r += int64_t(gridDim.x) * blockDim.x) {
+    const unsigned long long f = min(fb[r], fcap);
+    a += f;
+    x += f * (unsigned long long)W[r];
+  }
+  for (int o = 16; o; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    x += __shfl_xor_sync(0xffffffffu, x, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&out[0], a);
+    atomicAdd(&out[1], x);
+  }
+}
+
 __global__ void tile_rule_kernel(const int64_t* __restrict__ rule_off, int32_t R, int64_t G, int64_t ntiles,
                                  int32_t* __restrict__ tile_rule) {
   for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t <= ntiles; t += int64_t(gridDim.x) * blockDim.x) {
@@ -390,6 +436,11 @@ int64_t dedup_csr(gt_grammar* g, uint64_t* keys, int64_t n, int hi_bits, int64_t
 
 }  // namespace
 
+void csr_offsets_hi(const uint64_t* keys, int64_t n, int64_t nh, int64_t* off, cudaStream_t s) {
+  csr_offsets_kernel<<<grid_for(nh + 1, 256, 4096), 256, 0, s>>>(keys, n, nh, off);
+  GT_LAUNCH_CHECK();
+}
+
 void load_build_dag(gt_grammar* g, cudaStream_t s) {
   gt_ctx* ctx = g->ctx;
   DevGrammar& d = g->d;
@@ -438,11 +489,34 @@ void load_build_dag(gt_grammar* g, cudaStream_t s) {
   int64_t* redge_off;
   int32_t* redge_child;
   uint32_t* redge_mult;
+  uint64_t* rukeys = nullptr;
   d.ER = dedup_csr(g, rkeys.as<uint64_t>(), nref_root, bits_for(F), F, &redge_off, &redge_child, &redge_mult,
-                   nullptr, s);
+                   &rukeys, s);
   d.redge_off = redge_off;
   d.redge_child = redge_child;
   d.redge_mult = redge_mult;
+  // the same root edges child-major: for each child, the files referencing it
+  {
+    const int64_t ER = d.ER;
+    Buf tk(ctx, size_t(ER) * 8, s), tks(ctx, size_t(ER) * 8, s), mv(ctx, size_t(ER) * 4, s);
+    Buf rs(ctx, radix_scratch_bytes(ER, true, 4), s);
+    uint32_t* fm = dalloc<uint32_t>(g, size_t(ER), s);
+    int32_t* ff = dalloc<int32_t>(g, size_t(ER), s);
+    int64_t* fo = dalloc<int64_t>(g, size_t(R) + 1, s);
+    if (ER > 0) {
+      transpose_keys_kernel<<<grid_for(ER, threads, cap), threads, 0, s>>>(rukeys, ER, tk.as<uint64_t>());
+      GT_LAUNCH_CHECK();
+      GT_CUDA(cudaMemcpyAsync(mv.p, redge_mult, size_t(ER) * 4, cudaMemcpyDeviceToDevice, s));
+      radix_sort_u64(tk.as<uint64_t>(), tks.as<uint64_t>(), mv.p, fm, 4, ER, 0, 32 + rbits, rs.p, s);
+      low32_kernel<<<grid_for(ER, threads, cap), threads, 0, s>>>(tks.as<uint64_t>(), ER, ff);
+      GT_LAUNCH_CHECK();
+    }
+    csr_offsets_kernel<<<grid_for(int64_t(R) + 1, threads, cap), threads, 0, s>>>(tks.as<uint64_t>(), ER, R, fo);
+    GT_LAUNCH_CHECK();
+    d.rfile_off = fo;
+    d.rfile_f = ff;
+    d.rfile_m = fm;
+  }
 
   // ---- parent lists: transpose the distinct edges, keep multiplicities ----
   {
@@ -605,6 +679,31 @@ void load_build_dag(gt_grammar* g, cudaStream_t s) {
     g->info.num_tokens = int64_t(n);
     g->info.owned_windows = int64_t(hv[0] + hv[5]);
     GT_CUDA(cudaStreamSynchronize(s));
+  }
+
+  // ---- bounds for the per-file (top-down, <= 64 files) buffers ----
+  {
+    const unsigned long long fcap = (unsigned long long)std::min(F, 64);
+    Buf fb(ctx, size_t(R) * 8, s);
+    auto* FB = fb.as<unsigned long long>();
+    fbound_init_kernel<<<grid_for(R, threads, cap), threads, 0, s>>>(d.rfile_off, R, FB);
+    GT_LAUNCH_CHECK();
+    for (int32_t lv = 2; lv < d.depth; ++lv) {
+      const int64_t a = g->ledge_off[lv], b = g->ledge_off[lv + 1];
+      if (b > a) {
+        fbound_edges_kernel<<<grid_for(b - a, threads, cap), threads, 0, s>>>(d.ledge_child, d.ledge_par, a, b, fcap,
+                                                                               FB);
+        GT_LAUNCH_CHECK();
+      }
+    }
+    GT_CUDA(cudaMemsetAsync(ctr + 12, 0, 16, s));
+    fbound_sum_kernel<<<grid_for(R, threads, cap), threads, 0, s>>>(FB, d.nwords, R, fcap, ctr + 12);
+    GT_LAUNCH_CHECK();
+    unsigned long long hb[2];
+    GT_CUDA(cudaMemcpyAsync(hb, ctr + 12, 16, cudaMemcpyDeviceToHost, s));
+    GT_CUDA(cudaStreamSynchronize(s));
+    g->fentry_bound = int64_t(hb[0]);
+    g->fword_bound = int64_t(hb[1]);
   }
 
   // ---- tiles ----
