@@ -142,6 +142,24 @@ gt_status gt_inverted_index(gt_grammar* g, void* stream, gt_result** out);
  * Same strategy and file limit as gt_inverted_index. */
 gt_status gt_term_vector(gt_grammar* g, int top_k, void* stream, gt_result** out);
 
+/* Sequence count for l = 3 (Section IV-D): every window of three consecutive
+ * words inside one file (windows never cross a file boundary), keyed as
+ * key = w1 << 42 | w2 << 21 | w3 (requires num_words <= 2^21).
+ * per_file == 0: fields "key" uint64[n], "count" uint64[n], ascending key.
+ * per_file == 1: fields "file" int32[n], "key" uint64[n], "count" uint64[n],
+ *                ascending (file, key); top-down file weights, <= 64 files.
+ * Each window is counted once, by the lowest rule whose body it crosses, with
+ * that rule's weight; the windows a rule owns are built from its body, a
+ * two-symbol look-ahead and its children's head/tail buffers. */
+gt_status gt_sequence_count(gt_grammar* g, int per_file, void* stream, gt_result** out);
+
+/* Ranked inverted index.  n == 3: keys are 3-word windows as in
+ * gt_sequence_count; n == 1: keys are words.  For each key (ascending), the
+ * files containing it with the in-file count, by descending count then
+ * ascending file.  Fields: "offsets" int64[nkeys+1], "key" uint64[nkeys],
+ * "file" int32[m], "count" uint64[m].  Top-down file weights, <= 64 files. */
+gt_status gt_ranked_index(gt_grammar* g, int n, void* stream, gt_result** out);
+
 /* Head and tail buffers (Section IV-C): for every rule, the first two and
  * the last two words of its expansion (word IDs; -1 pads a rule whose
  * expansion has a single word).  d_head, d_tail: device int32[2*num_rules]. */

@@ -233,6 +233,28 @@ def make_corpus(name: str, seed: int | None = None, scale: float = 1.0) -> Corpu
             files.append(inject(rng, base, pieces))
         toks = np.concatenate(files).astype(np.int32)
         lens = np.array([f.shape[0] for f in files], np.int64)
+    elif kind == "nested":
+        # passages of passages: level 0 phrases of Zipf words, level d items
+        # are concatenations of `fanout` level d-1 items; pieces from every
+        # level are injected until `inject_frac` of the tokens
+        N = max(int(spec["N"] * scale), 1000)
+        levels = [[zipf_tokens(rng, spec["phrase_len"], cdf, perm) for _ in range(spec["phrases"])]]
+        for _ in range(spec["depth"]):
+            prev = levels[-1]
+            levels.append([np.concatenate([prev[i] for i in rng.integers(0, len(prev), size=spec["fanout"])])
+                           for _ in range(spec["pool"])])
+        want = int(N * spec["inject_frac"])
+        pieces, got = [], 0
+        while got < want:
+            lv = int(rng.integers(1, spec["depth"] + 1))
+            p = levels[lv][int(rng.integers(0, len(levels[lv])))]
+            if got + p.shape[0] > want and pieces:
+                break
+            pieces.append(p)
+            got += p.shape[0]
+        base = zipf_tokens(rng, max(N - got, 0), cdf, perm)
+        toks = inject(rng, base, pieces)
+        lens = np.array([toks.shape[0]], np.int64)
     else:
         raise ValueError(f"unknown corpus kind {kind}")
     meta = {"name": name, "seed": int(seed), "scale": scale, "V": V, "s": s, "N": int(toks.shape[0]),
@@ -247,6 +269,9 @@ CONFIGS = {
                            passages=50, passage_len=200, copies=4),
     "multi64_50m": dict(kind="files_passages", seed=20210614, N=50_000_000, F=64, len_range=(10_000, 2_000_000),
                         V=500_000, s=1.0, passages=500, passage_len=200, passage_frac=0.05),
+    # one large file with nested repeats (like dataset E): a deep rule DAG
+    "nested_500m": dict(kind="nested", seed=20210615, N=500_000_000, V=1_000_000, s=1.05, phrases=4096,
+                        phrase_len=16, depth=6, fanout=4, pool=256, inject_frac=0.5),
 }
 
 

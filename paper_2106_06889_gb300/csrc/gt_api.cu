@@ -382,6 +382,24 @@ GT_API gt_status gt_term_vector(gt_grammar* g, int top_k, void* stream, gt_resul
   });
 }
 
+GT_API gt_status gt_sequence_count(gt_grammar* g, int per_file, void* stream, gt_result** out) {
+  if (!g || !out || (per_file != 0 && per_file != 1)) return GT_EINVAL;
+  *out = nullptr;
+  return guard(g->ctx, [&] {
+    use_device(g->ctx);
+    *out = gt::run_sequence_count(g, per_file, as_stream(stream));
+  });
+}
+
+GT_API gt_status gt_ranked_index(gt_grammar* g, int n, void* stream, gt_result** out) {
+  if (!g || !out || (n != 1 && n != 3)) return GT_EINVAL;
+  *out = nullptr;
+  return guard(g->ctx, [&] {
+    use_device(g->ctx);
+    *out = n == 3 ? gt::run_ranked_windows(g, as_stream(stream)) : gt::run_ranked_words(g, as_stream(stream));
+  });
+}
+
 GT_API gt_status gt_inverted_index(gt_grammar* g, void* stream, gt_result** out) {
   if (!g || !out) return GT_EINVAL;
   *out = nullptr;

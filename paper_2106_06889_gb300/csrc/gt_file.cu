@@ -470,7 +470,9 @@ int bits_for(int64_t x) {
 // Steps 1-5: the dense (file, bucket) pieces, their sizes and the II bits.
 // Nothing here waits for the GPU: buffers are sized by bounds computed when
 // the grammar was loaded, and sorts run over padded, bound-sized arrays.
-void file_hist(gt_grammar* g, cudaStream_t s, FileHist& fh) {
+}  // namespace
+
+void file_weights(gt_grammar* g, cudaStream_t s, FileWeights& fw) {
   gt_ctx* ctx = g->ctx;
   const DevGrammar& d = g->d;
   const int threads = 256, cap = ctx->num_sms * 16;
@@ -478,13 +480,12 @@ void file_hist(gt_grammar* g, cudaStream_t s, FileHist& fh) {
   if (F > 64) fail(GT_EOVERFLOW, "per-file analytics use the top-down strategy, limited to 64 files");
   if (d.N >= (uint64_t(1) << 32)) fail(GT_EOVERFLOW, "per-file analytics need fewer than 2^32 tokens per grammar");
   if (V > (1 << 21)) fail(GT_EOVERFLOW, "per-file analytics support num_words <= 2^21");
-  const int64_t EB = g->fentry_bound, XB = g->fword_bound;
-  Phase ph(ctx, "file_weights", s);
-  Buf mask(ctx, size_t(R) * 8, s), cnt(ctx, size_t(R) * 8, s), off(ctx, size_t(R) * 8, s);
-  Buf sc(ctx, scan_scratch_bytes(R), s), dev(ctx, 8 * 8, s);
-  int64_t* nnz_d = dev.as<int64_t>();      // (rule, file) pairs
-  int64_t* nx_d = dev.as<int64_t>() + 1;   // emitted rule words
-  auto* M = mask.as<unsigned long long>();
+  const int64_t EB = g->fentry_bound;
+  fw.mask = Buf(ctx, size_t(R) * 8, s);
+  fw.off = Buf(ctx, size_t(R) * 8, s);
+  fw.nnz = Buf(ctx, 8, s);
+  Buf cnt(ctx, size_t(R) * 8, s), sc(ctx, scan_scratch_bytes(R), s);
+  auto* M = fw.mask.as<unsigned long long>();
   fmask_root_kernel<<<grid_for(R, threads, cap), threads, 0, s>>>(d.rfile_off, d.rfile_f, R, M);
   GT_LAUNCH_CHECK();
   for (int lv = 2; lv < d.depth; ++lv) {
@@ -496,22 +497,41 @@ void file_hist(gt_grammar* g, cudaStream_t s, FileHist& fh) {
   }
   popc_kernel<<<grid_for(R, threads, cap), threads, 0, s>>>(M, R, cnt.as<int64_t>());
   GT_LAUNCH_CHECK();
-  exclusive_scan_i64(cnt.as<int64_t>(), off.as<int64_t>(), R, sc.p, s);
-  last_total_kernel<<<1, 1, 0, s>>>(off.as<int64_t>(), cnt.as<int64_t>(), R, nnz_d, nullptr);
+  exclusive_scan_i64(cnt.as<int64_t>(), fw.off.as<int64_t>(), R, sc.p, s);
+  last_total_kernel<<<1, 1, 0, s>>>(fw.off.as<int64_t>(), cnt.as<int64_t>(), R, fw.nnz.as<int64_t>(), nullptr);
   GT_LAUNCH_CHECK();
-  Buf w(ctx, size_t(EB) * 4, s);
-  if (EB > 0) GT_CUDA(cudaMemsetAsync(w.p, 0, size_t(EB) * 4, s));
+  fw.w = Buf(ctx, size_t(EB) * 4, s);
+  if (EB > 0) GT_CUDA(cudaMemsetAsync(fw.w.p, 0, size_t(EB) * 4, s));
   fweight_root_kernel<<<grid_for(R, threads, cap), threads, 0, s>>>(d.rfile_off, d.rfile_f, d.rfile_m, R,
-                                                                     off.as<int64_t>(), M, w.as<uint32_t>());
+                                                                     fw.off.as<int64_t>(), M, fw.w.as<uint32_t>());
   GT_LAUNCH_CHECK();
   for (int lv = 2; lv < d.depth; ++lv) {
     const int64_t a = g->ledge_off[lv], b = g->ledge_off[lv + 1];
     if (b > a) {
       fweight_edges_kernel<<<grid_for(b - a, threads, cap), threads, 0, s>>>(
-          d.ledge_child, d.ledge_par, d.ledge_mult, a, b, off.as<int64_t>(), M, w.as<uint32_t>());
+          d.ledge_child, d.ledge_par, d.ledge_mult, a, b, fw.off.as<int64_t>(), M, fw.w.as<uint32_t>());
       GT_LAUNCH_CHECK();
     }
   }
+}
+
+namespace {
+
+void file_hist(gt_grammar* g, cudaStream_t s, FileHist& fh) {
+  gt_ctx* ctx = g->ctx;
+  const DevGrammar& d = g->d;
+  const int threads = 256, cap = ctx->num_sms * 16;
+  const int32_t R = d.R, F = d.F, V = d.V;
+  const int64_t EB = g->fentry_bound, XB = g->fword_bound;
+  Phase ph(ctx, "file_weights", s);
+  FileWeights fwt;
+  file_weights(g, s, fwt);
+  auto* M = fwt.mask.as<unsigned long long>();
+  Buf dev(ctx, 8, s);
+  int64_t* nnz_d = fwt.nnz.as<int64_t>();
+  int64_t* nx_d = dev.as<int64_t>();  // emitted rule words
+  Buf& off = fwt.off;
+  Buf& w = fwt.w;
   // ---- rule words per file (file-major) ----
   Buf keys(ctx, size_t(EB) * 8, s), skeys(ctx, size_t(EB) * 8, s), swt(ctx, size_t(EB) * 4, s);
   Buf rs(ctx, radix_scratch_bytes(EB, true, 4), s);
@@ -672,7 +692,45 @@ gt_result* inverted_index_from(gt_grammar* g, FileHist& fh, cudaStream_t s) {
   return rb.finish();
 }
 
+__global__ void tv_rows_kernel(const int32_t* __restrict__ word, const int64_t* __restrict__ tv_off, int32_t F,
+                               int64_t bound, uint64_t* __restrict__ rkey, int32_t* __restrict__ rfile) {
+  const int64_t n = tv_off[F];
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < bound && i < n;
+       i += int64_t(gridDim.x) * blockDim.x) {
+    int32_t lo = 0, hi = F;  // file of row i: last f with tv_off[f] <= i
+    while (hi - lo > 1) {
+      const int32_t mid = (lo + hi) >> 1;
+      if (tv_off[mid] <= i) lo = mid;
+      else hi = mid;
+    }
+    rkey[i] = uint64_t(uint32_t(word[i]));
+    rfile[i] = lo;
+  }
+}
+
 }  // namespace
+
+gt_result* run_ranked_words(gt_grammar* g, cudaStream_t s) {
+  gt_ctx* ctx = g->ctx;
+  const DevGrammar& d = g->d;
+  const int threads = 256, cap = ctx->num_sms * 16;
+  FileHist fh;
+  file_hist(g, s, fh);
+  const int64_t pieces = int64_t(d.F) * fh.nb, bound = fh.bound;
+  TvSlots ts{fh.slot_word.as<int32_t>(), fh.slot_cnt.as<uint32_t>(), fh.nnz.as<int64_t>(), fh.bits.as<uint32_t>()};
+  Buf tw(ctx, size_t(bound) * 4, s), tc(ctx, size_t(bound) * 8, s), toff(ctx, size_t(d.F + 1) * 8, s);
+  Buf rkey(ctx, size_t(bound) * 8, s), rfile(ctx, size_t(bound) * 4, s);
+  tv_gather_kernel<<<unsigned(pieces), 256, 0, s>>>(ts, fh.off.as<int64_t>(), tw.as<int32_t>(), tc.as<uint64_t>());
+  GT_LAUNCH_CHECK();
+  tv_file_off_kernel<<<1, 256, 0, s>>>(fh.off.as<int64_t>(), fh.nb, d.F, fh.total.as<int64_t>(), toff.as<int64_t>());
+  GT_LAUNCH_CHECK();
+  if (bound > 0) {
+    tv_rows_kernel<<<grid_for(bound, threads, cap), threads, 0, s>>>(tw.as<int32_t>(), toff.as<int64_t>(), d.F, bound,
+                                                                      rkey.as<uint64_t>(), rfile.as<int32_t>());
+    GT_LAUNCH_CHECK();
+  }
+  return ranked_from_rows(ctx, rkey, rfile, tc, fh.total.as<int64_t>(), bound, 0, false, uint64_t(d.V), s);
+}
 
 void run_file_batch(gt_grammar* g, const int* tv_topk, int n_tv, gt_result** tv_out, gt_result** ii_out,
                     cudaStream_t s) {

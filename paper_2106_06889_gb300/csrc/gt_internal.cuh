@@ -176,6 +176,7 @@ struct gt_grammar {
   int64_t root_chunks = 0;        // host copy of *rch_count
   int64_t fentry_bound = 0;       // bound on (rule, file) pairs with a nonzero per-file weight
   int64_t fword_bound = 0;        // bound on rule words emitted once per such pair
+  int64_t fsym_bound = 0;         // bound on rule body symbols visited once per such pair
   std::vector<void*> owned;      // device allocations to free with the grammar
 };
 
@@ -329,8 +330,27 @@ void run_rule_weights(gt_grammar* g, uint64_t* d_wt, cudaStream_t s);
 void run_word_count(gt_grammar* g, const uint64_t* d_wt, uint64_t* d_counts, cudaStream_t s);
 void run_head_tail(gt_grammar* g, int32_t* d_head, int32_t* d_tail, cudaStream_t s);
 
+// gt_seq.cu: sequence count (l = 3) and ranked inverted index
+gt_result* run_sequence_count(gt_grammar* g, int per_file, cudaStream_t s);
+gt_result* run_ranked_windows(gt_grammar* g, cudaStream_t s);
+// rows (key, file, count) -> ranked index; keys are compact 3-word keys
+// (windows = true, kb bits per word) or word ids (windows = false)
+gt_result* ranked_from_rows(gt_ctx* ctx, Buf& rkey, Buf& rfile, Buf& rcnt, const int64_t* n_dev, int64_t bound,
+                            int kb, bool windows, uint64_t key_pad, cudaStream_t s);
+// gt_file.cu: ranked index over words (rows from the term vector)
+gt_result* run_ranked_words(gt_grammar* g, cudaStream_t s);
+
 // gt_file.cu: per-file analytics (top-down strategy, up to 64 files)
 gt_result* run_term_vector(gt_grammar* g, int top_k, cudaStream_t s);
+// Top-down per-file weights (<= 64 files): rule r's files are the set bits of
+// mask[r]; its weight in its k-th file (ascending) is w[off[r] + k].
+struct FileWeights {
+  Buf mask;  // uint64 [R]
+  Buf off;   // int64  [R]
+  Buf w;     // uint32 [bound]
+  Buf nnz;   // int64: number of (rule, file) pairs
+};
+void file_weights(gt_grammar* g, cudaStream_t s, FileWeights& fw);
 // One shared traversal for several per-file queries on one grammar: n_tv term
 // vectors (top_k each) and, if ii_out is set, the inverted index.
 void run_file_batch(gt_grammar* g, const int* tv_topk, int n_tv, gt_result** tv_out, gt_result** ii_out,

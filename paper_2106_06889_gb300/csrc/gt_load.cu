@@ -348,21 +348,25 @@ __global__ void fbound_edges_kernel(const int32_t* __restrict__ lchild, const in
   }
 }
 
-__global__ void fbound_sum_kernel(const unsigned long long* __restrict__ fb, const int32_t* __restrict__ W, int32_t R,
-                                  unsigned long long fcap, unsigned long long* __restrict__ out) {
-  unsigned long long a = 0, x = 0;
+__global__ void fbound_sum_kernel(const unsigned long long* __restrict__ fb, const int32_t* __restrict__ W,
+                                  const int32_t* __restrict__ S, int32_t R, unsigned long long fcap,
+                                  unsigned long long* __restrict__ out) {
+  unsigned long long a = 0, x = 0, y = 0;
   for (int64_t r = 1 + blockIdx.x * int64_t(blockDim.x) + threadIdx.x; r < R; r += int64_t(gridDim.x) * blockDim.x) {
     const unsigned long long f = min(fb[r], fcap);
     a += f;
     x += f * (unsigned long long)W[r];
+    y += f * (unsigned long long)(W[r] + S[r]);
   }
   for (int o = 16; o; o >>= 1) {
     a += __shfl_xor_sync(0xffffffffu, a, o);
     x += __shfl_xor_sync(0xffffffffu, x, o);
+    y += __shfl_xor_sync(0xffffffffu, y, o);
   }
   if ((threadIdx.x & 31) == 0) {
     atomicAdd(&out[0], a);
     atomicAdd(&out[1], x);
+    atomicAdd(&out[2], y);
   }
 }
 
@@ -696,14 +700,15 @@ void load_build_dag(gt_grammar* g, cudaStream_t s) {
         GT_LAUNCH_CHECK();
       }
     }
-    GT_CUDA(cudaMemsetAsync(ctr + 12, 0, 16, s));
-    fbound_sum_kernel<<<grid_for(R, threads, cap), threads, 0, s>>>(FB, d.nwords, R, fcap, ctr + 12);
+    GT_CUDA(cudaMemsetAsync(ctr + 12, 0, 24, s));
+    fbound_sum_kernel<<<grid_for(R, threads, cap), threads, 0, s>>>(FB, d.nwords, d.nrefs, R, fcap, ctr + 12);
     GT_LAUNCH_CHECK();
-    unsigned long long hb[2];
-    GT_CUDA(cudaMemcpyAsync(hb, ctr + 12, 16, cudaMemcpyDeviceToHost, s));
+    unsigned long long hb[3];
+    GT_CUDA(cudaMemcpyAsync(hb, ctr + 12, 24, cudaMemcpyDeviceToHost, s));
     GT_CUDA(cudaStreamSynchronize(s));
     g->fentry_bound = int64_t(hb[0]);
     g->fword_bound = int64_t(hb[1]);
+    g->fsym_bound = int64_t(hb[2]);
   }
 
   // ---- tiles ----

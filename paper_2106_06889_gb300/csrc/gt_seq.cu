@@ -1,0 +1,500 @@
+// Sequence count (l = 3) and the ranked inverted index (Section IV-C/D).
+//
+// Every 3-word window of a file lies inside the expansion of exactly one
+// lowest rule occurrence: the rule whose body it crosses (it touches two or
+// more body symbols).  That rule "owns" the window, and the window occurs as
+// many times as the rule does (its top-down weight).  So instead of the
+// paper's two traversal phases with retry-on-unready relaunches, the engine
+//   1. builds the head/tail buffers bottom-up (first and last two words of
+//      every rule's expansion);
+//   2. enumerates, for every body position j, the windows that start in
+//      symbol j and leave it: a word starts one window, a child rule with two
+//      or more words starts two (at its last two words).  Their words come from
+//      the symbol, the next two body symbols (look-ahead that stops at the end
+//      of the rule, or of the file in the root) and children's head/tail
+//      buffers - the boundary fix-up between rule pieces;
+//   3. weights each window by its rule's weight (global counts) or by the
+//      rule's per-file weights (per-file counts);
+//   4. canonicalises: radix sort by key, then a segmented sum per key.
+// For rule r this yields W_r + 2 S_r - 2 windows when all children expand to
+// two or more words - Eq. 1's bound with l = 3, which is then exact.
+#include <algorithm>
+
+#include "gt_device.cuh"
+
+namespace gt {
+namespace {
+
+struct Sym3 {
+  int32_t first, second, second_last, last;  // -1 where the expansion is too short
+};
+
+__device__ __forceinline__ Sym3 sym_words(const DevGrammar& d, const int32_t* __restrict__ head,
+                                          const int32_t* __restrict__ tail, int32_t x) {
+  Sym3 r;
+  if (x < d.V) {
+    r.first = r.last = x;
+    r.second = r.second_last = -1;
+  } else {
+    const int32_t c = x - d.V;
+    r.first = head[2 * c];
+    r.second = head[2 * c + 1];
+    r.second_last = tail[2 * c];
+    r.last = tail[2 * c + 1];
+  }
+  return r;
+}
+
+__device__ __forceinline__ uint64_t pack_compact(int32_t a, int32_t b, int32_t c, int kb) {
+  return (uint64_t(uint32_t(a)) << (2 * kb)) | (uint64_t(uint32_t(b)) << kb) | uint64_t(uint32_t(c));
+}
+
+// End (exclusive) of the body sequence holding position j: the file's end in
+// the root, the rule's end elsewhere.  Also returns the rule.
+__device__ __forceinline__ int64_t seq_end(const DevGrammar& d, int64_t j, int32_t* rule, int32_t* file) {
+  if (j < d.root_len) {
+    const int64_t f = upper_bound_dev(d.file_off, int64_t(d.F) + 1, j) - 1;
+    *rule = 0;
+    *file = int32_t(f);
+    return d.file_off[f + 1];
+  }
+  const int32_t r = d.sym_rule[j - d.first_rule_tile * kTile];
+  *rule = r;
+  *file = -1;
+  return d.rule_off[r + 1];
+}
+
+// The (at most two) owned windows starting in body symbol j; returns how many.
+__device__ __forceinline__ int windows_at(const DevGrammar& d, const int32_t* __restrict__ head,
+                                          const int32_t* __restrict__ tail, int64_t j, int64_t end, int kb,
+                                          uint64_t* k) {
+  if (j + 1 >= end) return 0;
+  const Sym3 a = sym_words(d, head, tail, d.sym[j]);
+  const Sym3 b = sym_words(d, head, tail, d.sym[j + 1]);
+  const int32_t n1 = b.first;
+  int32_t n2 = b.second;
+  if (n2 < 0) n2 = j + 2 < end ? sym_words(d, head, tail, d.sym[j + 2]).first : -1;
+  int n = 0;
+  if (a.second_last >= 0) k[n++] = pack_compact(a.second_last, a.last, n1, kb);  // child with >= 2 words
+  if (n2 >= 0) k[n++] = pack_compact(a.last, n1, n2, kb);
+  return n;
+}
+
+// Global counts: two key slots per body position (kNoKey where unused),
+// weighted by the rule's top-down weight.
+__global__ void win_emit_kernel(DevGrammar d, const int32_t* __restrict__ head, const int32_t* __restrict__ tail,
+                                const uint64_t* __restrict__ wt, int kb, uint64_t key_pad,
+                                uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+  for (int64_t j = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; j < d.G; j += int64_t(gridDim.x) * blockDim.x) {
+    int32_t r, f;
+    const int64_t end = seq_end(d, j, &r, &f);
+    uint64_t k[2];
+    const int n = windows_at(d, head, tail, j, end, kb, k);
+    const uint32_t w = uint32_t(wt[r]);  // 0 for a rule nothing references: no rows
+    keys[2 * j] = (n > 0 && w) ? k[0] : key_pad;
+    keys[2 * j + 1] = (n > 1 && w) ? k[1] : key_pad;
+    vals[2 * j] = w;
+    vals[2 * j + 1] = w;
+  }
+}
+
+// Per-file counts, pass 1: entries produced at each position (windows x files).
+__global__ void win_count_file_kernel(DevGrammar d, const int32_t* __restrict__ head,
+                                      const int32_t* __restrict__ tail, const unsigned long long* __restrict__ mask,
+                                      int kb, int64_t* __restrict__ cnt) {
+  for (int64_t j = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; j < d.G; j += int64_t(gridDim.x) * blockDim.x) {
+    int32_t r, f;
+    const int64_t end = seq_end(d, j, &r, &f);
+    uint64_t k[2];
+    const int n = windows_at(d, head, tail, j, end, kb, k);
+    cnt[j] = r == 0 ? n : n * __popcll(mask[r]);
+  }
+}
+
+// Pass 2: write (file << 32 | slot) and the key of every entry.
+__global__ void win_emit_file_kernel(DevGrammar d, const int32_t* __restrict__ head, const int32_t* __restrict__ tail,
+                                     const unsigned long long* __restrict__ mask, const int64_t* __restrict__ woff,
+                                     const uint32_t* __restrict__ fw, int kb, const int64_t* __restrict__ pos,
+                                     uint64_t* __restrict__ keys, uint64_t* __restrict__ fkeys,
+                                     uint32_t* __restrict__ vals) {
+  for (int64_t j = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; j < d.G; j += int64_t(gridDim.x) * blockDim.x) {
+    int32_t r, f;
+    const int64_t end = seq_end(d, j, &r, &f);
+    uint64_t k[2];
+    const int n = windows_at(d, head, tail, j, end, kb, k);
+    if (n == 0) continue;
+    int64_t o = pos[j];
+    if (r == 0) {
+      for (int i = 0; i < n; ++i, ++o) {
+        keys[o] = k[i];
+        fkeys[o] = uint64_t(uint32_t(f));
+        vals[o] = 1u;
+      }
+    } else {
+      unsigned long long m = mask[r];
+      int64_t slot = woff[r];
+      while (m) {
+        const int ff = __ffsll(m) - 1;
+        m &= m - 1;
+        const uint32_t w = fw[slot++];
+        for (int i = 0; i < n; ++i, ++o) {
+          keys[o] = k[i];
+          fkeys[o] = uint64_t(uint32_t(ff));
+          vals[o] = w;
+        }
+      }
+    }
+  }
+}
+
+__global__ void pad_tail_kernel(uint64_t* __restrict__ keys, uint64_t* __restrict__ fkeys,
+                                uint32_t* __restrict__ vals, const int64_t* __restrict__ n_dev, int64_t bound,
+                                uint64_t key_pad, uint64_t file_pad) {
+  const int64_t n = *n_dev;
+  for (int64_t i = n + blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < bound; i += int64_t(gridDim.x) * blockDim.x) {
+    keys[i] = key_pad;
+    if (fkeys) fkeys[i] = file_pad;
+    if (vals) vals[i] = 0;
+  }
+}
+
+__global__ void gather_u64_kernel(const uint64_t* __restrict__ src, const uint32_t* __restrict__ idx, int64_t n,
+                                  uint64_t* __restrict__ dst) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    dst[i] = src[idx[i]];
+}
+
+__global__ void gather_u32_kernel(const uint32_t* __restrict__ src, const uint32_t* __restrict__ idx, int64_t n,
+                                  uint32_t* __restrict__ dst) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    dst[i] = src[idx[i]];
+}
+
+__global__ void iota_kernel(uint32_t* __restrict__ a, int64_t n) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    a[i] = uint32_t(i);
+}
+
+// Run heads of the sorted (file, key) sequence; entries whose key is the pad
+// (kNoKey-derived) are not heads.
+__global__ void run_heads_kernel(const uint64_t* __restrict__ keys, const uint64_t* __restrict__ fkeys, int64_t n,
+                                 uint64_t key_pad, int64_t* __restrict__ flag, int64_t* __restrict__ v64,
+                                 const uint32_t* __restrict__ vals) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    const bool real = keys[i] != key_pad;
+    const bool head = real && (i == 0 || keys[i] != keys[i - 1] || (fkeys && fkeys[i] != fkeys[i - 1]));
+    flag[i] = head;
+    v64[i] = real ? int64_t(vals[i]) : 0;
+  }
+}
+
+// compact key (kb bits per word) -> w1 << 42 | w2 << 21 | w3; kb == 0 keeps it
+__device__ __forceinline__ uint64_t to_output_key(uint64_t k, int kb) {
+  if (kb == 0) return k;
+  const uint64_t m = (uint64_t(1) << kb) - 1;
+  return ((k >> (2 * kb)) << 42) | (((k >> kb) & m) << 21) | (k & m);
+}
+
+// One output row per run: key (21-bit fields), file, summed count.
+__global__ void run_write_kernel(const uint64_t* __restrict__ keys, const uint64_t* __restrict__ fkeys, int64_t n,
+                                 const int64_t* __restrict__ flag, const int64_t* __restrict__ pos,
+                                 const int64_t* __restrict__ wsum, const int64_t* __restrict__ v64, int kb,
+                                 int64_t* __restrict__ run_start, uint64_t* __restrict__ out_key,
+                                 int32_t* __restrict__ out_file) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    if (flag[i]) {
+      const int64_t u = pos[i];
+      out_key[u] = to_output_key(keys[i], kb);
+      if (out_file) out_file[u] = int32_t(fkeys[i]);
+      run_start[u] = i;
+    }
+}
+
+__global__ void run_sum_kernel(const int64_t* __restrict__ run_start, const int64_t* __restrict__ nruns_d,
+                               const int64_t* __restrict__ wsum, const int64_t* __restrict__ v64, int64_t n,
+                               uint64_t* __restrict__ out_count) {
+  const int64_t nr = *nruns_d;
+  for (int64_t u = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; u < nr; u += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t a = run_start[u];
+    int64_t b;
+    if (u + 1 < nr) b = run_start[u + 1];
+    else b = n;  // past the last run only pads follow, and they add 0
+    const int64_t end_sum = b < n ? wsum[b] : wsum[n - 1] + v64[n - 1];
+    out_count[u] = uint64_t(end_sum - wsum[a]);
+  }
+}
+
+__global__ void last_total2_kernel(const int64_t* __restrict__ ex, const int64_t* __restrict__ cnt, int64_t n,
+                                   int64_t* __restrict__ out, int64_t* __restrict__ out2) {
+  const int64_t t = n > 0 ? ex[n - 1] + cnt[n - 1] : 0;
+  *out = t;
+  if (out2) *out2 = t;
+}
+
+int bits_for(int64_t x) {
+  int b = 1;
+  while ((int64_t(1) << b) <= x) ++b;
+  return b;
+}
+
+// Sorted rows -> result (key, [file], count); nrows_slot receives the row count.
+void reduce_rows(gt_ctx* ctx, uint64_t* keys, uint64_t* fkeys, uint32_t* vals, int64_t n, int kb, uint64_t key_pad,
+                 uint64_t* out_key, int32_t* out_file, uint64_t* out_count, int64_t* nrows_slot, cudaStream_t s,
+                 bool output_keys = true) {
+  const int threads = 256, cap = ctx->num_sms * 16;
+  Buf flag(ctx, size_t(n) * 8, s), pos(ctx, size_t(n) * 8, s), v64(ctx, size_t(n) * 8, s), wsum(ctx, size_t(n) * 8, s);
+  Buf sc(ctx, scan_scratch_bytes(n), s), rstart(ctx, size_t(n) * 8, s), nr(ctx, 8, s);
+  if (n == 0) {
+    GT_CUDA(cudaMemsetAsync(nrows_slot, 0, 8, s));
+    return;
+  }
+  run_heads_kernel<<<grid_for(n, threads, cap), threads, 0, s>>>(keys, fkeys, n, key_pad, flag.as<int64_t>(),
+                                                                  v64.as<int64_t>(), vals);
+  GT_LAUNCH_CHECK();
+  exclusive_scan_i64(flag.as<int64_t>(), pos.as<int64_t>(), n, sc.p, s);
+  exclusive_scan_i64(v64.as<int64_t>(), wsum.as<int64_t>(), n, sc.p, s);
+  last_total2_kernel<<<1, 1, 0, s>>>(pos.as<int64_t>(), flag.as<int64_t>(), n, nr.as<int64_t>(), nrows_slot);
+  GT_LAUNCH_CHECK();
+  run_write_kernel<<<grid_for(n, threads, cap), threads, 0, s>>>(keys, fkeys, n, flag.as<int64_t>(), pos.as<int64_t>(),
+                                                                  wsum.as<int64_t>(), v64.as<int64_t>(),
+                                                                  output_keys ? kb : 0, rstart.as<int64_t>(), out_key,
+                                                                  out_file);
+  GT_LAUNCH_CHECK();
+  run_sum_kernel<<<grid_for(n, threads, cap), threads, 0, s>>>(rstart.as<int64_t>(), nr.as<int64_t>(),
+                                                                wsum.as<int64_t>(), v64.as<int64_t>(), n, out_count);
+  GT_LAUNCH_CHECK();
+}
+
+// Windows of the whole corpus, sorted: keys (compact packing), optional file
+// keys, weights.  Returns the number of (padded) rows.
+struct Windows {
+  Buf keys, fkeys, vals;
+  int64_t n = 0;
+  int kb = 1;
+  uint64_t key_pad = 0;
+};
+
+void sorted_windows(gt_grammar* g, bool per_file, cudaStream_t s, Windows& out) {
+  gt_ctx* ctx = g->ctx;
+  const DevGrammar& d = g->d;
+  const int threads = 256, cap = ctx->num_sms * 16;
+  if (d.V > (1 << 21)) fail(GT_EOVERFLOW, "3-word keys need num_words <= 2^21");
+  if (d.N >= (uint64_t(1) << 32)) fail(GT_EOVERFLOW, "sequence count needs fewer than 2^32 tokens per grammar");
+  const int kb = bits_for(d.V > 1 ? d.V - 1 : 1);  // bits per word id
+  out.kb = kb;
+  out.key_pad = uint64_t(1) << (3 * kb);  // above every real key: unused rows sort last
+  const int key_bits = 3 * kb + 1;
+  Buf head(ctx, size_t(d.R) * 8, s), tail(ctx, size_t(d.R) * 8, s);
+  {
+    Phase ph(ctx, "seq_headtail", s);
+    run_head_tail(g, head.as<int32_t>(), tail.as<int32_t>(), s);
+  }
+  if (!per_file) {
+    const int64_t n = 2 * d.G;
+    Buf k0(ctx, size_t(n) * 8, s), v0(ctx, size_t(n) * 4, s);
+    out.keys = Buf(ctx, size_t(n) * 8, s);
+    out.vals = Buf(ctx, size_t(n) * 4, s);
+    out.n = n;
+    if (n == 0) return;
+    {
+      Phase ph(ctx, "seq_emit", s);
+      Buf wt(ctx, size_t(d.R) * 8, s);
+      run_rule_weights(g, wt.as<uint64_t>(), s);
+      win_emit_kernel<<<grid_for(d.G, threads, cap), threads, 0, s>>>(d, head.as<int32_t>(), tail.as<int32_t>(),
+                                                                       wt.as<uint64_t>(), kb, out.key_pad,
+                                                                       k0.as<uint64_t>(), v0.as<uint32_t>());
+      GT_LAUNCH_CHECK();
+    }
+    Phase ph(ctx, "seq_sort", s);
+    Buf rs(ctx, radix_scratch_bytes(n, true, 4), s);
+    radix_sort_u64(k0.as<uint64_t>(), out.keys.as<uint64_t>(), v0.p, out.vals.p, 4, n, 0, key_bits, rs.p, s);
+    return;
+  }
+  // ---- per file: count, scan, emit (windows x files of the rule) ----
+  Phase ph(ctx, "seq_emit", s);
+  FileWeights fw;
+  file_weights(g, s, fw);
+  const int64_t bound = 2 * d.root_len + 2 * g->fsym_bound;
+  out.n = bound;
+  out.keys = Buf(ctx, size_t(bound) * 8, s);
+  out.fkeys = Buf(ctx, size_t(bound) * 8, s);
+  out.vals = Buf(ctx, size_t(bound) * 4, s);
+  if (bound == 0) return;
+  Buf cnt(ctx, size_t(d.G) * 8, s), pos(ctx, size_t(d.G) * 8, s), sc(ctx, scan_scratch_bytes(d.G), s), nd(ctx, 8, s);
+  GT_CUDA(cudaMemsetAsync(nd.p, 0, 8, s));
+  Buf k0(ctx, size_t(bound) * 8, s), f0(ctx, size_t(bound) * 8, s), v0(ctx, size_t(bound) * 4, s);
+  if (d.G > 0) {
+    win_count_file_kernel<<<grid_for(d.G, threads, cap), threads, 0, s>>>(
+        d, head.as<int32_t>(), tail.as<int32_t>(), fw.mask.as<unsigned long long>(), kb, cnt.as<int64_t>());
+    GT_LAUNCH_CHECK();
+    exclusive_scan_i64(cnt.as<int64_t>(), pos.as<int64_t>(), d.G, sc.p, s);
+    last_total2_kernel<<<1, 1, 0, s>>>(pos.as<int64_t>(), cnt.as<int64_t>(), d.G, nd.as<int64_t>(), nullptr);
+    GT_LAUNCH_CHECK();
+    win_emit_file_kernel<<<grid_for(d.G, threads, cap), threads, 0, s>>>(
+        d, head.as<int32_t>(), tail.as<int32_t>(), fw.mask.as<unsigned long long>(), fw.off.as<int64_t>(),
+        fw.w.as<uint32_t>(), kb, pos.as<int64_t>(), k0.as<uint64_t>(), f0.as<uint64_t>(), v0.as<uint32_t>());
+    GT_LAUNCH_CHECK();
+  }
+  pad_tail_kernel<<<grid_for(bound, threads, cap), threads, 0, s>>>(k0.as<uint64_t>(), f0.as<uint64_t>(),
+                                                                     v0.as<uint32_t>(), nd.as<int64_t>(), bound,
+                                                                     out.key_pad, uint64_t(d.F));
+  GT_LAUNCH_CHECK();
+  // ---- order by (file, key): sort by key, then stably by file ----
+  Phase ph2(ctx, "seq_sort", s);
+  Buf pin(ctx, size_t(bound) * 4, s), pkey(ctx, size_t(bound) * 4, s), pfile(ctx, size_t(bound) * 4, s);
+  Buf k1(ctx, size_t(bound) * 8, s), fk(ctx, size_t(bound) * 8, s), comp(ctx, size_t(bound) * 4, s);
+  Buf rs(ctx, radix_scratch_bytes(bound, true, 4), s);
+  iota_kernel<<<grid_for(bound, threads, cap), threads, 0, s>>>(pin.as<uint32_t>(), bound);
+  GT_LAUNCH_CHECK();
+  radix_sort_u64(k0.as<uint64_t>(), k1.as<uint64_t>(), pin.p, pkey.p, 4, bound, 0, key_bits, rs.p, s);
+  gather_u64_kernel<<<grid_for(bound, threads, cap), threads, 0, s>>>(f0.as<uint64_t>(), pkey.as<uint32_t>(), bound,
+                                                                       fk.as<uint64_t>());
+  GT_LAUNCH_CHECK();
+  iota_kernel<<<grid_for(bound, threads, cap), threads, 0, s>>>(pin.as<uint32_t>(), bound);
+  GT_LAUNCH_CHECK();
+  radix_sort_u64(fk.as<uint64_t>(), out.fkeys.as<uint64_t>(), pin.p, pfile.p, 4, bound, 0, bits_for(d.F), rs.p, s);
+  gather_u64_kernel<<<grid_for(bound, threads, cap), threads, 0, s>>>(k1.as<uint64_t>(), pfile.as<uint32_t>(), bound,
+                                                                       out.keys.as<uint64_t>());
+  GT_LAUNCH_CHECK();
+  gather_u32_kernel<<<grid_for(bound, threads, cap), threads, 0, s>>>(pkey.as<uint32_t>(), pfile.as<uint32_t>(), bound,
+                                                                       comp.as<uint32_t>());
+  GT_LAUNCH_CHECK();
+  gather_u32_kernel<<<grid_for(bound, threads, cap), threads, 0, s>>>(v0.as<uint32_t>(), comp.as<uint32_t>(), bound,
+                                                                       out.vals.as<uint32_t>());
+  GT_LAUNCH_CHECK();
+}
+
+__global__ void rank_keys_kernel(const uint64_t* __restrict__ cnt, const int64_t* __restrict__ n_dev, int64_t bound,
+                                 uint64_t* __restrict__ k, uint32_t* __restrict__ idx) {
+  const int64_t n = *n_dev;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < bound; i += int64_t(gridDim.x) * blockDim.x) {
+    k[i] = i < n ? uint64_t(0xffffffffu - uint32_t(cnt[i])) : 0xffffffffull;
+    idx[i] = uint32_t(i);
+  }
+}
+
+__global__ void key_heads_kernel(const uint64_t* __restrict__ key, const int64_t* __restrict__ n_dev, int64_t bound,
+                                 int64_t* __restrict__ flag) {
+  const int64_t n = *n_dev;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < bound; i += int64_t(gridDim.x) * blockDim.x)
+    flag[i] = (i < n && (i == 0 || key[i] != key[i - 1])) ? 1 : 0;
+}
+
+__global__ void key_offsets_kernel(const uint64_t* __restrict__ key, const int64_t* __restrict__ flag,
+                                   const int64_t* __restrict__ pos, const int64_t* __restrict__ n_dev, int64_t bound,
+                                   int kb, bool windows, int64_t* __restrict__ off, uint64_t* __restrict__ okey,
+                                   int64_t* __restrict__ nkeys, int64_t* __restrict__ nkeys1) {
+  const int64_t n = *n_dev;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < bound; i += int64_t(gridDim.x) * blockDim.x)
+    if (flag[i]) {
+      off[pos[i]] = i;
+      okey[pos[i]] = windows ? to_output_key(key[i], kb) : key[i];
+    }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const int64_t nk = bound > 0 ? pos[bound - 1] + flag[bound - 1] : 0;
+    off[nk] = n;
+    *nkeys = nk;
+    *nkeys1 = nk + 1;
+  }
+}
+
+}  // namespace
+
+// Rows (key, file, count), n_dev of them (bound allocated) -> ranked index:
+// keys ascending; inside a key, count descending then file ascending.
+gt_result* ranked_from_rows(gt_ctx* ctx, Buf& rkey, Buf& rfile, Buf& rcnt, const int64_t* n_dev, int64_t bound,
+                            int kb, bool windows, uint64_t key_pad, cudaStream_t s) {
+  const int threads = 256, cap = ctx->num_sms * 16;
+  ResultBuilder rb(ctx, s);
+  Phase ph(ctx, "ranked", s);
+  auto* off = static_cast<int64_t*>(rb.alloc(size_t(bound + 1) * 8));
+  auto* okey = static_cast<uint64_t*>(rb.alloc(size_t(bound) * 8));
+  auto* ofile = static_cast<int32_t*>(rb.alloc(size_t(bound) * 4));
+  auto* ocnt = static_cast<uint64_t*>(rb.alloc(size_t(bound) * 8));
+  int64_t* len_off = rb.new_len_slot();
+  int64_t* len_key = rb.new_len_slot();
+  int64_t* len_row = rb.new_len_slot();
+  GT_CUDA(cudaMemcpyAsync(len_row, n_dev, 8, cudaMemcpyDeviceToDevice, s));
+  if (bound == 0) {
+    GT_CUDA(cudaMemsetAsync(off, 0, 8, s));
+    GT_CUDA(cudaMemsetAsync(len_key, 0, 8, s));
+    const int64_t one = 1;
+    GT_CUDA(cudaMemcpyAsync(len_off, &one, 8, cudaMemcpyHostToDevice, s));
+  } else {
+    Buf k0(ctx, size_t(bound) * 8, s), k1(ctx, size_t(bound) * 8, s), i0(ctx, size_t(bound) * 4, s);
+    Buf p1(ctx, size_t(bound) * 4, s), p2(ctx, size_t(bound) * 4, s), comp(ctx, size_t(bound) * 4, s);
+    Buf rs(ctx, radix_scratch_bytes(bound, true, 4), s), skey(ctx, size_t(bound) * 8, s);
+    Buf flag(ctx, size_t(bound) * 8, s), pos(ctx, size_t(bound) * 8, s), sc(ctx, scan_scratch_bytes(bound), s);
+    // rows past n_dev must carry the pad key so they sort last
+    pad_tail_kernel<<<grid_for(bound, threads, cap), threads, 0, s>>>(rkey.as<uint64_t>(), nullptr, nullptr, n_dev,
+                                                                       bound, key_pad, 0);
+    GT_LAUNCH_CHECK();
+    rank_keys_kernel<<<grid_for(bound, threads, cap), threads, 0, s>>>(rcnt.as<uint64_t>(), n_dev, bound,
+                                                                        k0.as<uint64_t>(), i0.as<uint32_t>());
+    GT_LAUNCH_CHECK();
+    radix_sort_u64(k0.as<uint64_t>(), k1.as<uint64_t>(), i0.p, p1.p, 4, bound, 0, 32, rs.p, s);
+    gather_u64_kernel<<<grid_for(bound, threads, cap), threads, 0, s>>>(rkey.as<uint64_t>(), p1.as<uint32_t>(), bound,
+                                                                         k0.as<uint64_t>());
+    GT_LAUNCH_CHECK();
+    iota_kernel<<<grid_for(bound, threads, cap), threads, 0, s>>>(i0.as<uint32_t>(), bound);
+    GT_LAUNCH_CHECK();
+    int kbits = 1;
+    while (kbits < 64 && (uint64_t(1) << kbits) <= key_pad) ++kbits;
+    radix_sort_u64(k0.as<uint64_t>(), skey.as<uint64_t>(), i0.p, p2.p, 4, bound, 0, kbits, rs.p, s);
+    gather_u32_kernel<<<grid_for(bound, threads, cap), threads, 0, s>>>(p1.as<uint32_t>(), p2.as<uint32_t>(), bound,
+                                                                         comp.as<uint32_t>());
+    GT_LAUNCH_CHECK();
+    gather_u32_kernel<<<grid_for(bound, threads, cap), threads, 0, s>>>(rfile.as<uint32_t>(), comp.as<uint32_t>(),
+                                                                         bound, reinterpret_cast<uint32_t*>(ofile));
+    GT_LAUNCH_CHECK();
+    gather_u64_kernel<<<grid_for(bound, threads, cap), threads, 0, s>>>(rcnt.as<uint64_t>(), comp.as<uint32_t>(),
+                                                                         bound, ocnt);
+    GT_LAUNCH_CHECK();
+    key_heads_kernel<<<grid_for(bound, threads, cap), threads, 0, s>>>(skey.as<uint64_t>(), n_dev, bound,
+                                                                        flag.as<int64_t>());
+    GT_LAUNCH_CHECK();
+    exclusive_scan_i64(flag.as<int64_t>(), pos.as<int64_t>(), bound, sc.p, s);
+    key_offsets_kernel<<<grid_for(bound, threads, cap), threads, 0, s>>>(
+        skey.as<uint64_t>(), flag.as<int64_t>(), pos.as<int64_t>(), n_dev, bound, kb, windows, off, okey, len_key,
+        len_off);
+    GT_LAUNCH_CHECK();
+  }
+  rb.field_dyn("offsets", off, len_off);
+  rb.field_dyn("key", okey, len_key);
+  rb.field_dyn("file", ofile, len_row);
+  rb.field_dyn("count", ocnt, len_row);
+  GT_CUDA(cudaMemcpyAsync(rb.status(), ctx->d_status, 4, cudaMemcpyDeviceToDevice, s));
+  return rb.finish();
+}
+
+gt_result* run_ranked_windows(gt_grammar* g, cudaStream_t s) {
+  gt_ctx* ctx = g->ctx;
+  Windows w;
+  sorted_windows(g, true, s, w);
+  // per-file 3-gram rows (file, key, count) in (file, key) order
+  Buf rkey(ctx, size_t(w.n) * 8, s), rfile(ctx, size_t(w.n) * 4, s), rcnt(ctx, size_t(w.n) * 8, s), nd(ctx, 8, s);
+  reduce_rows(ctx, w.keys.as<uint64_t>(), w.fkeys.as<uint64_t>(), w.vals.as<uint32_t>(), w.n, w.kb, w.key_pad,
+              rkey.as<uint64_t>(), rfile.as<int32_t>(), rcnt.as<uint64_t>(), nd.as<int64_t>(), s, false);
+  return ranked_from_rows(ctx, rkey, rfile, rcnt, nd.as<int64_t>(), w.n, w.kb, true, w.key_pad, s);
+}
+
+gt_result* run_sequence_count(gt_grammar* g, int per_file, cudaStream_t s) {
+  gt_ctx* ctx = g->ctx;
+  ResultBuilder rb(ctx, s);
+  Windows w;
+  sorted_windows(g, per_file != 0, s, w);
+  Phase ph(ctx, "seq_reduce", s);
+  auto* key = static_cast<uint64_t*>(rb.alloc(size_t(w.n) * 8));
+  auto* count = static_cast<uint64_t*>(rb.alloc(size_t(w.n) * 8));
+  int32_t* file = per_file ? static_cast<int32_t*>(rb.alloc(size_t(w.n) * 4)) : nullptr;
+  int64_t* len = rb.new_len_slot();
+  reduce_rows(ctx, w.keys.as<uint64_t>(), per_file ? w.fkeys.as<uint64_t>() : nullptr, w.vals.as<uint32_t>(), w.n,
+              w.kb, w.key_pad, key, file, count, len, s);
+  if (per_file) rb.field_dyn("file", file, len);
+  rb.field_dyn("key", key, len);
+  rb.field_dyn("count", count, len);
+  GT_CUDA(cudaMemcpyAsync(rb.status(), ctx->d_status, 4, cudaMemcpyDeviceToDevice, s));
+  return rb.finish();
+}
+
+}  // namespace gt
