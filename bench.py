@@ -95,13 +95,26 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def algorithmic_bytes(info: dict) -> dict:
-    """Bytes the word-count traversal must move per query (whole query:
-    4 B per body symbol + 8 B per distinct edge + 8 B per rule weight + 8 B
-    per word count).  The partition kernel's share is the symbol stream,
-    4 B per body symbol; its intermediate buckets are overhead, not counted."""
-    G, R, E, V = info["num_syms"], info["num_rules"], info["num_edges"], info["num_words"]
-    return {"wc_partition": 4 * G, "weights": 8 * E + 16 * R, "total": 4 * G + 8 * E + 8 * R + 8 * V}
+# DRAM bytes (read + write) per launch from one `ncu --set full` capture of the
+# kernel as it stands (see the named profile); None once the kernel changes.
+NCU_TRAFFIC = {
+    "tv_hist_kernel": (211.35e6, "profiles/tv_hist_kernel_multi64_50m.md"),
+    "wc_partition_kernel": (222.57e6, "profiles/wc_partition_kernel_multi64_50m.md"),
+}
+
+
+def algorithmic_bytes(info: dict, tv_entries: int) -> dict:
+    """Bytes each timed kernel must move per launch.
+    wc_partition_kernel: the symbol stream, 4 B per body symbol (its bucketed
+      output is overhead).
+    tv_hist_kernel: its bucket-sorted input, 2 B per root word and 8 B per
+      emitted (word, weight) of a (rule, file) pair, plus 8 B per term-vector
+      entry written, plus 2056 B of bits and size per (file, 2^14-word bucket)."""
+    G, V, F = info["num_syms"], info["num_words"], info["num_files"]
+    pieces = F * ((V + 16383) // 16384)
+    return {"wc_partition": ("wc_partition_kernel", 4 * G),
+            "tv_hist_kernel": ("tv_hist_kernel", 2 * info["root_words"] + 8 * info["file_words"] + 8 * tv_entries
+                               + 2056 * pieces)}
 
 
 def run_step(B, gh, bufs, analytics, stream, keep):
@@ -144,6 +157,7 @@ def main():
     ap.add_argument("--workload", default="multi64_50m", choices=list(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (used for profiling runs)")
+    ap.add_argument("--no-extras", action="store_true", help="skip the secondary sequence-count timing")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -221,6 +235,12 @@ def main():
         torch.cuda.synchronize()
         barrier()
         clk = clocks.stop()
+        tv_entries = 0
+        for r in keep:
+            try:
+                tv_entries = max(tv_entries, B.gt_result_view(r, "count")[1])
+            except B.GtError:
+                pass
         for r in keep:
             B.gt_free_result(r)
         keep.clear()
@@ -236,18 +256,45 @@ def main():
 
     # ---- dominant kernel: live CUDA-event time of its phase ----
     phases = {}
-    for ph in ("weights", "wc_partition", "wc_hist", "sort_canon", "file_weights", "tv_hist", "tv_out", "ii_out"):
+    for ph in ("weights", "wc_partition", "wc_hist", "sort_canon", "file_weights", "tv_hist", "tv_hist_kernel",
+               "tv_out", "ii_out"):
         tot, spans, la = B.gt_profile_read(ctx, ph)
         if spans:
             phases[ph] = {"ms_per_launch": tot / spans, "spans": spans, "launches": la}
     hbm, src = peaks()
-    ab = algorithmic_bytes(info)
-    dom = "wc_partition"
+    ab = algorithmic_bytes(info, tv_entries)
+    # the dominant kernel: the measured one with the largest time per step
+    cands = [(phases[p]["ms_per_launch"] * phases[p]["launches"] / phases[p]["spans"], p)
+             for p in ab if p in phases and phases[p]["launches"] == phases[p]["spans"]]
+    dom = max(cands)[1]
+    kname, abytes = ab[dom]
     dom_ms = phases[dom]["ms_per_launch"]
-    achieved = ab[dom] / (dom_ms / 1e3) / 1e9
-    roofline = {"bound": "hbm", "kernel": "wc_partition_kernel", "achieved": achieved, "peak": hbm,
-                "peak_source": src, "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
-                "algorithmic_bytes_per_launch": ab[dom]}
+    achieved = abytes / (dom_ms / 1e3) / 1e9
+    traffic = NCU_TRAFFIC.get(kname)
+    roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm, "peak_source": src,
+                "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic[0] if traffic else None,
+                "traffic_source": traffic[1] if traffic else None, "algorithmic_bytes_per_launch": abytes,
+                "ms_per_launch": dom_ms}
+
+    # ---- secondary: 3-word sequence count on the same corpus ----
+    extras = {}
+    if not args.no_extras:
+        with torch.cuda.stream(stream):
+            r = B.gt_sequence_count(gh, 0, stream)
+            torch.cuda.synchronize()
+            B.gt_free_result(r)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            n3 = max(2, min(args.steps, 5))
+            e0.record(stream)
+            for _ in range(n3):
+                keep.append(B.gt_sequence_count(gh, 0, stream))
+            e1.record(stream)
+            torch.cuda.synchronize()
+            for r in keep:
+                B.gt_free_result(r)
+            keep.clear()
+        ms3 = e0.elapsed_time(e1) / n3
+        extras["sequence_count"] = {"tokens_per_s": N / (ms3 / 1e3), "ms_per_query": ms3}
 
     # ---- end to end through the public API with host buffers ----
     e2e = None
@@ -307,7 +354,7 @@ def main():
                            "tokens": N, "grammar_symbols": info["num_syms"], "rules": info["num_rules"],
                            "files": info["num_files"], "l2": "inputs larger than L2 (symbol array "
                            f"{4 * info['num_syms'] / 1e6:.0f} MB > 129 MB)"},
-                "roofline": roofline, "phases": phases, "cpu_baseline": cpu, "e2e": e2e,
+                "roofline": roofline, "phases": phases, "extras": extras, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clk}
         print(json.dumps(line))
     B.gt_free_grammar(gh)

@@ -85,6 +85,9 @@ typedef struct {
   int64_t num_tokens;      /* N: length of the fully expanded corpus             */
   int64_t owned_windows;   /* sum over rules of the owned 3-word windows (Eq. 1) */
   int64_t device_bytes;    /* device memory held by the loaded grammar           */
+  int64_t root_words;      /* words (not rule references) in the root body       */
+  int64_t file_pairs;      /* (rule, file) pairs with a nonzero per-file weight (<= 64 files, else 0) */
+  int64_t file_words;      /* sum over those pairs of the rule's own words       */
 } gt_grammar_info;
 
 /* ---- context ---------------------------------------------------------- */

@@ -43,7 +43,7 @@ GT_Q_WORD_COUNT, GT_Q_SORT, GT_Q_INVERTED_INDEX, GT_Q_TERM_VECTOR = 0, 1, 2, 3
 class gt_grammar_info(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in ("num_words", "num_rules", "num_files", "num_syms", "num_edges",
                                               "num_root_edges", "depth", "num_tokens", "owned_windows",
-                                              "device_bytes")]
+                                              "device_bytes", "root_words", "file_pairs", "file_words")]
 
 
 _lib = None

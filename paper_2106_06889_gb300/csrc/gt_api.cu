@@ -258,6 +258,9 @@ GT_API gt_status gt_load_grammar(gt_ctx* ctx, const gt_grammar_desc* desc, void*
       d.rch_count = static_cast<int64_t*>(q) + F + 1;
     }
     gt::load_build_dag(g, s);
+    gt::file_sizes(g, s);
+    g->info.file_pairs = g->fentry_bound;
+    g->info.file_words = g->fword_bound;
     g->info.num_words = V;
     g->info.num_rules = R;
     g->info.num_files = F;

@@ -66,6 +66,27 @@ __global__ void popc_kernel(const unsigned long long* __restrict__ mask, int32_t
     cnt[r] = r == 0 ? 0 : __popcll(mask[r]);
 }
 
+__global__ void mask_totals_kernel(const unsigned long long* __restrict__ mask, const int32_t* __restrict__ W,
+                                   const int32_t* __restrict__ S, int32_t R, unsigned long long* __restrict__ out) {
+  unsigned long long a = 0, x = 0, y = 0;
+  for (int64_t r = 1 + blockIdx.x * int64_t(blockDim.x) + threadIdx.x; r < R; r += int64_t(gridDim.x) * blockDim.x) {
+    const unsigned long long f = __popcll(mask[r]);
+    a += f;
+    x += f * (unsigned long long)W[r];
+    y += f * (unsigned long long)(W[r] + S[r]);
+  }
+  for (int o = 16; o; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    x += __shfl_xor_sync(0xffffffffu, x, o);
+    y += __shfl_xor_sync(0xffffffffu, y, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&out[0], a);
+    atomicAdd(&out[1], x);
+    atomicAdd(&out[2], y);
+  }
+}
+
 __device__ __forceinline__ int64_t slot_of(const int64_t* off, const unsigned long long* mask, int32_t r, int f) {
   return off[r] + __popcll(mask[r] & ((1ull << f) - 1ull));
 }
@@ -472,6 +493,37 @@ int bits_for(int64_t x) {
 // the grammar was loaded, and sorts run over padded, bound-sized arrays.
 }  // namespace
 
+// At load: the file masks once, to size every per-file buffer exactly (pairs,
+// their words, their body symbols).  Grammars with more than 64 files keep 0.
+void file_sizes(gt_grammar* g, cudaStream_t s) {
+  gt_ctx* ctx = g->ctx;
+  const DevGrammar& d = g->d;
+  g->fentry_bound = g->fword_bound = g->fsym_bound = 0;
+  if (d.F > 64) return;
+  const int threads = 256, cap = ctx->num_sms * 16;
+  Buf mask(ctx, size_t(d.R) * 8, s), tot(ctx, 32, s);
+  auto* M = mask.as<unsigned long long>();
+  fmask_root_kernel<<<grid_for(d.R, threads, cap), threads, 0, s>>>(d.rfile_off, d.rfile_f, d.R, M);
+  GT_LAUNCH_CHECK();
+  for (int lv = 2; lv < d.depth; ++lv) {
+    const int64_t a = g->ledge_off[lv], b = g->ledge_off[lv + 1];
+    if (b > a) {
+      fmask_edges_kernel<<<grid_for(b - a, threads, cap), threads, 0, s>>>(d.ledge_child, d.ledge_par, a, b, M);
+      GT_LAUNCH_CHECK();
+    }
+  }
+  GT_CUDA(cudaMemsetAsync(tot.p, 0, 32, s));
+  mask_totals_kernel<<<grid_for(d.R, threads, cap), threads, 0, s>>>(M, d.nwords, d.nrefs, d.R,
+                                                                      tot.as<unsigned long long>());
+  GT_LAUNCH_CHECK();
+  unsigned long long h[3];
+  GT_CUDA(cudaMemcpyAsync(h, tot.p, 24, cudaMemcpyDeviceToHost, s));
+  GT_CUDA(cudaStreamSynchronize(s));
+  g->fentry_bound = int64_t(h[0]);
+  g->fword_bound = int64_t(h[1]);
+  g->fsym_bound = int64_t(h[2]);
+}
+
 void file_weights(gt_grammar* g, cudaStream_t s, FileWeights& fw) {
   gt_ctx* ctx = g->ctx;
   const DevGrammar& d = g->d;
@@ -594,6 +646,7 @@ void file_hist(gt_grammar* g, cudaStream_t s, FileHist& fh) {
     chunk_sort_kernel<true><<<unsigned(std::min<int64_t>(nxc, 65535)), kCsThreads, 0, s>>>(
         xc, xw.as<int32_t>(), xwt.as<uint32_t>(), nb, V, xent.p, xrs.as<int64_t>(), xrl.as<int32_t>());
     GT_LAUNCH_CHECK();
+    Phase ph3(ctx, "tv_hist_kernel", s);
     tv_hist_kernel<<<unsigned(pieces), kTvThreads, 0, s>>>(F, nb, rc, rrs.as<int64_t>(), rrl.as<int32_t>(),
                                                            rent.as<uint16_t>(), xc, xrs.as<int64_t>(),
                                                            xrl.as<int32_t>(), xent.as<uint64_t>(), ts);

@@ -174,9 +174,9 @@ struct gt_grammar {
   std::vector<int64_t> lvl_off;  // host copy: rules of level l are lvl_order[lvl_off[l] .. lvl_off[l+1])
   std::vector<int64_t> ledge_off; // host copy: parent edges of level-l children are ledge_*[ledge_off[l] ..)
   int64_t root_chunks = 0;        // host copy of *rch_count
-  int64_t fentry_bound = 0;       // bound on (rule, file) pairs with a nonzero per-file weight
-  int64_t fword_bound = 0;        // bound on rule words emitted once per such pair
-  int64_t fsym_bound = 0;         // bound on rule body symbols visited once per such pair
+  int64_t fentry_bound = 0;       // (rule, file) pairs with a nonzero per-file weight (<= 64 files)
+  int64_t fword_bound = 0;        // rule words emitted once per such pair
+  int64_t fsym_bound = 0;         // rule body symbols visited once per such pair
   std::vector<void*> owned;      // device allocations to free with the grammar
 };
 
@@ -351,6 +351,8 @@ struct FileWeights {
   Buf nnz;   // int64: number of (rule, file) pairs
 };
 void file_weights(gt_grammar* g, cudaStream_t s, FileWeights& fw);
+// at load: exact sizes of the per-file buffers (<= 64 files)
+void file_sizes(gt_grammar* g, cudaStream_t s);
 // One shared traversal for several per-file queries on one grammar: n_tv term
 // vectors (top_k each) and, if ii_out is set, the inverted index.
 void run_file_batch(gt_grammar* g, const int* tv_topk, int n_tv, gt_result** tv_out, gt_result** ii_out,

@@ -320,56 +320,6 @@ __global__ void sym_rule_kernel(const int64_t* __restrict__ rule_off, int32_t R,
   }
 }
 
-// Upper bound on the files holding each rule (for sizing per-file buffers
-// without waiting on the GPU): root files referencing it, plus its parents'
-// bounds, each capped at fcap.
-__global__ void fbound_init_kernel(const int64_t* __restrict__ rfile_off, int32_t R, unsigned long long* __restrict__ fb) {
-  for (int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; r < R; r += int64_t(gridDim.x) * blockDim.x)
-    fb[r] = (unsigned long long)(rfile_off[r + 1] - rfile_off[r]);
-}
-
-__global__ void fbound_edges_kernel(const int32_t* __restrict__ lchild, const int32_t* __restrict__ lpar, int64_t a,
-                                    int64_t b, unsigned long long fcap, unsigned long long* __restrict__ fb) {
-  const int lane = threadIdx.x & 31;
-  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-  for (int64_t i = a + blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i - lane < b; i += stride) {
-    const bool in = i < b;
-    const int32_t c = in ? lchild[i] : -1;
-    const int32_t p = in ? lpar[i] : 0;
-    unsigned long long v = (in && p != 0) ? min(fb[p], fcap) : 0ull;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const unsigned long long u = __shfl_down_sync(0xffffffffu, v, o);
-      const int32_t c2 = __shfl_down_sync(0xffffffffu, c, o);
-      if (lane + o < 32 && c2 == c) v += u;
-    }
-    const int32_t cp = __shfl_up_sync(0xffffffffu, c, 1);
-    if (in && (lane == 0 || cp != c) && v) atomicAdd(&fb[c], v);
-  }
-}
-
-__global__ void fbound_sum_kernel(const unsigned long long* __restrict__ fb, const int32_t* __restrict__ W,
-                                  const int32_t* __restrict__ S, int32_t R, unsigned long long fcap,
-                                  unsigned long long* __restrict__ out) {
-  unsigned long long a = 0, x = 0, y = 0;
-  for (int64_t r = 1 + blockIdx.x * int64_t(blockDim.x) + threadIdx.x; r < R; r += int64_t(gridDim.x) * blockDim.x) {
-    const unsigned long long f = min(fb[r], fcap);
-    a += f;
-    x += f * (unsigned long long)W[r];
-    y += f * (unsigned long long)(W[r] + S[r]);
-  }
-  for (int o = 16; o; o >>= 1) {
-    a += __shfl_xor_sync(0xffffffffu, a, o);
-    x += __shfl_xor_sync(0xffffffffu, x, o);
-    y += __shfl_xor_sync(0xffffffffu, y, o);
-  }
-  if ((threadIdx.x & 31) == 0) {
-    atomicAdd(&out[0], a);
-    atomicAdd(&out[1], x);
-    atomicAdd(&out[2], y);
-  }
-}
-
 __global__ void tile_rule_kernel(const int64_t* __restrict__ rule_off, int32_t R, int64_t G, int64_t ntiles,
                                  int32_t* __restrict__ tile_rule) {
   for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t <= ntiles; t += int64_t(gridDim.x) * blockDim.x) {
@@ -681,34 +631,9 @@ void load_build_dag(gt_grammar* g, cudaStream_t s) {
     d.file_len = flen;
     d.N = n;
     g->info.num_tokens = int64_t(n);
+    g->info.root_words = int64_t(hv[2]);
     g->info.owned_windows = int64_t(hv[0] + hv[5]);
     GT_CUDA(cudaStreamSynchronize(s));
-  }
-
-  // ---- bounds for the per-file (top-down, <= 64 files) buffers ----
-  {
-    const unsigned long long fcap = (unsigned long long)std::min(F, 64);
-    Buf fb(ctx, size_t(R) * 8, s);
-    auto* FB = fb.as<unsigned long long>();
-    fbound_init_kernel<<<grid_for(R, threads, cap), threads, 0, s>>>(d.rfile_off, R, FB);
-    GT_LAUNCH_CHECK();
-    for (int32_t lv = 2; lv < d.depth; ++lv) {
-      const int64_t a = g->ledge_off[lv], b = g->ledge_off[lv + 1];
-      if (b > a) {
-        fbound_edges_kernel<<<grid_for(b - a, threads, cap), threads, 0, s>>>(d.ledge_child, d.ledge_par, a, b, fcap,
-                                                                               FB);
-        GT_LAUNCH_CHECK();
-      }
-    }
-    GT_CUDA(cudaMemsetAsync(ctr + 12, 0, 24, s));
-    fbound_sum_kernel<<<grid_for(R, threads, cap), threads, 0, s>>>(FB, d.nwords, d.nrefs, R, fcap, ctr + 12);
-    GT_LAUNCH_CHECK();
-    unsigned long long hb[3];
-    GT_CUDA(cudaMemcpyAsync(hb, ctr + 12, 24, cudaMemcpyDeviceToHost, s));
-    GT_CUDA(cudaStreamSynchronize(s));
-    g->fentry_bound = int64_t(hb[0]);
-    g->fword_bound = int64_t(hb[1]);
-    g->fsym_bound = int64_t(hb[2]);
   }
 
   // ---- tiles ----
