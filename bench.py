@@ -127,6 +127,83 @@ def run_step(B, gh, bufs, analytics, stream, keep):
     keep.extend(r for r in B.gt_run_batch(gh.ctx, qs, stream) if r is not None)
 
 
+def serving_bench(B, ctx, n_corpora=8, n_queries=1000, seed=7):
+    """Continuous-batching server vs the plain one-query-at-a-time path on a set
+    of resident corpora; mix 40% word count / 30% inverted index / 30% 3-gram
+    count, corpus chosen uniformly; Poisson arrivals at 50/80/95% of the
+    measured saturated capacity."""
+    import torch
+    from paper_2106_06889_gb300.corpus import load_serving
+    gs = [load_serving(i) for i in range(n_corpora)]
+    hs = [B.gt_load_grammar(ctx, g) for g in gs]
+    ntok = [int(g.meta["N"]) for g in gs]
+    rng = np.random.default_rng(seed)
+    kinds = rng.choice([B.GT_Q_WORD_COUNT, B.GT_Q_INVERTED_INDEX, B.GT_Q_SEQUENCE_COUNT], size=n_queries,
+                       p=[0.4, 0.3, 0.3])
+    which = rng.integers(0, n_corpora, size=n_queries)
+    bufs = [torch.empty(g.num_words, dtype=torch.int64, device="cuda") for g in gs]
+
+    def q(i):
+        k = int(kinds[i])
+        return [(hs[which[i]], k, 0, bufs[which[i]] if k == B.GT_Q_WORD_COUNT else None)]
+
+    tokens = sum(ntok[which[i]] for i in range(n_queries))
+    # plain: one query at a time, each waited for
+    st = torch.cuda.Stream()
+    for i in range(min(20, n_queries)):  # warm-up
+        for r in B.gt_run_batch(ctx, q(i), st):
+            if r is not None:
+                B.gt_free_result(r)
+    st.synchronize()
+    t0 = time.perf_counter()
+    for i in range(n_queries):
+        out = B.gt_run_batch(ctx, q(i), st)
+        st.synchronize()
+        for r in out:
+            if r is not None:
+                B.gt_free_result(r)
+    t_plain = time.perf_counter() - t0
+    sv = B.gt_server_create(ctx, slots=8)
+
+    def run(arrivals):
+        tickets, t_start = [], time.perf_counter()
+        for i in range(n_queries):
+            if arrivals is not None:
+                delay = t_start + arrivals[i] - time.perf_counter()
+                if delay > 0:
+                    time.sleep(delay)
+            tickets.append(B.gt_submit(sv, q(i)))
+        lats = []
+        for t in tickets:
+            out, lat = B.gt_poll(sv, t, 1, wait=True)
+            lats.append(lat / 1e6)
+            for r in out:
+                if r is not None:
+                    B.gt_free_result(r)
+        return time.perf_counter() - t_start, np.array(lats)
+
+    run(None)  # warm-up
+    t_sat, _ = run(None)
+    cap_qps = n_queries / t_sat
+    rates = []
+    for frac in (0.5, 0.8, 0.95):
+        lam = frac * cap_qps
+        arr = np.cumsum(rng.exponential(1.0 / lam, size=n_queries))
+        t, lats = run(arr)
+        rates.append({"load": frac, "offered_qps": lam, "achieved_qps": n_queries / t,
+                      "p50_ms": float(np.percentile(lats, 50)), "p99_ms": float(np.percentile(lats, 99))})
+    stats = B.gt_server_stats(sv)
+    B.gt_server_destroy(sv)
+    for h in hs:
+        B.gt_free_grammar(h)
+    return {"corpora": n_corpora, "corpus_tokens": ntok, "queries": n_queries,
+            "mix": "40% word count / 30% inverted index / 30% 3-gram count, corpus uniform",
+            "plain": {"qps": n_queries / t_plain, "tokens_per_s": tokens / t_plain},
+            "served_saturated": {"qps": cap_qps, "tokens_per_s": tokens / t_sat, "slots": 8,
+                                 "max_inflight": stats["max_inflight"]},
+            "poisson": rates}
+
+
 def oracle_sample(g, budget_s: float = 20.0):
     """Time the CPU oracle on a bounded prefix of files; returns tokens/s, sample note."""
     import oracle
@@ -158,6 +235,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (used for profiling runs)")
     ap.add_argument("--no-extras", action="store_true", help="skip the secondary sequence-count timing")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving (p50/p99) measurement")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -339,6 +417,11 @@ def main():
                "d2h_bytes_per_step": d2h,
                "note": "gt_load_grammar from pinned host arrays + analytics + result copy back, per step"}
 
+    # ---- serving: continuous batching vs one query at a time, p50/p99 ----
+    serving = None
+    if rank == 0 and not args.no_serving:
+        serving = serving_bench(B, ctx)
+
     # ---- CPU baseline: the oracle on a bounded sample, rank 0 ----
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -354,7 +437,8 @@ def main():
                            "tokens": N, "grammar_symbols": info["num_syms"], "rules": info["num_rules"],
                            "files": info["num_files"], "l2": "inputs larger than L2 (symbol array "
                            f"{4 * info['num_syms'] / 1e6:.0f} MB > 129 MB)"},
-                "roofline": roofline, "phases": phases, "extras": extras, "cpu_baseline": cpu, "e2e": e2e,
+                "roofline": roofline, "phases": phases, "extras": extras, "serving": serving,
+                "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clk}
         print(json.dumps(line))
     B.gt_free_grammar(gh)

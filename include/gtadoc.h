@@ -179,7 +179,9 @@ typedef enum {
   GT_Q_WORD_COUNT = 0,     /* d_counts: device uint64[num_words]                */
   GT_Q_SORT = 1,           /* param: order (0 or 1)                             */
   GT_Q_INVERTED_INDEX = 2,
-  GT_Q_TERM_VECTOR = 3     /* param: top_k (0 = all)                            */
+  GT_Q_TERM_VECTOR = 3,    /* param: top_k (0 = all)                            */
+  GT_Q_SEQUENCE_COUNT = 4, /* param: per_file (0 or 1)                          */
+  GT_Q_RANKED_INDEX = 5    /* param: n (1 or 3)                                 */
 } gt_query_kind;
 
 typedef struct {
@@ -190,6 +192,34 @@ typedef struct {
 } gt_query;
 
 gt_status gt_run_batch(gt_ctx* ctx, const gt_query* q, int nq, void* stream, gt_result** out);
+
+/* ---- serving (not in the paper) ------------------------------------------
+ * A server keeps the context's grammars resident and runs submitted requests
+ * (each a list of gt_query, like one gt_run_batch call) with continuous
+ * batching: a worker thread owns `slots` CUDA streams; whenever a slot is free
+ * it admits waiting requests in arrival order while their estimated device
+ * footprint fits `mem_budget` bytes (0 = unlimited), groups the admitted
+ * queries by grammar so that they share one traversal, and launches each
+ * group on a free stream, so that groups overlap on the device.  Results of a
+ * request are the same as those of gt_run_batch on the same queries.
+ *   gt_submit: enqueue; *ticket identifies the request.  GT_EBUSY if the
+ *     request's footprint alone exceeds the budget.  Word-count buffers must
+ *     stay valid until the request completes.
+ *   gt_poll: wait != 0 blocks until the request completes; otherwise
+ *     GT_EBUSY while it runs.  On completion, out (room for the request's nq
+ *     results, or NULL to discard them) receives the results, *latency_ns the
+ *     time from submission to completion, and the ticket is released; the
+ *     return value is the request's status.
+ *   gt_server_destroy: finishes every submitted request, then frees the
+ *     results nobody polled.
+ * Profiling (gt_profile_enable) must be off while a server runs. */
+typedef struct gt_server gt_server;
+gt_status gt_server_create(gt_ctx* ctx, int slots, size_t mem_budget, gt_server** out);
+gt_status gt_submit(gt_server* sv, const gt_query* q, int nq, uint64_t* ticket);
+gt_status gt_poll(gt_server* sv, uint64_t ticket, int wait, gt_result** out, int64_t* latency_ns);
+gt_status gt_server_stats(gt_server* sv, int64_t* waiting, int64_t* inflight, int64_t* max_inflight,
+                          uint64_t* mem_in_use);
+gt_status gt_server_destroy(gt_server* sv);
 
 /* ---- results ---------------------------------------------------------- */
 

@@ -38,6 +38,7 @@ class gt_query(ctypes.Structure):
 
 
 GT_Q_WORD_COUNT, GT_Q_SORT, GT_Q_INVERTED_INDEX, GT_Q_TERM_VECTOR = 0, 1, 2, 3
+GT_Q_SEQUENCE_COUNT, GT_Q_RANKED_INDEX = 4, 5
 
 
 class gt_grammar_info(ctypes.Structure):
@@ -77,6 +78,12 @@ def lib() -> ctypes.CDLL:
             "gt_profile_enable": [_P, ctypes.c_int],
             "gt_set_param": [_P, ctypes.c_char_p, ctypes.c_int64],
             "gt_run_batch": [_P, _P, ctypes.c_int, _P, _P],
+            "gt_server_create": [_P, ctypes.c_int, ctypes.c_size_t, ctypes.POINTER(_P)],
+            "gt_submit": [_P, _P, ctypes.c_int, ctypes.POINTER(ctypes.c_uint64)],
+            "gt_poll": [_P, ctypes.c_uint64, ctypes.c_int, _P, ctypes.POINTER(ctypes.c_int64)],
+            "gt_server_stats": [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                                ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_uint64)],
+            "gt_server_destroy": [_P],
             "gt_profile_reset": [_P],
             "gt_profile_read": [_P, ctypes.c_char_p, ctypes.POINTER(ctypes.c_double),
                                 ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)],
@@ -300,9 +307,7 @@ def gt_set_param(ctx: Context, name: str, value: int) -> None:
     _check(lib().gt_set_param(ctx.handle, name.encode(), int(value)), ctx.handle)
 
 
-def gt_run_batch(ctx: Context, queries, stream=None):
-    """queries: list of (GrammarHandle, kind, param, counts_tensor_or_None).
-    Returns a list with a ResultHandle (or None for word counts) per query."""
+def _query_array(queries):
     n = len(queries)
     arr = (gt_query * max(n, 1))()
     for i, (gh, kind, param, counts) in enumerate(queries):
@@ -310,7 +315,59 @@ def gt_run_batch(ctx: Context, queries, stream=None):
         arr[i].kind = int(kind)
         arr[i].param = int(param)
         arr[i].d_counts = _dptr(counts).value if counts is not None else None
+    return arr
+
+
+def gt_run_batch(ctx: Context, queries, stream=None):
+    """queries: list of (GrammarHandle, kind, param, counts_tensor_or_None).
+    Returns a list with a ResultHandle (or None for word counts) per query."""
+    n = len(queries)
+    arr = _query_array(queries)
     outs = (ctypes.c_void_p * max(n, 1))()
     _check(lib().gt_run_batch(ctx.handle, ctypes.cast(arr, ctypes.c_void_p), n, _stream(stream),
                               ctypes.cast(outs, ctypes.c_void_p)), ctx.handle)
     return [ResultHandle(ctypes.c_void_p(outs[i]), ctx) if outs[i] else None for i in range(n)]
+
+
+# ---- serving --------------------------------------------------------------------
+
+@dataclass
+class Server:
+    handle: ctypes.c_void_p
+    ctx: Context
+
+
+def gt_server_create(ctx: Context, slots: int = 4, mem_budget: int = 0) -> Server:
+    h = _P()
+    _check(lib().gt_server_create(ctx.handle, slots, mem_budget, ctypes.byref(h)), ctx.handle)
+    return Server(h, ctx)
+
+
+def gt_submit(sv: Server, queries) -> int:
+    """queries: list of (GrammarHandle, kind, param, counts_tensor_or_None)."""
+    arr = _query_array(queries)
+    t = ctypes.c_uint64()
+    _check(lib().gt_submit(sv.handle, ctypes.cast(arr, ctypes.c_void_p), len(queries), ctypes.byref(t)),
+           sv.ctx.handle)
+    return int(t.value)
+
+
+def gt_poll(sv: Server, ticket: int, nq: int, wait: bool = True):
+    """(results or None while running, latency in ns)."""
+    outs = (ctypes.c_void_p * max(nq, 1))()
+    lat = ctypes.c_int64()
+    rc = lib().gt_poll(sv.handle, ticket, int(wait), ctypes.cast(outs, ctypes.c_void_p), ctypes.byref(lat))
+    if rc == 7 and not wait:  # GT_EBUSY: still running
+        return None, None
+    _check(rc, sv.ctx.handle)
+    return [ResultHandle(ctypes.c_void_p(outs[i]), sv.ctx) if outs[i] else None for i in range(nq)], int(lat.value)
+
+
+def gt_server_stats(sv: Server) -> dict:
+    a, b, c, d = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_uint64()
+    _check(lib().gt_server_stats(sv.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d)))
+    return {"waiting": a.value, "inflight": b.value, "max_inflight": c.value, "mem_in_use": d.value}
+
+
+def gt_server_destroy(sv: Server) -> None:
+    _check(lib().gt_server_destroy(sv.handle))

@@ -24,7 +24,7 @@ import numpy as np
 from .._build import build_corpus, CORPUS_SO, ROOT
 
 __all__ = ["Grammar", "sequitur", "zipf_tokens", "Corpus", "make_corpus", "CONFIGS", "load_config",
-           "root_only_grammar", "refactor_grammar", "prefix_files"]
+           "root_only_grammar", "refactor_grammar", "prefix_files", "serving_corpus", "load_serving"]
 
 
 @dataclass
@@ -273,6 +273,40 @@ CONFIGS = {
     "nested_500m": dict(kind="nested", seed=20210615, N=500_000_000, V=1_000_000, s=1.05, phrases=4096,
                         phrase_len=16, depth=6, fanout=4, pool=256, inject_frac=0.5),
 }
+
+
+def serving_corpus(i: int, seed: int = 20210617, tokens_range=(1_000_000, 8_000_000)) -> Corpus:
+    """Corpus i of the serving set: size log-uniform in tokens_range, Zipf
+    exponent uniform in [1.0, 1.2] over 1M words, files log-uniform in
+    [10k, 2M] tokens (at most 64 per corpus)."""
+    rng = np.random.default_rng(seed + 7919 * i)
+    n = int(np.exp(rng.uniform(np.log(tokens_range[0]), np.log(tokens_range[1]))))
+    s_exp = float(rng.uniform(1.0, 1.2))
+    V = 1_000_000
+    cdf = zipf_cdf(V, s_exp)
+    perm = rng.permutation(V).astype(np.int32)
+    lens = []
+    while sum(lens) < n and len(lens) < 64:
+        lens.append(int(np.exp(rng.uniform(np.log(10_000), np.log(2_000_000)))))
+    lens = np.array(lens, np.float64)
+    lens = np.maximum(np.round(lens / lens.sum() * n), 1).astype(np.int64)
+    toks = zipf_tokens(rng, int(lens.sum()), cdf, perm)
+    meta = {"name": f"serving{i}", "seed": seed, "V": V, "s": s_exp, "N": int(toks.shape[0]), "F": int(lens.shape[0])}
+    return Corpus(toks, lens, V, meta)
+
+
+def load_serving(i: int, **kw) -> Grammar:
+    tag = hashlib.sha1(json.dumps(["serving", i, kw, "v1"], sort_keys=True, default=str).encode()).hexdigest()[:12]
+    path = cache_dir() / f"serving{i}_{tag}.npz"
+    if path.exists():
+        return Grammar.load(path)
+    c = serving_corpus(i, **kw)
+    g = sequitur(c.tokens, c.file_lens, c.num_words)
+    g.meta = dict(c.meta)
+    tmp = path.with_suffix(f".tmp{os.getpid()}.npz")
+    g.save(tmp)
+    os.replace(tmp, path)
+    return g
 
 
 def cache_dir() -> Path:

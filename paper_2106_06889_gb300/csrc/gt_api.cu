@@ -421,7 +421,9 @@ GT_API gt_status gt_run_batch(gt_ctx* ctx, const gt_query* q, int nq, void* stre
   for (int i = 0; i < nq; ++i) {
     out[i] = nullptr;
     if (!q[i].grammar || q[i].grammar->ctx != ctx) return GT_EINVAL;
-    if (q[i].kind < GT_Q_WORD_COUNT || q[i].kind > GT_Q_TERM_VECTOR) return GT_EINVAL;
+    if (q[i].kind < GT_Q_WORD_COUNT || q[i].kind > GT_Q_RANKED_INDEX) return GT_EINVAL;
+    if (q[i].kind == GT_Q_SEQUENCE_COUNT && q[i].param != 0 && q[i].param != 1) return GT_EINVAL;
+    if (q[i].kind == GT_Q_RANKED_INDEX && q[i].param != 1 && q[i].param != 3) return GT_EINVAL;
     if (q[i].kind == GT_Q_WORD_COUNT && !q[i].d_counts) return GT_EINVAL;
     if (q[i].kind == GT_Q_SORT && q[i].param != 0 && q[i].param != 1) return GT_EINVAL;
     if (q[i].kind == GT_Q_TERM_VECTOR && q[i].param < 0) return GT_EINVAL;
@@ -479,6 +481,11 @@ GT_API gt_status gt_run_batch(gt_ctx* ctx, const gt_query* q, int nq, void* stre
         if (ii >= 0) out[ii] = iir;
         for (int j : same)  // a second inverted-index query on the same grammar gets its own copy
           if (q[j].kind == GT_Q_INVERTED_INDEX && j != ii) out[j] = gt::run_inverted_index(g, s);
+      }
+      for (int j : same) {
+        if (q[j].kind == GT_Q_SEQUENCE_COUNT) out[j] = gt::run_sequence_count(g, q[j].param, s);
+        if (q[j].kind == GT_Q_RANKED_INDEX)
+          out[j] = q[j].param == 3 ? gt::run_ranked_windows(g, s) : gt::run_ranked_words(g, s);
       }
       for (int j : same) done[j] = true;
     }
