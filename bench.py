@@ -204,6 +204,36 @@ def serving_bench(B, ctx, n_corpora=8, n_queries=1000, seed=7):
             "poisson": rates}
 
 
+def small_word_count(B, ctx, reps=200):
+    """Word count on the 200k-token single-file corpus, where launch latency
+    dominates: per-query time with the launch sequence replayed from a CUDA
+    graph against launched kernel by kernel."""
+    import torch
+    from paper_2106_06889_gb300.corpus import load_config
+    g, _ = load_config("wc_single_200k")
+    gh = B.gt_load_grammar(ctx, g)
+    out = torch.empty(g.num_words, dtype=torch.int64, device="cuda")
+    st = torch.cuda.Stream()
+    res = {}
+    for use in (1, 0):
+        B.gt_set_param(ctx, "use_graphs", use)
+        with torch.cuda.stream(st):
+            for _ in range(5):
+                B.gt_word_count(gh, out, st)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            for _ in range(reps):
+                B.gt_word_count(gh, out, st)
+            b.record(st)
+            torch.cuda.synchronize()
+        res["graph_us" if use else "direct_us"] = 1e3 * a.elapsed_time(b) / reps
+    B.gt_set_param(ctx, "use_graphs", 1)
+    B.gt_free_grammar(gh)
+    res["tokens"] = 200_000
+    return res
+
+
 def oracle_sample(g, budget_s: float = 20.0):
     """Time the CPU oracle on a bounded prefix of files; returns tokens/s, sample note."""
     import oracle
@@ -299,8 +329,6 @@ def main():
         for r in keep:
             B.gt_free_result(r)
         keep.clear()
-        B.gt_profile_reset(ctx)
-        B.gt_profile_enable(ctx, True)
         launches0 = B.gt_kernel_launches()
         barrier()
         torch.cuda.synchronize()
@@ -313,6 +341,7 @@ def main():
         torch.cuda.synchronize()
         barrier()
         clk = clocks.stop()
+        launches = B.gt_kernel_launches() - launches0
         tv_entries = 0
         for r in keep:
             try:
@@ -322,8 +351,17 @@ def main():
         for r in keep:
             B.gt_free_result(r)
         keep.clear()
-        launches = B.gt_kernel_launches() - launches0
+        # phase timers: a separate pass with CUDA events around every phase
+        # (kept out of the timed region; graphs are not replayed while profiling)
+        B.gt_profile_reset(ctx)
+        B.gt_profile_enable(ctx, True)
+        for _ in range(max(3, min(args.steps, 10))):
+            run_step(B, gh, bufs, wl["analytics"], stream, keep)
+        torch.cuda.synchronize()
         B.gt_profile_enable(ctx, False)
+        for r in keep:
+            B.gt_free_result(r)
+        keep.clear()
     ms = ev0.elapsed_time(ev1)
     if world > 1:
         import torch.distributed as dist
@@ -373,6 +411,7 @@ def main():
             keep.clear()
         ms3 = e0.elapsed_time(e1) / n3
         extras["sequence_count"] = {"tokens_per_s": N / (ms3 / 1e3), "ms_per_query": ms3}
+        extras["small_word_count"] = small_word_count(B, ctx)
 
     # ---- end to end through the public API with host buffers ----
     e2e = None

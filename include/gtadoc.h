@@ -124,7 +124,8 @@ gt_status gt_grammar_info_get(const gt_grammar* g, gt_grammar_info* info);
 gt_status gt_rule_weights(gt_grammar* g, uint64_t* d_weights, void* stream);
 
 /* Word count (Fig. 2): d_counts[w] = occurrences of word w in all files.
- * d_counts: device uint64[num_words], written entirely. */
+ * d_counts: device uint64[num_words], written entirely.  Replayed from a CUDA
+ * graph once the same buffer has been used before (see "use_graphs"). */
 gt_status gt_word_count(gt_grammar* g, uint64_t* d_counts, void* stream);
 
 /* Sort: the distinct words with their counts.  order 0: ascending word ID;
@@ -246,6 +247,12 @@ int64_t gt_kernel_launches(void);
  *   "wc_aggregate"  1: merge equal words inside a warp (__match_any_sync)
  *                   before the shared-memory histogram update; 0 (default):
  *                   update per lane.
+ *   "use_graphs"    1 (default): word counts (gt_word_count, and word-count
+ *                   queries of gt_run_batch / the server) capture a grammar's
+ *                   launch sequence into a CUDA graph on the second call that
+ *                   writes into a given output buffer, and replay it from then
+ *                   on (that call should happen outside any stream capture);
+ *                   not while profiling is enabled.  0: launch kernel by kernel.
  * GT_ENOTFOUND for an unknown name. */
 gt_status gt_set_param(gt_ctx* ctx, const char* name, int64_t value);
 

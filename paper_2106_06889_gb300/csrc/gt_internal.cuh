@@ -178,6 +178,15 @@ struct gt_grammar {
   int64_t fword_bound = 0;        // rule words emitted once per such pair
   int64_t fsym_bound = 0;         // rule body symbols visited once per such pair
   std::vector<void*> owned;      // device allocations to free with the grammar
+  // word-count launch sequences captured as CUDA graphs, keyed by output buffer
+  struct WcGraph {
+    uint64_t* out;
+    cudaGraphExec_t exec;  // null until the second call with this buffer
+    int uses;
+    int kernels;           // kernels one replay launches
+  };
+  std::vector<WcGraph> wc_graphs;
+  std::mutex graph_mu;
 };
 
 struct gt_result {

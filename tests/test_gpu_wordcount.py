@@ -157,3 +157,27 @@ def test_full_size_multifile_word_count(ctx):
     g, _ = load_config("multi64_50m")
     got = word_count_gpu(ctx, g)
     assert np.array_equal(got, oracle.word_count(g))
+
+
+def test_graph_replay_matches(ctx):
+    """Word counts replayed from a captured CUDA graph equal direct launches and
+    the oracle, across calls and after the buffer is reused."""
+    c = make_corpus("wc_single_200k")
+    g = sequitur(c.tokens, c.file_lens, c.num_words)
+    gh = B.gt_load_grammar(ctx, g)
+    want = oracle.word_count(g)
+    out = torch.empty(g.num_words, dtype=torch.int64, device="cuda")
+    for i in range(4):  # call 1 direct, call 2 captures, calls 3-4 replay
+        out.fill_(-7)
+        before = B.gt_kernel_launches()
+        B.gt_word_count(gh, out)
+        B.gt_sync(ctx)
+        assert B.gt_kernel_launches() > before
+        assert np.array_equal(out.cpu().numpy().astype(np.uint64), want), i
+    B.gt_set_param(ctx, "use_graphs", 0)
+    out.fill_(-7)
+    B.gt_word_count(gh, out)
+    B.gt_sync(ctx)
+    assert np.array_equal(out.cpu().numpy().astype(np.uint64), want)
+    B.gt_set_param(ctx, "use_graphs", 1)
+    B.gt_free_grammar(gh)
