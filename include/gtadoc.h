@@ -135,15 +135,15 @@ gt_status gt_sort(gt_grammar* g, int order, void* stream, gt_result** out);
 
 /* Inverted index: for each word, the ascending list of files containing it.
  * Result fields: "offsets" int64[num_words+1], "file" int32[offsets[V]].
- * Top-down strategy (Section IV-A), currently for at most 64 files;
- * GT_EOVERFLOW beyond that. */
+ * Top-down strategy (Section IV-A) for at most 64 files, bottom-up beyond
+ * (see "file_strategy"). */
 gt_status gt_inverted_index(gt_grammar* g, void* stream, gt_result** out);
 
 /* Term vector: for each file, its distinct words with their in-file counts.
  * top_k == 0: all words, ascending word ID.  top_k > 0: the top_k largest
  * counts of each file, by descending count then ascending word ID.
  * Result fields: "offsets" int64[num_files+1], "word" int32[], "count" uint64[].
- * Same strategy and file limit as gt_inverted_index. */
+ * Same strategy selection as gt_inverted_index. */
 gt_status gt_term_vector(gt_grammar* g, int top_k, void* stream, gt_result** out);
 
 /* Sequence count for l = 3 (Section IV-D): every window of three consecutive
@@ -151,7 +151,7 @@ gt_status gt_term_vector(gt_grammar* g, int top_k, void* stream, gt_result** out
  * key = w1 << 42 | w2 << 21 | w3 (requires num_words <= 2^21).
  * per_file == 0: fields "key" uint64[n], "count" uint64[n], ascending key.
  * per_file == 1: fields "file" int32[n], "key" uint64[n], "count" uint64[n],
- *                ascending (file, key); top-down file weights, <= 64 files.
+ *                ascending (file, key); strategy as for gt_inverted_index.
  * Each window is counted once, by the lowest rule whose body it crosses, with
  * that rule's weight; the windows a rule owns are built from its body, a
  * two-symbol look-ahead and its children's head/tail buffers. */
@@ -161,7 +161,7 @@ gt_status gt_sequence_count(gt_grammar* g, int per_file, void* stream, gt_result
  * gt_sequence_count; n == 1: keys are words.  For each key (ascending), the
  * files containing it with the in-file count, by descending count then
  * ascending file.  Fields: "offsets" int64[nkeys+1], "key" uint64[nkeys],
- * "file" int32[m], "count" uint64[m].  Top-down file weights, <= 64 files. */
+ * "file" int32[m], "count" uint64[m].  Strategy as for gt_inverted_index. */
 gt_status gt_ranked_index(gt_grammar* g, int n, void* stream, gt_result** out);
 
 /* Head and tail buffers (Section IV-C): for every rule, the first two and
@@ -253,6 +253,11 @@ int64_t gt_kernel_launches(void);
  *                   writes into a given output buffer, and replay it from then
  *                   on (that call should happen outside any stream capture);
  *                   not while profiling is enabled.  0: launch kernel by kernel.
+ *   "file_strategy" per-file analytics (term vector, inverted index, per-file
+ *                   sequence count, ranked index): 0 (default) picks top-down
+ *                   for at most 64 files and bottom-up otherwise (the paper's
+ *                   strategy selection, Section V-C); 1 forces top-down, 2
+ *                   forces bottom-up.
  * GT_ENOTFOUND for an unknown name. */
 gt_status gt_set_param(gt_ctx* ctx, const char* name, int64_t value);
 

@@ -115,4 +115,61 @@ __device__ __forceinline__ uint64_t hash_u64(uint64_t x) {
   return x;
 }
 
+// ---- 3-word windows (shared by the top-down and bottom-up sequence paths) ----
+
+struct Sym3 {
+  int32_t first, second, second_last, last;  // -1 where the expansion is too short
+};
+
+__device__ __forceinline__ Sym3 sym_words(const DevGrammar& d, const int32_t* __restrict__ head,
+                                          const int32_t* __restrict__ tail, int32_t x) {
+  Sym3 r;
+  if (x < d.V) {
+    r.first = r.last = x;
+    r.second = r.second_last = -1;
+  } else {
+    const int32_t c = x - d.V;
+    r.first = head[2 * c];
+    r.second = head[2 * c + 1];
+    r.second_last = tail[2 * c];
+    r.last = tail[2 * c + 1];
+  }
+  return r;
+}
+
+__device__ __forceinline__ uint64_t pack_compact(int32_t a, int32_t b, int32_t c, int kb) {
+  return (uint64_t(uint32_t(a)) << (2 * kb)) | (uint64_t(uint32_t(b)) << kb) | uint64_t(uint32_t(c));
+}
+
+// End (exclusive) of the body sequence holding position j: the file's end in
+// the root, the rule's end elsewhere.  Also returns the rule.
+__device__ __forceinline__ int64_t seq_end(const DevGrammar& d, int64_t j, int32_t* rule, int32_t* file) {
+  if (j < d.root_len) {
+    const int64_t f = upper_bound_dev(d.file_off, int64_t(d.F) + 1, j) - 1;
+    *rule = 0;
+    *file = int32_t(f);
+    return d.file_off[f + 1];
+  }
+  const int32_t r = d.sym_rule[j - d.first_rule_tile * kTile];
+  *rule = r;
+  *file = -1;
+  return d.rule_off[r + 1];
+}
+
+// The (at most two) owned windows starting in body symbol j; returns how many.
+__device__ __forceinline__ int windows_at(const DevGrammar& d, const int32_t* __restrict__ head,
+                                          const int32_t* __restrict__ tail, int64_t j, int64_t end, int kb,
+                                          uint64_t* k) {
+  if (j + 1 >= end) return 0;
+  const Sym3 a = sym_words(d, head, tail, d.sym[j]);
+  const Sym3 b = sym_words(d, head, tail, d.sym[j + 1]);
+  const int32_t n1 = b.first;
+  int32_t n2 = b.second;
+  if (n2 < 0) n2 = j + 2 < end ? sym_words(d, head, tail, d.sym[j + 2]).first : -1;
+  int n = 0;
+  if (a.second_last >= 0) k[n++] = pack_compact(a.second_last, a.last, n1, kb);  // child with >= 2 words
+  if (n2 >= 0) k[n++] = pack_compact(a.last, n1, n2, kb);
+  return n;
+}
+
 }  // namespace gt

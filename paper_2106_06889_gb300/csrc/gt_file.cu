@@ -529,7 +529,7 @@ void file_weights(gt_grammar* g, cudaStream_t s, FileWeights& fw) {
   const DevGrammar& d = g->d;
   const int threads = 256, cap = ctx->num_sms * 16;
   const int32_t R = d.R, F = d.F, V = d.V;
-  if (F > 64) fail(GT_EOVERFLOW, "per-file analytics use the top-down strategy, limited to 64 files");
+  if (F > 64) fail(GT_EOVERFLOW, "the top-down per-file strategy holds at most 64 files (file_strategy 0 or 2 selects bottom-up)");
   if (d.N >= (uint64_t(1) << 32)) fail(GT_EOVERFLOW, "per-file analytics need fewer than 2^32 tokens per grammar");
   if (V > (1 << 21)) fail(GT_EOVERFLOW, "per-file analytics support num_words <= 2^21");
   const int64_t EB = g->fentry_bound;
@@ -662,59 +662,37 @@ void file_hist(gt_grammar* g, cudaStream_t s, FileHist& fh) {
 gt_result* term_vector_from(gt_grammar* g, FileHist& fh, int top_k, cudaStream_t s) {
   gt_ctx* ctx = g->ctx;
   const DevGrammar& d = g->d;
-  const int threads = 256, cap = ctx->num_sms * 16;
-  ResultBuilder rb(ctx, s);
   const int64_t pieces = int64_t(d.F) * fh.nb;
   const int64_t nb_ = fh.bound;
+  TvSlots ts{fh.slot_word.as<int32_t>(), fh.slot_cnt.as<uint32_t>(), fh.nnz.as<int64_t>(), fh.bits.as<uint32_t>()};
+  if (top_k > 0) {
+    Buf tw(ctx, size_t(nb_) * 4, s), tc(ctx, size_t(nb_) * 8, s), full_off(ctx, size_t(d.F + 1) * 8, s);
+    {
+      Phase ph(ctx, "tv_out", s);
+      tv_gather_kernel<<<unsigned(pieces), 256, 0, s>>>(ts, fh.off.as<int64_t>(), tw.as<int32_t>(),
+                                                        tc.as<uint64_t>());
+      GT_LAUNCH_CHECK();
+      tv_file_off_kernel<<<1, 256, 0, s>>>(fh.off.as<int64_t>(), fh.nb, d.F, fh.total.as<int64_t>(),
+                                           full_off.as<int64_t>());
+      GT_LAUNCH_CHECK();
+    }
+    return tv_from_arrays(ctx, tw.as<int32_t>(), tc.as<uint64_t>(), full_off.as<int64_t>(), fh.total.as<int64_t>(),
+                          nb_, d.F, top_k, s);
+  }
+  ResultBuilder rb(ctx, s);
   Phase ph(ctx, "tv_out", s);
   auto* tv_off = static_cast<int64_t*>(rb.alloc(size_t(d.F + 1) * 8));
-  TvSlots ts{fh.slot_word.as<int32_t>(), fh.slot_cnt.as<uint32_t>(), fh.nnz.as<int64_t>(), fh.bits.as<uint32_t>()};
-  if (top_k <= 0) {
-    auto* word = static_cast<int32_t*>(rb.alloc(size_t(nb_) * 4));
-    auto* cnt = static_cast<uint64_t*>(rb.alloc(size_t(nb_) * 8));
-    int64_t* len = rb.new_len_slot();
-    tv_gather_kernel<<<unsigned(pieces), 256, 0, s>>>(ts, fh.off.as<int64_t>(), word, cnt);
-    GT_LAUNCH_CHECK();
-    tv_file_off_kernel<<<1, 256, 0, s>>>(fh.off.as<int64_t>(), fh.nb, d.F, fh.total.as<int64_t>(), tv_off);
-    GT_LAUNCH_CHECK();
-    GT_CUDA(cudaMemcpyAsync(len, fh.total.p, 8, cudaMemcpyDeviceToDevice, s));
-    rb.field("offsets", tv_off, int64_t(d.F) + 1);
-    rb.field_dyn("word", word, len);
-    rb.field_dyn("count", cnt, len);
-  } else {
-    Buf tw(ctx, size_t(nb_) * 4, s), tc(ctx, size_t(nb_) * 8, s), full_off(ctx, size_t(d.F + 1) * 8, s);
-    tv_gather_kernel<<<unsigned(pieces), 256, 0, s>>>(ts, fh.off.as<int64_t>(), tw.as<int32_t>(), tc.as<uint64_t>());
-    GT_LAUNCH_CHECK();
-    tv_file_off_kernel<<<1, 256, 0, s>>>(fh.off.as<int64_t>(), fh.nb, d.F, fh.total.as<int64_t>(),
-                                         full_off.as<int64_t>());
-    GT_LAUNCH_CHECK();
-    Buf k0(ctx, size_t(nb_) * 8, s), k1(ctx, size_t(nb_) * 8, s), i0(ctx, size_t(nb_) * 4, s), i1(ctx, size_t(nb_) * 4, s);
-    Buf rs(ctx, radix_scratch_bytes(nb_, true, 4), s);
-    Buf kc(ctx, size_t(d.F) * 8 + 8, s), sc(ctx, scan_scratch_bytes(d.F + 1), s);
-    if (nb_ > 0) {
-      topk_keys_kernel<<<grid_for(nb_, threads, cap), threads, 0, s>>>(tw.as<int32_t>(), tc.as<uint64_t>(),
-                                                                        full_off.as<int64_t>(), d.F, nb_,
-                                                                        k0.as<uint64_t>(), i0.as<uint32_t>());
-      GT_LAUNCH_CHECK();
-      radix_sort_u64(k0.as<uint64_t>(), k1.as<uint64_t>(), i0.p, i1.p, 4, nb_, 0, 32 + bits_for(d.F), rs.p, s);
-    }
-    topk_count_kernel<<<1, 256, 0, s>>>(full_off.as<int64_t>(), d.F, top_k, kc.as<int64_t>());
-    GT_LAUNCH_CHECK();
-    GT_CUDA(cudaMemsetAsync(kc.as<int64_t>() + d.F, 0, 8, s));
-    exclusive_scan_i64(kc.as<int64_t>(), tv_off, d.F + 1, sc.p, s);
-    const int64_t kb = std::min<int64_t>(int64_t(top_k) * d.F, nb_);
-    auto* kw = static_cast<int32_t*>(rb.alloc(size_t(kb) * 4));
-    auto* kcnt = static_cast<uint64_t*>(rb.alloc(size_t(kb) * 8));
-    int64_t* len = rb.new_len_slot();
-    topk_gather_kernel<<<std::max(1, std::min(d.F, cap)), 256, 0, s>>>(i1.as<uint32_t>(), full_off.as<int64_t>(),
-                                                                       tv_off, d.F, tw.as<int32_t>(),
-                                                                       tc.as<uint64_t>(), kw, kcnt);
-    GT_LAUNCH_CHECK();
-    GT_CUDA(cudaMemcpyAsync(len, tv_off + d.F, 8, cudaMemcpyDeviceToDevice, s));
-    rb.field("offsets", tv_off, int64_t(d.F) + 1);
-    rb.field_dyn("word", kw, len);
-    rb.field_dyn("count", kcnt, len);
-  }
+  auto* word = static_cast<int32_t*>(rb.alloc(size_t(nb_) * 4));
+  auto* cnt = static_cast<uint64_t*>(rb.alloc(size_t(nb_) * 8));
+  int64_t* len = rb.new_len_slot();
+  tv_gather_kernel<<<unsigned(pieces), 256, 0, s>>>(ts, fh.off.as<int64_t>(), word, cnt);
+  GT_LAUNCH_CHECK();
+  tv_file_off_kernel<<<1, 256, 0, s>>>(fh.off.as<int64_t>(), fh.nb, d.F, fh.total.as<int64_t>(), tv_off);
+  GT_LAUNCH_CHECK();
+  GT_CUDA(cudaMemcpyAsync(len, fh.total.p, 8, cudaMemcpyDeviceToDevice, s));
+  rb.field("offsets", tv_off, int64_t(d.F) + 1);
+  rb.field_dyn("word", word, len);
+  rb.field_dyn("count", cnt, len);
   GT_CUDA(cudaMemcpyAsync(rb.status(), ctx->d_status, 4, cudaMemcpyDeviceToDevice, s));
   return rb.finish();
 }
@@ -764,6 +742,7 @@ __global__ void tv_rows_kernel(const int32_t* __restrict__ word, const int64_t* 
 }  // namespace
 
 gt_result* run_ranked_words(gt_grammar* g, cudaStream_t s) {
+  if (file_strategy(g) == 2) return run_ranked_words_bu(g, s);
   gt_ctx* ctx = g->ctx;
   const DevGrammar& d = g->d;
   const int threads = 256, cap = ctx->num_sms * 16;
@@ -785,8 +764,73 @@ gt_result* run_ranked_words(gt_grammar* g, cudaStream_t s) {
   return ranked_from_rows(ctx, rkey, rfile, tc, fh.total.as<int64_t>(), bound, 0, false, uint64_t(d.V), s);
 }
 
+__global__ void copy_rows_kernel(const int32_t* __restrict__ w, const uint64_t* __restrict__ c,
+                                 const int64_t* __restrict__ n_dev, int32_t* __restrict__ ow,
+                                 uint64_t* __restrict__ oc) {
+  const int64_t n = *n_dev;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    ow[i] = w[i];
+    oc[i] = c[i];
+  }
+}
+
+// Term-vector result from (word, count) rows in (file, word) order with file
+// offsets; top_k > 0 keeps each file's top_k counts (count desc, word asc).
+gt_result* tv_from_arrays(gt_ctx* ctx, const int32_t* word, const uint64_t* cnt, const int64_t* tv_off_in,
+                          const int64_t* total, int64_t bound, int32_t F, int top_k, cudaStream_t s) {
+  const int threads = 256, cap = ctx->num_sms * 16;
+  ResultBuilder rb(ctx, s);
+  Phase ph(ctx, "tv_out", s);
+  auto* tv_off = static_cast<int64_t*>(rb.alloc(size_t(F + 1) * 8));
+  if (top_k <= 0) {
+    auto* ow = static_cast<int32_t*>(rb.alloc(size_t(bound) * 4));
+    auto* oc = static_cast<uint64_t*>(rb.alloc(size_t(bound) * 8));
+    int64_t* len = rb.new_len_slot();
+    GT_CUDA(cudaMemcpyAsync(tv_off, tv_off_in, size_t(F + 1) * 8, cudaMemcpyDeviceToDevice, s));
+    GT_CUDA(cudaMemcpyAsync(len, total, 8, cudaMemcpyDeviceToDevice, s));
+    if (bound > 0) {
+      copy_rows_kernel<<<grid_for(bound, threads, cap), threads, 0, s>>>(word, cnt, total, ow, oc);
+      GT_LAUNCH_CHECK();
+    }
+    rb.field("offsets", tv_off, int64_t(F) + 1);
+    rb.field_dyn("word", ow, len);
+    rb.field_dyn("count", oc, len);
+  } else {
+    Buf k0(ctx, size_t(bound) * 8, s), k1(ctx, size_t(bound) * 8, s), i0(ctx, size_t(bound) * 4, s);
+    Buf i1(ctx, size_t(bound) * 4, s), rs(ctx, radix_scratch_bytes(bound, true, 4), s);
+    Buf kc(ctx, size_t(F) * 8 + 8, s), sc(ctx, scan_scratch_bytes(F + 1), s);
+    if (bound > 0) {
+      topk_keys_kernel<<<grid_for(bound, threads, cap), threads, 0, s>>>(word, cnt, tv_off_in, F, bound,
+                                                                          k0.as<uint64_t>(), i0.as<uint32_t>());
+      GT_LAUNCH_CHECK();
+      radix_sort_u64(k0.as<uint64_t>(), k1.as<uint64_t>(), i0.p, i1.p, 4, bound, 0, 32 + bits_for(F), rs.p, s);
+    }
+    topk_count_kernel<<<grid_for(F, 256, cap), 256, 0, s>>>(tv_off_in, F, top_k, kc.as<int64_t>());
+    GT_LAUNCH_CHECK();
+    GT_CUDA(cudaMemsetAsync(kc.as<int64_t>() + F, 0, 8, s));
+    exclusive_scan_i64(kc.as<int64_t>(), tv_off, F + 1, sc.p, s);
+    const int64_t kb = std::min<int64_t>(int64_t(top_k) * F, bound);
+    auto* kw = static_cast<int32_t*>(rb.alloc(size_t(kb) * 4));
+    auto* kcnt = static_cast<uint64_t*>(rb.alloc(size_t(kb) * 8));
+    int64_t* len = rb.new_len_slot();
+    topk_gather_kernel<<<std::max(1, std::min(F, cap)), 256, 0, s>>>(i1.as<uint32_t>(), tv_off_in, tv_off, F, word,
+                                                                     cnt, kw, kcnt);
+    GT_LAUNCH_CHECK();
+    GT_CUDA(cudaMemcpyAsync(len, tv_off + F, 8, cudaMemcpyDeviceToDevice, s));
+    rb.field("offsets", tv_off, int64_t(F) + 1);
+    rb.field_dyn("word", kw, len);
+    rb.field_dyn("count", kcnt, len);
+  }
+  GT_CUDA(cudaMemcpyAsync(rb.status(), ctx->d_status, 4, cudaMemcpyDeviceToDevice, s));
+  return rb.finish();
+}
+
 void run_file_batch(gt_grammar* g, const int* tv_topk, int n_tv, gt_result** tv_out, gt_result** ii_out,
                     cudaStream_t s) {
+  if (file_strategy(g) == 2) {
+    run_file_batch_bu(g, tv_topk, n_tv, tv_out, ii_out, s);
+    return;
+  }
   FileHist fh;
   file_hist(g, s, fh);
   for (int i = 0; i < n_tv; ++i) tv_out[i] = term_vector_from(g, fh, tv_topk[i], s);

@@ -177,6 +177,8 @@ struct gt_grammar {
   int64_t fentry_bound = 0;       // (rule, file) pairs with a nonzero per-file weight (<= 64 files)
   int64_t fword_bound = 0;        // rule words emitted once per such pair
   int64_t fsym_bound = 0;         // rule body symbols visited once per such pair
+  int64_t bu_words = 0;           // sum over distinct (file, root child) pairs of the child's length
+  int64_t bu_windows = 0;         // ... and of the child's 3-word windows
   std::vector<void*> owned;      // device allocations to free with the grammar
   // word-count launch sequences captured as CUDA graphs, keyed by output buffer
   struct WcGraph {
@@ -338,6 +340,32 @@ void csr_offsets_hi(const uint64_t* keys, int64_t n, int64_t nh, int64_t* off, c
 void run_rule_weights(gt_grammar* g, uint64_t* d_wt, cudaStream_t s);
 void run_word_count(gt_grammar* g, const uint64_t* d_wt, uint64_t* d_counts, cudaStream_t s);
 void run_head_tail(gt_grammar* g, int32_t* d_head, int32_t* d_tail, cudaStream_t s);
+
+// Sorted 3-word window rows: compact keys (kb bits per word, key_pad above
+// every real key), optional file keys, weights; n rows including pads.
+struct Windows {
+  Buf keys, fkeys, vals;
+  int64_t n = 0;
+  int kb = 1;
+  uint64_t key_pad = 0;
+};
+
+// per-file strategy: 1 top-down (file masks, <= 64 files), 2 bottom-up
+// (expansion of each distinct (file, root child) pair); "file_strategy" 0 = auto
+int file_strategy(const gt_grammar* g);
+
+// gt_seq.cu
+void sort_by_file_key(gt_ctx* ctx, Buf& k0, Buf& f0, Buf& v0, int64_t bound, int key_bits, int file_bits,
+                      cudaStream_t s, Windows& out);
+
+// gt_bu.cu: bottom-up per-file rows
+void bu_window_rows(gt_grammar* g, Buf& head, Buf& tail, int kb, uint64_t key_pad, cudaStream_t s, Windows& out);
+void run_file_batch_bu(gt_grammar* g, const int* tv_topk, int n_tv, gt_result** tv_out, gt_result** ii_out,
+                       cudaStream_t s);
+gt_result* run_ranked_words_bu(gt_grammar* g, cudaStream_t s);
+// gt_file.cu: term-vector result from (word, count) rows in (file, word) order
+gt_result* tv_from_arrays(gt_ctx* ctx, const int32_t* word, const uint64_t* cnt, const int64_t* tv_off_in,
+                          const int64_t* total, int64_t bound, int32_t F, int top_k, cudaStream_t s);
 
 // gt_seq.cu: sequence count (l = 3) and ranked inverted index
 gt_result* run_sequence_count(gt_grammar* g, int per_file, cudaStream_t s);

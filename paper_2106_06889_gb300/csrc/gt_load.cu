@@ -320,6 +320,26 @@ __global__ void sym_rule_kernel(const int64_t* __restrict__ rule_off, int32_t R,
   }
 }
 
+// Sizes for the bottom-up per-file path: over every distinct (file, child)
+// root pair, the child's expansion length and its number of 3-word windows.
+__global__ void bu_sizes_kernel(const int32_t* __restrict__ redge_child, int64_t ER, const uint64_t* __restrict__ L,
+                                unsigned long long* __restrict__ out) {
+  unsigned long long a = 0, b = 0;
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < ER; e += int64_t(gridDim.x) * blockDim.x) {
+    const uint64_t l = L[redge_child[e]];
+    a += l;
+    b += l >= 2 ? l - 2 : 0;
+  }
+  for (int o = 16; o; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&out[0], a);
+    atomicAdd(&out[1], b);
+  }
+}
+
 __global__ void tile_rule_kernel(const int64_t* __restrict__ rule_off, int32_t R, int64_t G, int64_t ntiles,
                                  int32_t* __restrict__ tile_rule) {
   for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t <= ntiles; t += int64_t(gridDim.x) * blockDim.x) {
@@ -634,6 +654,20 @@ void load_build_dag(gt_grammar* g, cudaStream_t s) {
     g->info.root_words = int64_t(hv[2]);
     g->info.owned_windows = int64_t(hv[0] + hv[5]);
     GT_CUDA(cudaStreamSynchronize(s));
+  }
+
+  // ---- sizes of the bottom-up per-file rows ----
+  {
+    GT_CUDA(cudaMemsetAsync(ctr + 12, 0, 16, s));
+    if (d.ER > 0) {
+      bu_sizes_kernel<<<grid_for(d.ER, threads, cap), threads, 0, s>>>(d.redge_child, d.ER, d.exp_len, ctr + 12);
+      GT_LAUNCH_CHECK();
+    }
+    unsigned long long hb[2];
+    GT_CUDA(cudaMemcpyAsync(hb, ctr + 12, 16, cudaMemcpyDeviceToHost, s));
+    GT_CUDA(cudaStreamSynchronize(s));
+    g->bu_words = int64_t(hb[0]);
+    g->bu_windows = int64_t(hb[1]);
   }
 
   // ---- tiles ----

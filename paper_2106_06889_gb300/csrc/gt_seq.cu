@@ -25,61 +25,6 @@
 namespace gt {
 namespace {
 
-struct Sym3 {
-  int32_t first, second, second_last, last;  // -1 where the expansion is too short
-};
-
-__device__ __forceinline__ Sym3 sym_words(const DevGrammar& d, const int32_t* __restrict__ head,
-                                          const int32_t* __restrict__ tail, int32_t x) {
-  Sym3 r;
-  if (x < d.V) {
-    r.first = r.last = x;
-    r.second = r.second_last = -1;
-  } else {
-    const int32_t c = x - d.V;
-    r.first = head[2 * c];
-    r.second = head[2 * c + 1];
-    r.second_last = tail[2 * c];
-    r.last = tail[2 * c + 1];
-  }
-  return r;
-}
-
-__device__ __forceinline__ uint64_t pack_compact(int32_t a, int32_t b, int32_t c, int kb) {
-  return (uint64_t(uint32_t(a)) << (2 * kb)) | (uint64_t(uint32_t(b)) << kb) | uint64_t(uint32_t(c));
-}
-
-// End (exclusive) of the body sequence holding position j: the file's end in
-// the root, the rule's end elsewhere.  Also returns the rule.
-__device__ __forceinline__ int64_t seq_end(const DevGrammar& d, int64_t j, int32_t* rule, int32_t* file) {
-  if (j < d.root_len) {
-    const int64_t f = upper_bound_dev(d.file_off, int64_t(d.F) + 1, j) - 1;
-    *rule = 0;
-    *file = int32_t(f);
-    return d.file_off[f + 1];
-  }
-  const int32_t r = d.sym_rule[j - d.first_rule_tile * kTile];
-  *rule = r;
-  *file = -1;
-  return d.rule_off[r + 1];
-}
-
-// The (at most two) owned windows starting in body symbol j; returns how many.
-__device__ __forceinline__ int windows_at(const DevGrammar& d, const int32_t* __restrict__ head,
-                                          const int32_t* __restrict__ tail, int64_t j, int64_t end, int kb,
-                                          uint64_t* k) {
-  if (j + 1 >= end) return 0;
-  const Sym3 a = sym_words(d, head, tail, d.sym[j]);
-  const Sym3 b = sym_words(d, head, tail, d.sym[j + 1]);
-  const int32_t n1 = b.first;
-  int32_t n2 = b.second;
-  if (n2 < 0) n2 = j + 2 < end ? sym_words(d, head, tail, d.sym[j + 2]).first : -1;
-  int n = 0;
-  if (a.second_last >= 0) k[n++] = pack_compact(a.second_last, a.last, n1, kb);  // child with >= 2 words
-  if (n2 >= 0) k[n++] = pack_compact(a.last, n1, n2, kb);
-  return n;
-}
-
 // Global counts: two key slots per body position (kNoKey where unused),
 // weighted by the rule's top-down weight.
 __global__ void win_emit_kernel(DevGrammar d, const int32_t* __restrict__ head, const int32_t* __restrict__ tail,
@@ -265,14 +210,41 @@ void reduce_rows(gt_ctx* ctx, uint64_t* keys, uint64_t* fkeys, uint32_t* vals, i
   GT_LAUNCH_CHECK();
 }
 
-// Windows of the whole corpus, sorted: keys (compact packing), optional file
-// keys, weights.  Returns the number of (padded) rows.
-struct Windows {
-  Buf keys, fkeys, vals;
-  int64_t n = 0;
-  int kb = 1;
-  uint64_t key_pad = 0;
-};
+}  // namespace
+
+void sort_by_file_key(gt_ctx* ctx, Buf& k0, Buf& f0, Buf& v0, int64_t bound, int key_bits, int file_bits,
+                      cudaStream_t s, Windows& out) {
+  const int threads = 256, cap = ctx->num_sms * 16;
+  out.keys = Buf(ctx, size_t(bound) * 8, s);
+  out.fkeys = Buf(ctx, size_t(bound) * 8, s);
+  out.vals = Buf(ctx, size_t(bound) * 4, s);
+  out.n = bound;
+  if (bound == 0) return;
+  Phase ph2(ctx, "seq_sort", s);
+  Buf pin(ctx, size_t(bound) * 4, s), pkey(ctx, size_t(bound) * 4, s), pfile(ctx, size_t(bound) * 4, s);
+  Buf k1(ctx, size_t(bound) * 8, s), fk(ctx, size_t(bound) * 8, s), comp(ctx, size_t(bound) * 4, s);
+  Buf rs(ctx, radix_scratch_bytes(bound, true, 4), s);
+  iota_kernel<<<grid_for(bound, threads, cap), threads, 0, s>>>(pin.as<uint32_t>(), bound);
+  GT_LAUNCH_CHECK();
+  radix_sort_u64(k0.as<uint64_t>(), k1.as<uint64_t>(), pin.p, pkey.p, 4, bound, 0, key_bits, rs.p, s);
+  gather_u64_kernel<<<grid_for(bound, threads, cap), threads, 0, s>>>(f0.as<uint64_t>(), pkey.as<uint32_t>(), bound,
+                                                                       fk.as<uint64_t>());
+  GT_LAUNCH_CHECK();
+  iota_kernel<<<grid_for(bound, threads, cap), threads, 0, s>>>(pin.as<uint32_t>(), bound);
+  GT_LAUNCH_CHECK();
+  radix_sort_u64(fk.as<uint64_t>(), out.fkeys.as<uint64_t>(), pin.p, pfile.p, 4, bound, 0, file_bits, rs.p, s);
+  gather_u64_kernel<<<grid_for(bound, threads, cap), threads, 0, s>>>(k1.as<uint64_t>(), pfile.as<uint32_t>(), bound,
+                                                                       out.keys.as<uint64_t>());
+  GT_LAUNCH_CHECK();
+  gather_u32_kernel<<<grid_for(bound, threads, cap), threads, 0, s>>>(pkey.as<uint32_t>(), pfile.as<uint32_t>(), bound,
+                                                                       comp.as<uint32_t>());
+  GT_LAUNCH_CHECK();
+  gather_u32_kernel<<<grid_for(bound, threads, cap), threads, 0, s>>>(v0.as<uint32_t>(), comp.as<uint32_t>(), bound,
+                                                                       out.vals.as<uint32_t>());
+  GT_LAUNCH_CHECK();
+}
+
+namespace {
 
 void sorted_windows(gt_grammar* g, bool per_file, cudaStream_t s, Windows& out) {
   gt_ctx* ctx = g->ctx;
@@ -310,16 +282,19 @@ void sorted_windows(gt_grammar* g, bool per_file, cudaStream_t s, Windows& out) 
     radix_sort_u64(k0.as<uint64_t>(), out.keys.as<uint64_t>(), v0.p, out.vals.p, 4, n, 0, key_bits, rs.p, s);
     return;
   }
-  // ---- per file: count, scan, emit (windows x files of the rule) ----
+  if (file_strategy(g) == 2) {
+    bu_window_rows(g, head, tail, kb, out.key_pad, s, out);
+    return;
+  }
+  // ---- per file, top-down: count, scan, emit (windows x files of the rule) ----
   Phase ph(ctx, "seq_emit", s);
   FileWeights fw;
   file_weights(g, s, fw);
   const int64_t bound = 2 * d.root_len + 2 * g->fsym_bound;
-  out.n = bound;
-  out.keys = Buf(ctx, size_t(bound) * 8, s);
-  out.fkeys = Buf(ctx, size_t(bound) * 8, s);
-  out.vals = Buf(ctx, size_t(bound) * 4, s);
-  if (bound == 0) return;
+  if (bound == 0) {
+    out.n = 0;
+    return;
+  }
   Buf cnt(ctx, size_t(d.G) * 8, s), pos(ctx, size_t(d.G) * 8, s), sc(ctx, scan_scratch_bytes(d.G), s), nd(ctx, 8, s);
   GT_CUDA(cudaMemsetAsync(nd.p, 0, 8, s));
   Buf k0(ctx, size_t(bound) * 8, s), f0(ctx, size_t(bound) * 8, s), v0(ctx, size_t(bound) * 4, s);
@@ -339,29 +314,7 @@ void sorted_windows(gt_grammar* g, bool per_file, cudaStream_t s, Windows& out) 
                                                                      v0.as<uint32_t>(), nd.as<int64_t>(), bound,
                                                                      out.key_pad, uint64_t(d.F));
   GT_LAUNCH_CHECK();
-  // ---- order by (file, key): sort by key, then stably by file ----
-  Phase ph2(ctx, "seq_sort", s);
-  Buf pin(ctx, size_t(bound) * 4, s), pkey(ctx, size_t(bound) * 4, s), pfile(ctx, size_t(bound) * 4, s);
-  Buf k1(ctx, size_t(bound) * 8, s), fk(ctx, size_t(bound) * 8, s), comp(ctx, size_t(bound) * 4, s);
-  Buf rs(ctx, radix_scratch_bytes(bound, true, 4), s);
-  iota_kernel<<<grid_for(bound, threads, cap), threads, 0, s>>>(pin.as<uint32_t>(), bound);
-  GT_LAUNCH_CHECK();
-  radix_sort_u64(k0.as<uint64_t>(), k1.as<uint64_t>(), pin.p, pkey.p, 4, bound, 0, key_bits, rs.p, s);
-  gather_u64_kernel<<<grid_for(bound, threads, cap), threads, 0, s>>>(f0.as<uint64_t>(), pkey.as<uint32_t>(), bound,
-                                                                       fk.as<uint64_t>());
-  GT_LAUNCH_CHECK();
-  iota_kernel<<<grid_for(bound, threads, cap), threads, 0, s>>>(pin.as<uint32_t>(), bound);
-  GT_LAUNCH_CHECK();
-  radix_sort_u64(fk.as<uint64_t>(), out.fkeys.as<uint64_t>(), pin.p, pfile.p, 4, bound, 0, bits_for(d.F), rs.p, s);
-  gather_u64_kernel<<<grid_for(bound, threads, cap), threads, 0, s>>>(k1.as<uint64_t>(), pfile.as<uint32_t>(), bound,
-                                                                       out.keys.as<uint64_t>());
-  GT_LAUNCH_CHECK();
-  gather_u32_kernel<<<grid_for(bound, threads, cap), threads, 0, s>>>(pkey.as<uint32_t>(), pfile.as<uint32_t>(), bound,
-                                                                       comp.as<uint32_t>());
-  GT_LAUNCH_CHECK();
-  gather_u32_kernel<<<grid_for(bound, threads, cap), threads, 0, s>>>(v0.as<uint32_t>(), comp.as<uint32_t>(), bound,
-                                                                       out.vals.as<uint32_t>());
-  GT_LAUNCH_CHECK();
+  sort_by_file_key(ctx, k0, f0, v0, bound, key_bits, bits_for(d.F), s, out);
 }
 
 __global__ void rank_keys_kernel(const uint64_t* __restrict__ cnt, const int64_t* __restrict__ n_dev, int64_t bound,

@@ -73,6 +73,10 @@ size_t query_footprint(const gt_grammar* g, int kind) {
   const double R = d.R, V = d.V, F = d.F, N = double(d.N);
   const double nb = std::ceil(V / 16384.0);
   double b = 0;
+  if (file_strategy(g) == 2 && kind >= GT_Q_INVERTED_INDEX) {  // bottom-up rows: keys, sort, reduce
+    const double rows = std::max(double(d.root_len + g->bu_words), 2.0 * double(d.root_len) + double(g->bu_windows));
+    return size_t(128 * rows + 24 * V) + (size_t(64) << 20);
+  }
   switch (kind) {
     case GT_Q_WORD_COUNT:
     case GT_Q_SORT:

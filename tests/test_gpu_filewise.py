@@ -69,18 +69,6 @@ def test_inverted_index(ctx, name, g):
     B.gt_free_grammar(gh)
 
 
-def test_too_many_files_reported(ctx):
-    rng = np.random.default_rng(2)
-    toks = rng.integers(0, 50, size=2000).astype(np.int32)
-    lens = np.full(100, 20, np.int64)
-    g = sequitur(toks, lens, 50)
-    gh = B.gt_load_grammar(ctx, g)
-    with pytest.raises(B.GtError) as e:
-        B.gt_term_vector(gh, 0)
-    assert e.value.code == 6  # GT_EOVERFLOW: more than 64 files needs the bottom-up strategy
-    B.gt_free_grammar(gh)
-
-
 def test_full_size_multifile_tv_ii(ctx):
     """64 files, ~50M tokens (the benchmark's corpus): the whole term vector
     and inverted index equal the oracle's."""
