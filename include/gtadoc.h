@@ -128,6 +128,21 @@ gt_status gt_rule_weights(gt_grammar* g, uint64_t* d_weights, void* stream);
  * graph once the same buffer has been used before (see "use_graphs"). */
 gt_status gt_word_count(gt_grammar* g, uint64_t* d_counts, void* stream);
 
+/* Word count that allocates no device memory: same result as gt_word_count
+ * (bit-identical counts), for callers that cannot allocate at the time of the
+ * call.  The paper has no counterpart.  Its only scratch, one uint64 weight
+ * per rule, is a fixed library-owned device array of 4,194,304 entries
+ * (32 MiB); a grammar with more rules is rejected with GT_EOVERFLOW (use
+ * gt_word_count).  The call clears d_counts and the scratch itself.
+ * d_counts: device uint64[num_words], written entirely.
+ * The scratch array's address is looked up on the first call on a device;
+ * make that first call outside any stream capture.  Every call on a device
+ * shares the one scratch array: calls that may overlap on the device
+ * (different streams with no ordering between them) race and give wrong
+ * counts; calls on one stream, or ordered by events, are safe.  Slower than
+ * gt_word_count (global atomics instead of shared-memory histograms). */
+gt_status gt_word_count_noalloc(gt_grammar* g, uint64_t* d_counts, void* stream);
+
 /* Sort: the distinct words with their counts.  order 0: ascending word ID;
  * order 1: descending count, ties by ascending word ID.
  * Result fields: "word" int32[n], "count" uint64[n]. */

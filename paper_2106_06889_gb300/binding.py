@@ -67,6 +67,7 @@ def lib() -> ctypes.CDLL:
             "gt_grammar_info_get": [_P, ctypes.POINTER(gt_grammar_info)],
             "gt_rule_weights": [_P, _P, _P],
             "gt_word_count": [_P, _P, _P],
+            "gt_word_count_noalloc": [_P, _P, _P],
             "gt_sort": [_P, ctypes.c_int, _P, ctypes.POINTER(_P)],
             "gt_inverted_index": [_P, _P, ctypes.POINTER(_P)],
             "gt_term_vector": [_P, ctypes.c_int, _P, ctypes.POINTER(_P)],
@@ -207,6 +208,10 @@ def gt_rule_weights(g: GrammarHandle, d_weights, stream=None) -> None:
 
 def gt_word_count(g: GrammarHandle, d_counts, stream=None) -> None:
     _check(lib().gt_word_count(g.handle, _dptr(d_counts), _stream(stream)), g.ctx.handle)
+
+
+def gt_word_count_noalloc(g: GrammarHandle, d_counts, stream=None) -> None:
+    _check(lib().gt_word_count_noalloc(g.handle, _dptr(d_counts), _stream(stream)), g.ctx.handle)
 
 
 def gt_head_tail(g: GrammarHandle, d_head, d_tail, stream=None) -> None:
