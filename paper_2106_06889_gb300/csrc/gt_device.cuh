@@ -166,10 +166,13 @@ __device__ __forceinline__ int windows_at(const DevGrammar& d, const int32_t* __
   const int32_t n1 = b.first;
   int32_t n2 = b.second;
   if (n2 < 0) n2 = j + 2 < end ? sym_words(d, head, tail, d.sym[j + 2]).first : -1;
-  int n = 0;
-  if (a.second_last >= 0) k[n++] = pack_compact(a.second_last, a.last, n1, kb);  // child with >= 2 words
-  if (n2 >= 0) k[n++] = pack_compact(a.last, n1, n2, kb);
-  return n;
+  // k[0], k[1] are always written (fixed indices keep them in registers)
+  const bool w0 = a.second_last >= 0;  // child with >= 2 words
+  const uint64_t x0 = w0 ? pack_compact(a.second_last, a.last, n1, kb) : 0;
+  const uint64_t x1 = n2 >= 0 ? pack_compact(a.last, n1, n2, kb) : 0;
+  k[0] = w0 ? x0 : x1;
+  k[1] = x1;
+  return int(w0) + int(n2 >= 0);
 }
 
 }  // namespace gt

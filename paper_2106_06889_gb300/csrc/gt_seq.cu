@@ -25,22 +25,102 @@
 namespace gt {
 namespace {
 
-// Global counts: two key slots per body position (kNoKey where unused),
-// weighted by the rule's top-down weight.
-__global__ void win_emit_kernel(DevGrammar d, const int32_t* __restrict__ head, const int32_t* __restrict__ tail,
-                                const uint64_t* __restrict__ wt, int kb, uint64_t key_pad,
-                                uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
-  for (int64_t j = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; j < d.G; j += int64_t(gridDim.x) * blockDim.x) {
-    int32_t r, f;
-    const int64_t end = seq_end(d, j, &r, &f);
-    uint64_t k[2];
-    const int n = windows_at(d, head, tail, j, end, kb, k);
-    const uint32_t w = uint32_t(wt[r]);  // 0 for a rule nothing references: no rows
-    keys[2 * j] = (n > 0 && w) ? k[0] : key_pad;
-    keys[2 * j + 1] = (n > 1 && w) ? k[1] : key_pad;
-    vals[2 * j] = w;
-    vals[2 * j + 1] = w;
+// Global counts, compacted: every owned window gets one row, in body
+// position order.  One CTA per tile of kTile symbols (4 per thread); pass 1
+// counts the windows of each tile, an exclusive scan over tiles gives each
+// tile its first row, and pass 2 ranks the windows inside the tile.
+constexpr int kWinThreads = kTile / 4;
+
+// Windows of the 4 symbols j0 .. j0+3: symbol i has n[i] of them, keys
+// k[i][0..n[i]), owner rule r[i].
+struct TileWin {
+  uint64_t k[4][2];
+  int32_t r[4];
+  int n[4];
+};
+
+__device__ __forceinline__ int tile_windows(const DevGrammar& d, const int32_t* __restrict__ head,
+                                            const int32_t* __restrict__ tail, int kb, int64_t j0, TileWin& t) {
+  int c = 0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int64_t j = j0 + i;
+    t.n[i] = 0;
+    t.r[i] = 0;
+    if (j < d.G) {
+      int32_t f;
+      const int64_t end = seq_end(d, j, &t.r[i], &f);
+      t.n[i] = windows_at(d, head, tail, j, end, kb, t.k[i]);
+    }
+    c += t.n[i];
   }
+  return c;
+}
+
+// Exclusive prefix of v over the CTA (kWinThreads threads); *total gets the sum.
+__device__ __forceinline__ int cta_excl_scan(int v, int* total) {
+  __shared__ int warp_tot[kWinThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) warp_tot[warp] = incl;
+  __syncthreads();
+  int before = 0, all = 0;
+#pragma unroll
+  for (int w = 0; w < kWinThreads / 32; ++w) {
+    const int t = warp_tot[w];
+    before += w < warp ? t : 0;
+    all += t;
+  }
+  __syncthreads();
+  *total = all;
+  return before + incl - v;
+}
+
+__global__ void __launch_bounds__(kWinThreads) win_tile_count_kernel(DevGrammar d, const int32_t* __restrict__ head,
+                                                                     const int32_t* __restrict__ tail, int kb,
+                                                                     int64_t* __restrict__ tile_cnt) {
+  TileWin t;
+  const int c = tile_windows(d, head, tail, kb, int64_t(blockIdx.x) * kTile + threadIdx.x * 4, t);
+  int total;
+  cta_excl_scan(c, &total);
+  if (threadIdx.x == 0) tile_cnt[blockIdx.x] = total;
+}
+
+// Rows of rules nothing references (weight 0) get the pad key.  Rows past
+// `bound` are not written; the status word records it.
+__global__ void __launch_bounds__(kWinThreads) win_emit_kernel(DevGrammar d, const int32_t* __restrict__ head,
+                                                               const int32_t* __restrict__ tail,
+                                                               const uint64_t* __restrict__ wt, int kb,
+                                                               uint64_t key_pad, const int64_t* __restrict__ tile_off,
+                                                               int64_t bound, uint64_t* __restrict__ keys,
+                                                               uint32_t* __restrict__ vals,
+                                                               unsigned* __restrict__ status) {
+  TileWin t;
+  const int c = tile_windows(d, head, tail, kb, int64_t(blockIdx.x) * kTile + threadIdx.x * 4, t);
+  int total;
+  int64_t pos = tile_off[blockIdx.x] + cta_excl_scan(c, &total);
+  bool over = false;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const uint32_t w = t.n[i] ? uint32_t(wt[t.r[i]]) : 0u;
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+      if (q < t.n[i]) {
+        if (pos < bound) {
+          keys[pos] = w ? t.k[i][q] : key_pad;
+          vals[pos] = w;
+        } else {
+          over = true;
+        }
+        ++pos;
+      }
+  }
+  if (over) atomicOr(status, ST_OVERFLOW);
 }
 
 // Per-file counts, pass 1: entries produced at each position (windows x files).
@@ -262,7 +342,9 @@ void sorted_windows(gt_grammar* g, bool per_file, cudaStream_t s, Windows& out) 
     run_head_tail(g, head.as<int32_t>(), tail.as<int32_t>(), s);
   }
   if (!per_file) {
-    const int64_t n = 2 * d.G;
+    // exactly the owned windows (Eq. 1's count, known since load); the pad
+    // key fills any rows the emit pass leaves
+    const int64_t n = g->info.owned_windows;
     Buf k0(ctx, size_t(n) * 8, s), v0(ctx, size_t(n) * 4, s);
     out.keys = Buf(ctx, size_t(n) * 8, s);
     out.vals = Buf(ctx, size_t(n) * 4, s);
@@ -272,9 +354,19 @@ void sorted_windows(gt_grammar* g, bool per_file, cudaStream_t s, Windows& out) 
       Phase ph(ctx, "seq_emit", s);
       Buf wt(ctx, size_t(d.R) * 8, s);
       run_rule_weights(g, wt.as<uint64_t>(), s);
-      win_emit_kernel<<<grid_for(d.G, threads, cap), threads, 0, s>>>(d, head.as<int32_t>(), tail.as<int32_t>(),
-                                                                       wt.as<uint64_t>(), kb, out.key_pad,
-                                                                       k0.as<uint64_t>(), v0.as<uint32_t>());
+      const int64_t nt = d.ntiles;
+      Buf tcnt(ctx, size_t(nt + 1) * 8, s), toff(ctx, size_t(nt + 1) * 8, s), tsc(ctx, scan_scratch_bytes(nt + 1), s);
+      GT_CUDA(cudaMemsetAsync(tcnt.as<int64_t>() + nt, 0, 8, s));
+      win_tile_count_kernel<<<unsigned(nt), kWinThreads, 0, s>>>(d, head.as<int32_t>(), tail.as<int32_t>(), kb,
+                                                                  tcnt.as<int64_t>());
+      GT_LAUNCH_CHECK();
+      exclusive_scan_i64(tcnt.as<int64_t>(), toff.as<int64_t>(), nt + 1, tsc.p, s);
+      win_emit_kernel<<<unsigned(nt), kWinThreads, 0, s>>>(d, head.as<int32_t>(), tail.as<int32_t>(),
+                                                            wt.as<uint64_t>(), kb, out.key_pad, toff.as<int64_t>(), n,
+                                                            k0.as<uint64_t>(), v0.as<uint32_t>(), ctx->d_status);
+      GT_LAUNCH_CHECK();
+      pad_tail_kernel<<<grid_for(n, threads, cap), threads, 0, s>>>(k0.as<uint64_t>(), nullptr, v0.as<uint32_t>(),
+                                                                     toff.as<int64_t>() + nt, n, out.key_pad, 0);
       GT_LAUNCH_CHECK();
     }
     Phase ph(ctx, "seq_sort", s);

@@ -3,6 +3,8 @@
 // These back the memory-pool sizing (exclusive scans of per-rule sizes, the
 // "memory pool" of Section IV-B), the edge deduplication at load time and the
 // canonical ordering of every result.
+#include <type_traits>
+
 #include "gt_internal.cuh"
 
 namespace gt {
@@ -87,87 +89,148 @@ __global__ void __launch_bounds__(kScanThreads) scan_apply_kernel(const int64_t*
 
 // ---- radix sort -------------------------------------------------------------
 
-constexpr int kRsThreads = 256;
+constexpr int kRsThreads = 256;  // one thread per digit value in the per-tile bookkeeping
 constexpr int kRsWarps = kRsThreads / 32;
-constexpr int kRsItems = 16;
+constexpr int kRsItems = 8;      // keys per thread; 8 x 256 threads with 4 CTAs per SM measured fastest
 constexpr int kRsTile = kRsThreads * kRsItems;  // keys per tile
 
+// Lanes of the warp holding the same 8-bit digit as this lane (among `active`),
+// from one ballot per digit bit.
+__device__ __forceinline__ unsigned warp_digit_peers(uint32_t d, unsigned active) {
+  unsigned peers = active;
+#pragma unroll
+  for (int b = 0; b < 8; ++b) {
+    const bool bit = (d >> b) & 1u;
+    const unsigned bal = __ballot_sync(0xffffffffu, bit);
+    peers &= bit ? bal : ~bal;
+  }
+  return peers;
+}
+
+// Per-tile digit counts, stored digit-major (hist[d * ntiles + tile]) so that
+// one exclusive scan gives every (digit, tile) its output offset.
 __global__ void __launch_bounds__(kRsThreads) radix_upsweep_kernel(const uint64_t* __restrict__ keys, int64_t n,
                                                                    int shift, uint32_t mask, int64_t ntiles,
                                                                    int64_t* __restrict__ hist) {
-  __shared__ uint32_t h[256];
-  for (int i = threadIdx.x; i < 256; i += kRsThreads) h[i] = 0;
+  __shared__ uint32_t h[kRsWarps][256];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i = threadIdx.x; i < kRsWarps * 256; i += kRsThreads) h[i / 256][i % 256] = 0;
   __syncthreads();
-  const int64_t base = int64_t(blockIdx.x) * kRsTile;
-  for (int i = threadIdx.x; i < kRsTile; i += kRsThreads) {
-    int64_t idx = base + i;
-    if (idx < n) atomicAdd(&h[(keys[idx] >> shift) & mask], 1u);
+  const int64_t wbase = int64_t(blockIdx.x) * kRsTile + int64_t(warp) * 32 * kRsItems;
+#pragma unroll 4
+  for (int it = 0; it < kRsItems; ++it) {
+    const int64_t idx = wbase + it * 32 + lane;
+    const bool valid = idx < n;
+    const uint32_t d = valid ? uint32_t(keys[idx] >> shift) & mask : 0u;
+    const unsigned peers = warp_digit_peers(d, __ballot_sync(0xffffffffu, valid));
+    // the lowest lane of each digit group adds the group; the counters are warp-private
+    if (valid && (peers & ((1u << lane) - 1u)) == 0) h[warp][d] += __popc(peers);
+    __syncwarp();
   }
   __syncthreads();
-  for (int d = threadIdx.x; d < 256; d += kRsThreads) hist[int64_t(d) * ntiles + blockIdx.x] = h[d];
+  const int d = threadIdx.x;
+  uint32_t t = 0;
+#pragma unroll
+  for (int w = 0; w < kRsWarps; ++w) t += h[w][d];
+  hist[int64_t(d) * ntiles + blockIdx.x] = t;
 }
 
-// Stable scatter: within a tile, keys keep their order because warp w owns the
-// w-th slice of the tile, walks it in order 32 keys at a time, and ranks equal
-// digits within each group of 32 by lane order (__match_any_sync).
+// Stable scatter of one tile.  Warp w owns the w-th slice of the tile and
+// ranks its keys 32 at a time in lane order; per-digit counts across warps
+// and digits give every key its place in the tile sorted by digit.  The tile
+// is rearranged in shared memory in that order and written out with
+// consecutive threads writing consecutive addresses of each digit's run.
+constexpr int kRsMinBlocks = 4;
+
 template <int VB>
-__global__ void __launch_bounds__(kRsThreads) radix_downsweep_kernel(
+__global__ void __launch_bounds__(kRsThreads, kRsMinBlocks) radix_downsweep_kernel(
     const uint64_t* __restrict__ kin, uint64_t* __restrict__ kout, const void* __restrict__ vin,
     void* __restrict__ vout, int64_t n, int shift, uint32_t mask, int64_t ntiles, const int64_t* __restrict__ offs) {
   __shared__ uint32_t wcnt[kRsWarps][256];
+  __shared__ uint32_t dstart[256];
+  __shared__ uint32_t wsum[kRsWarps];
   __shared__ int64_t goff[256];
+  extern __shared__ __align__(16) unsigned char rs_smem[];
+  uint64_t* skey = reinterpret_cast<uint64_t*>(rs_smem);
+  unsigned char* sval = rs_smem + kRsTile * 8;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int i = threadIdx.x; i < kRsWarps * 256; i += kRsThreads) wcnt[i / 256][i % 256] = 0;
-  for (int d = threadIdx.x; d < 256; d += kRsThreads) goff[d] = offs[int64_t(d) * ntiles + blockIdx.x];
+  goff[threadIdx.x] = offs[int64_t(threadIdx.x) * ntiles + blockIdx.x];
   __syncthreads();
   const unsigned lt_mask = (1u << lane) - 1u;
-  const int64_t wbase = int64_t(blockIdx.x) * kRsTile + int64_t(warp) * 32 * kRsItems;
+  const int64_t tbase = int64_t(blockIdx.x) * kRsTile;
+  const int64_t wbase = tbase + int64_t(warp) * 32 * kRsItems;
+  using VT = typename std::conditional<VB == 8, uint64_t, uint32_t>::type;
   uint64_t key[kRsItems];
   uint32_t rank[kRsItems];
-  uint64_t val[kRsItems];
+  VT val[kRsItems];
 #pragma unroll
   for (int it = 0; it < kRsItems; ++it) {
     const int64_t idx = wbase + it * 32 + lane;
     const bool valid = idx < n;
     key[it] = valid ? kin[idx] : 0;
-    if (VB == 4) val[it] = valid ? static_cast<const uint32_t*>(vin)[idx] : 0;
-    if (VB == 8) val[it] = valid ? static_cast<const uint64_t*>(vin)[idx] : 0;
-    const unsigned active = __ballot_sync(0xffffffffu, valid);
-    rank[it] = 0;
-    if (valid) {
-      const uint32_t d = uint32_t(key[it] >> shift) & mask;
-      const unsigned peers = __match_any_sync(active, d);
-      const uint32_t before = wcnt[warp][d];
-      const uint32_t r = __popc(peers & lt_mask);
-      rank[it] = before + r;
-      __syncwarp(active);
-      if (r == 0) wcnt[warp][d] = before + __popc(peers);
-    }
+    val[it] = 0;
+    if (VB != 0 && valid) val[it] = static_cast<const VT*>(vin)[idx];
+    const uint32_t d = uint32_t(key[it] >> shift) & mask;
+    const unsigned peers = warp_digit_peers(d, __ballot_sync(0xffffffffu, valid));
+    const uint32_t before = wcnt[warp][d];
+    const uint32_t r = __popc(peers & lt_mask);
+    rank[it] = before + r;
+    __syncwarp();
+    if (valid && r == 0) wcnt[warp][d] = before + __popc(peers);
     __syncwarp();
   }
   __syncthreads();
-  // exclusive prefix over warps, per digit
-  for (int d = threadIdx.x; d < 256; d += kRsThreads) {
-    uint32_t run = 0;
+  // per digit: exclusive prefix over warps, then exclusive prefix over digits
+  const int dd = threadIdx.x;
+  uint32_t run = 0;
 #pragma unroll
-    for (int w = 0; w < kRsWarps; ++w) {
-      uint32_t c = wcnt[w][d];
-      wcnt[w][d] = run;
-      run += c;
-    }
+  for (int w = 0; w < kRsWarps; ++w) {
+    const uint32_t c = wcnt[w][dd];
+    wcnt[w][dd] = run;
+    run += c;
   }
+  uint32_t incl = run;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) wsum[warp] = incl;
+  __syncthreads();
+  uint32_t wpre = 0;
+#pragma unroll
+  for (int w = 0; w < kRsWarps; ++w) wpre += w < warp ? wsum[w] : 0u;
+  dstart[dd] = wpre + incl - run;
   __syncthreads();
 #pragma unroll
   for (int it = 0; it < kRsItems; ++it) {
     const int64_t idx = wbase + it * 32 + lane;
     if (idx < n) {
       const uint32_t d = uint32_t(key[it] >> shift) & mask;
-      const int64_t pos = goff[d] + wcnt[warp][d] + rank[it];
-      kout[pos] = key[it];
-      if (VB == 4) static_cast<uint32_t*>(vout)[pos] = uint32_t(val[it]);
-      if (VB == 8) static_cast<uint64_t*>(vout)[pos] = val[it];
+      const uint32_t lp = dstart[d] + wcnt[warp][d] + rank[it];
+      skey[lp] = key[it];
+      if (VB != 0) reinterpret_cast<VT*>(sval)[lp] = val[it];
     }
   }
+  __syncthreads();
+  const int tn = int(n - tbase < kRsTile ? n - tbase : kRsTile);
+  for (int i = threadIdx.x; i < tn; i += kRsThreads) {
+    const uint64_t k = skey[i];
+    const uint32_t d = uint32_t(k >> shift) & mask;
+    const int64_t pos = goff[d] + (i - int64_t(dstart[d]));
+    kout[pos] = k;
+    if (VB != 0) static_cast<VT*>(vout)[pos] = reinterpret_cast<const VT*>(sval)[i];
+  }
+}
+
+template <int VB>
+void launch_downsweep(const uint64_t* ka, uint64_t* kb, const void* va, void* vb, int64_t n, int shift, uint32_t mask,
+                      int64_t ntiles, const int64_t* offs, cudaStream_t s) {
+  constexpr size_t smem = size_t(kRsTile) * (8 + VB);
+  GT_CUDA(cudaFuncSetAttribute(radix_downsweep_kernel<VB>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+  radix_downsweep_kernel<VB><<<unsigned(ntiles), kRsThreads, smem, s>>>(ka, kb, va, vb, n, shift, mask, ntiles, offs);
+  GT_LAUNCH_CHECK();
 }
 
 }  // namespace
@@ -221,13 +284,11 @@ void radix_sort_u64(uint64_t* keys_in, uint64_t* keys_out, void* vals_in, void* 
     GT_LAUNCH_CHECK();
     exclusive_scan_i64(hist, offs, m, sscratch, s);
     if (value_bytes == 4)
-      radix_downsweep_kernel<4><<<unsigned(ntiles), kRsThreads, 0, s>>>(ka, kb, va, vb, n, shift, mask, ntiles, offs);
+      launch_downsweep<4>(ka, kb, va, vb, n, shift, mask, ntiles, offs, s);
     else if (value_bytes == 8)
-      radix_downsweep_kernel<8><<<unsigned(ntiles), kRsThreads, 0, s>>>(ka, kb, va, vb, n, shift, mask, ntiles, offs);
+      launch_downsweep<8>(ka, kb, va, vb, n, shift, mask, ntiles, offs, s);
     else
-      radix_downsweep_kernel<0><<<unsigned(ntiles), kRsThreads, 0, s>>>(ka, kb, nullptr, nullptr, n, shift, mask,
-                                                                        ntiles, offs);
-    GT_LAUNCH_CHECK();
+      launch_downsweep<0>(ka, kb, nullptr, nullptr, n, shift, mask, ntiles, offs, s);
     std::swap(ka, kb);
     std::swap(va, vb);
   }
