@@ -320,7 +320,38 @@ __global__ void rule_chunks_kernel(const int64_t* __restrict__ xoff, int32_t F, 
 }
 
 // CTA (f, b): dense histogram of file f's words in bucket b, from the bucket-b
-// runs of f's root chunks and rule-word chunks.
+// runs of f's root chunks and rule-word chunks.  Run descriptors are staged
+// in shared memory a batch at a time, so each warp's next run starts without
+// a dependent global load.
+constexpr int kTvBatch = kTvThreads;
+
+template <typename E>
+__device__ __forceinline__ void tv_runs(uint32_t* hist, int64_t c0, int64_t c1, int nb, int b,
+                                        const int64_t* __restrict__ rs, const int32_t* __restrict__ rl,
+                                        const E* __restrict__ ent, int64_t* s_start, int32_t* s_len) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int64_t cb = c0; cb < c1; cb += kTvBatch) {
+    const int nbatch = int(min(int64_t(kTvBatch), c1 - cb));
+    __syncthreads();  // previous batch consumed
+    if (tid < nbatch) {
+      s_start[tid] = rs[(cb + tid) * nb + b];
+      s_len[tid] = rl[(cb + tid) * nb + b];
+    }
+    __syncthreads();
+    for (int q = warp; q < nbatch; q += kTvThreads / 32) {
+      const int64_t s0 = s_start[q];
+      const int32_t n = s_len[q];
+      for (int i = lane; i < n; i += 32) {
+        const E e = ent[s0 + i];
+        if (sizeof(E) == 2)
+          atomicAdd(&hist[uint32_t(e)], 1u);
+        else
+          atomicAdd(&hist[uint32_t(e) & (kFBucket - 1)], uint32_t(uint64_t(e) >> 16));
+      }
+    }
+  }
+}
+
 __global__ void __launch_bounds__(kTvThreads) tv_hist_kernel(int32_t F, int nb, Chunks rc, const int64_t* __restrict__ rrs,
                                                              const int32_t* __restrict__ rrl,
                                                              const uint16_t* __restrict__ rent, Chunks xc,
@@ -329,43 +360,34 @@ __global__ void __launch_bounds__(kTvThreads) tv_hist_kernel(int32_t F, int nb, 
                                                              const uint64_t* __restrict__ xent, TvSlots out) {
   __shared__ uint32_t hist[kFBucket];
   __shared__ int64_t warp_tot[kTvThreads / 32 + 1];
+  __shared__ int64_t s_start[kTvBatch];
+  __shared__ int32_t s_len[kTvBatch];
   const int f = blockIdx.x / nb, b = blockIdx.x % nb;
   const int tid = threadIdx.x;
   for (int i = tid; i < kFBucket; i += kTvThreads) hist[i] = 0;
+  tv_runs<uint16_t>(hist, rc.foff[f], rc.foff[f + 1], nb, b, rrs, rrl, rent, s_start, s_len);
+  tv_runs<uint64_t>(hist, xc.foff[f], xc.foff[f + 1], nb, b, xrs, xrl, xent, s_start, s_len);
   __syncthreads();
-  // one chunk run per warp at a time, so many runs are in flight
-  const int lane0 = tid & 31, warp0 = tid >> 5;
-  for (int64_t c = rc.foff[f] + warp0; c < rc.foff[f + 1]; c += kTvThreads / 32) {
-    const int64_t s0 = rrs[c * nb + b];
-    const int32_t n = rrl[c * nb + b];
-    for (int i = lane0; i < n; i += 32) atomicAdd(&hist[rent[s0 + i]], 1u);
-  }
-  for (int64_t c = xc.foff[f] + warp0; c < xc.foff[f + 1]; c += kTvThreads / 32) {
-    const int64_t s0 = xrs[c * nb + b];
-    const int32_t n = xrl[c * nb + b];
-    for (int i = lane0; i < n; i += 32) {
-      const uint64_t e = xent[s0 + i];
-      atomicAdd(&hist[uint32_t(e) & (kFBucket - 1)], uint32_t(e >> 16));
-    }
-  }
-  __syncthreads();
-  // compaction in word order: thread t owns bins [32 t, 32 t + 32)
-  uint32_t bits = 0;
-#pragma unroll
-  for (int j = 0; j < kBinsPerThread; ++j)
-    if (hist[tid * kBinsPerThread + j]) bits |= 1u << j;
-  const int n = __popc(bits);
+  // compaction in word order: warp w owns bins [1024 w, 1024 w + 1024), read
+  // 32 consecutive bins per round (no bank conflicts); the round masks are the
+  // inverted index's occupancy bits
+  constexpr int kBinsPerWarp = kFBucket / (kTvThreads / 32);
+  constexpr int kRounds = kBinsPerWarp / 32;
+  static_assert(kRounds == 32, "one round mask per lane");
   const int lane = tid & 31, warp = tid >> 5;
-  int incl = n;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int u = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += u;
+  uint32_t my_mask = 0;  // lane r keeps the mask of round r
+  int wcount = 0;
+#pragma unroll 8
+  for (int r = 0; r < kRounds; ++r) {
+    const uint32_t m = __ballot_sync(0xffffffffu, hist[warp * kBinsPerWarp + r * 32 + lane] != 0u);
+    if (lane == r) my_mask = m;
+    wcount += __popc(m);
   }
-  if (lane == 31) warp_tot[warp] = incl;
+  out.bits[int64_t(blockIdx.x) * kTvThreads + warp * 32 + lane] = my_mask;
+  if (lane == 0) warp_tot[warp] = wcount;
   __syncthreads();
   if (warp == 0) {
-    int64_t wv = lane < kTvThreads / 32 ? warp_tot[lane] : 0;
+    const int64_t wv = lane < kTvThreads / 32 ? warp_tot[lane] : 0;
     int64_t wi = wv;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -376,17 +398,21 @@ __global__ void __launch_bounds__(kTvThreads) tv_hist_kernel(int32_t F, int nb, 
     if (lane == kTvThreads / 32 - 1) warp_tot[kTvThreads / 32] = wi;
   }
   __syncthreads();
-  int64_t o = warp_tot[warp] + incl - n;
   const int64_t slot = int64_t(blockIdx.x) * kFBucket;
   const int32_t wbase = b << kFBLog2;
+  int64_t o = slot + warp_tot[warp];
+  const uint32_t below = (1u << lane) - 1u;
 #pragma unroll 4
-  for (int j = 0; j < kBinsPerThread; ++j)
-    if (bits >> j & 1u) {
-      out.word[slot + o] = wbase + tid * kBinsPerThread + j;
-      out.cnt[slot + o] = hist[tid * kBinsPerThread + j];
-      ++o;
+  for (int r = 0; r < kRounds; ++r) {
+    const uint32_t m = __shfl_sync(0xffffffffu, my_mask, r);
+    const int bin = warp * kBinsPerWarp + r * 32 + lane;
+    if ((m >> lane) & 1u) {
+      const int64_t p = o + __popc(m & below);
+      out.word[p] = wbase + bin;
+      out.cnt[p] = hist[bin];
     }
-  out.bits[int64_t(blockIdx.x) * kTvThreads + tid] = bits;
+    o += __popc(m);
+  }
   if (tid == 0) out.nnz[blockIdx.x] = warp_tot[kTvThreads / 32];
 }
 
