@@ -266,6 +266,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (used for profiling runs)")
     ap.add_argument("--no-extras", action="store_true", help="skip the secondary sequence-count timing")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving (p50/p99) measurement")
+    ap.add_argument("--no-autotune", action="store_true", help="time the default launch configuration")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -314,6 +315,16 @@ def main():
     info = B.gt_grammar_info_get(gh)
     N = info["num_tokens"]
     bufs = {"counts": torch.empty(g.num_words, dtype=torch.int64, device="cuda")}
+    # per-grammar launch configuration, chosen by measurement before timing
+    tune = None
+    if not args.no_autotune:
+        kinds = {"word_count": B.GT_Q_WORD_COUNT, "inverted_index": B.GT_Q_INVERTED_INDEX,
+                 "term_vector": B.GT_Q_TERM_VECTOR}
+        tune = B.gt_autotune(gh, [kinds[a] for a in wl["analytics"]], reps=3, stream=stream)
+        # grammars loaded later in this run (the end-to-end leg) start from the same choice
+        for name in ("wc_aggregate", "wc_slices", "file_strategy"):
+            if tune[name]:
+                B.gt_set_param(ctx, name, tune[name])
 
     def barrier():
         if world > 1:
@@ -475,7 +486,8 @@ def main():
                 "config": {"workload": args.workload, "analytics": wl["analytics"], "desc": wl["desc"],
                            "tokens": N, "grammar_symbols": info["num_syms"], "rules": info["num_rules"],
                            "files": info["num_files"], "l2": "inputs larger than L2 (symbol array "
-                           f"{4 * info['num_syms'] / 1e6:.0f} MB > 129 MB)"},
+                           f"{4 * info['num_syms'] / 1e6:.0f} MB > 129 MB)",
+                           "autotune": tune},
                 "roofline": roofline, "phases": phases, "extras": extras, "serving": serving,
                 "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clk}

@@ -268,6 +268,8 @@ int64_t gt_kernel_launches(void);
  *                   writes into a given output buffer, and replay it from then
  *                   on (that call should happen outside any stream capture);
  *                   not while profiling is enabled.  0: launch kernel by kernel.
+ *   "wc_slices"     histogram CTAs per 16k-word bucket in the word count
+ *                   (1..64); 0 (default): about 3 x SMs / buckets.
  *   "file_strategy" per-file analytics (term vector, inverted index, per-file
  *                   sequence count, ranked index): 0 (default) picks top-down
  *                   for at most 64 files and bottom-up otherwise (the paper's
@@ -275,6 +277,30 @@ int64_t gt_kernel_launches(void);
  *                   forces bottom-up.
  * GT_ENOTFOUND for an unknown name. */
 gt_status gt_set_param(gt_ctx* ctx, const char* name, int64_t value);
+
+/* Autotuner (the schedule choice of the batched form, Section V-C's
+ * top-down/bottom-up selection made by measurement).  Times, on g itself,
+ * the candidates of the analytics in `kinds` (a bit mask of 1 << gt_query_kind):
+ *   word count / sort: "wc_aggregate" in {0, 1} x "wc_slices" in {k/2, k, 2k}
+ *                      (k = the default number of histogram CTAs per bucket);
+ *   per-file kinds:    "file_strategy" top-down (when F <= 64) vs bottom-up,
+ *                      timed on a term vector + inverted index batch.
+ * Each candidate runs once untimed, then `reps` times (1..1000) on `stream`;
+ * the median device time decides.  The choices are stored on g and take
+ * precedence over gt_set_param values for every later call on g (direct,
+ * gt_run_batch, server).  kinds = 0 clears g's choices.  Synchronises the
+ * device; must not run while other work on g is in flight.  A candidate that
+ * runs out of memory is skipped.  `out` (may be null) receives the choices
+ * and the best median times (ms; 0 for analytics not tuned). */
+typedef struct {
+  int32_t wc_aggregate;
+  int32_t wc_slices;
+  int32_t file_strategy; /* 1 top-down, 2 bottom-up; 0 if not tuned */
+  int32_t candidates;    /* configurations timed */
+  double wc_ms;          /* best word-count time */
+  double file_ms;        /* best per-file batch time */
+} gt_tune_result;
+gt_status gt_autotune(gt_grammar* g, uint32_t kinds, int reps, void* stream, gt_tune_result* out);
 
 #ifdef __cplusplus
 }

@@ -32,6 +32,11 @@ class gt_grammar_desc(ctypes.Structure):
                 ("on_device", ctypes.c_int32)]
 
 
+class gt_tune_result(ctypes.Structure):
+    _fields_ = [("wc_aggregate", ctypes.c_int32), ("wc_slices", ctypes.c_int32), ("file_strategy", ctypes.c_int32),
+                ("candidates", ctypes.c_int32), ("wc_ms", ctypes.c_double), ("file_ms", ctypes.c_double)]
+
+
 class gt_query(ctypes.Structure):
     _fields_ = [("grammar", ctypes.c_void_p), ("kind", ctypes.c_int32), ("param", ctypes.c_int32),
                 ("d_counts", ctypes.c_void_p)]
@@ -78,6 +83,7 @@ def lib() -> ctypes.CDLL:
             "gt_free_result": [_P],
             "gt_profile_enable": [_P, ctypes.c_int],
             "gt_set_param": [_P, ctypes.c_char_p, ctypes.c_int64],
+            "gt_autotune": [_P, ctypes.c_uint32, ctypes.c_int, _P, _P],
             "gt_run_batch": [_P, _P, ctypes.c_int, _P, _P],
             "gt_server_create": [_P, ctypes.c_int, ctypes.c_size_t, ctypes.POINTER(_P)],
             "gt_submit": [_P, _P, ctypes.c_int, ctypes.POINTER(ctypes.c_uint64)],
@@ -310,6 +316,16 @@ def gt_kernel_launches() -> int:
 
 def gt_set_param(ctx: Context, name: str, value: int) -> None:
     _check(lib().gt_set_param(ctx.handle, name.encode(), int(value)), ctx.handle)
+
+
+def gt_autotune(g: GrammarHandle, kinds, reps: int = 3, stream=None) -> dict:
+    """kinds: iterable of GT_Q_* kinds (empty clears the grammar's choices)."""
+    mask = 0
+    for k in kinds:
+        mask |= 1 << int(k)
+    res = gt_tune_result()
+    _check(lib().gt_autotune(g.handle, mask, int(reps), _stream(stream), ctypes.byref(res)), g.ctx.handle)
+    return {n: getattr(res, n) for n, _ in gt_tune_result._fields_}
 
 
 def _query_array(queries):

@@ -18,7 +18,7 @@
 namespace gt {
 
 int file_strategy(const gt_grammar* g) {
-  const int64_t p = g->ctx->param("file_strategy", 0);
+  const int64_t p = gparam(g, "file_strategy", 0);
   if (p == 1 || p == 2) return int(p);
   return g->d.F <= 64 ? 1 : 2;
 }

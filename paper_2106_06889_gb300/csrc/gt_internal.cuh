@@ -189,6 +189,10 @@ struct gt_grammar {
   };
   std::vector<WcGraph> wc_graphs;
   std::mutex graph_mu;
+  // per-grammar parameter choices of gt_autotune; they take precedence over
+  // the context's gt_set_param values
+  std::map<std::string, int64_t> tuned;
+  mutable std::mutex tune_mu;
 };
 
 struct gt_result {
@@ -363,6 +367,8 @@ void bu_window_rows(gt_grammar* g, Buf& head, Buf& tail, int kb, uint64_t key_pa
 void run_file_batch_bu(gt_grammar* g, const int* tv_topk, int n_tv, gt_result** tv_out, gt_result** ii_out,
                        cudaStream_t s);
 gt_result* run_ranked_words_bu(gt_grammar* g, cudaStream_t s);
+// gt_tune.cu: a parameter of this grammar (autotuned value, else the context's)
+int64_t gparam(const gt_grammar* g, const char* name, int64_t dflt);
 // gt_file.cu: term-vector result from (word, count) rows in (file, word) order
 gt_result* tv_from_arrays(gt_ctx* ctx, const int32_t* word, const uint64_t* cnt, const int64_t* tv_off_in,
                           const int64_t* total, int64_t bound, int32_t F, int top_k, cudaStream_t s);

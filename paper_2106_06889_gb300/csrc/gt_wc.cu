@@ -377,7 +377,9 @@ void run_word_count(gt_grammar* g, const uint64_t* d_wt, uint64_t* d_counts, cud
   po.cap_p = (4 * my_syms / nb + 4096 + 7) / 8 * 8;
   po.cap_w = my_nr > 0 ? (4 * my_nr / nb + 1024 + 1) / 2 * 2 : 2;
   po.ovf_cap = d.ntiles * kTile;
-  const int K = std::max(1, (3 * ctx->num_sms + nb - 1) / nb);
+  // hist CTAs per bucket (partial histograms reduced afterwards)
+  const int64_t k_param = gparam(g, "wc_slices", 0);
+  const int K = k_param > 0 ? int(std::min<int64_t>(k_param, 64)) : std::max(1, (3 * ctx->num_sms + nb - 1) / nb);
   Buf plain(ctx, size_t(nb) * grid1 * po.cap_p * 2, s), wgt(ctx, size_t(nb) * grid1 * po.cap_w * 8, s);
   Buf cnt(ctx, size_t(nb) * grid1 * 16 + 16, s), ovf(ctx, size_t(po.ovf_cap) * 8, s);
   Buf partial(ctx, size_t(nb) * K * kBucket * 4, s);
@@ -397,7 +399,7 @@ void run_word_count(gt_grammar* g, const uint64_t* d_wt, uint64_t* d_counts, cud
   }
   {
     Phase ph2(ctx, "wc_hist", s);
-    if (ctx->param("wc_aggregate", 0))
+    if (gparam(g, "wc_aggregate", 0))
       wc_hist_kernel<true><<<nb * K, kHistThreads, 0, s>>>(po, grid1, K, partial.as<uint32_t>());
     else
       wc_hist_kernel<false><<<nb * K, kHistThreads, 0, s>>>(po, grid1, K, partial.as<uint32_t>());
