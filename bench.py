@@ -194,9 +194,26 @@ def serving_bench(B, ctx, n_corpora=8, n_queries=1000, seed=7):
                       "p50_ms": float(np.percentile(lats, 50)), "p99_ms": float(np.percentile(lats, 99))})
     stats = B.gt_server_stats(sv)
     B.gt_server_destroy(sv)
+    # word counts of every resident corpus: one fused launch sequence against
+    # one call per corpus (both device-timed on one stream)
+    fused = {}
+    with torch.cuda.stream(st):
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for mode in ("per_corpus", "fused", "per_corpus", "fused"):  # second round is timed
+            ev0.record(st)
+            for _ in range(20):
+                if mode == "fused":
+                    B.gt_word_count_batch(hs, bufs, st)
+                else:
+                    for h, b in zip(hs, bufs):
+                        B.gt_word_count(h, b, st)
+            ev1.record(st)
+            st.synchronize()
+            fused[mode] = ev0.elapsed_time(ev1) / 20
     for h in hs:
         B.gt_free_grammar(h)
     return {"corpora": n_corpora, "corpus_tokens": ntok, "queries": n_queries,
+            "word_count_all_corpora_ms": fused,
             "mix": "40% word count / 30% inverted index / 30% 3-gram count, corpus uniform",
             "plain": {"qps": n_queries / t_plain, "tokens_per_s": tokens / t_plain},
             "served_saturated": {"qps": cap_qps, "tokens_per_s": tokens / t_sat, "slots": 8,

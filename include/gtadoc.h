@@ -128,6 +128,13 @@ gt_status gt_rule_weights(gt_grammar* g, uint64_t* d_weights, void* stream);
  * graph once the same buffer has been used before (see "use_graphs"). */
 gt_status gt_word_count(gt_grammar* g, uint64_t* d_counts, void* stream);
 
+/* Word counts of n grammars of one context in one fused launch sequence
+ * (the batched form: one launch per DAG level covers every grammar, then one
+ * partition, one histogram and one reduce launch for all of them, up to 64
+ * grammars per sequence).  d_counts[i]: device uint64[num_words of gs[i]],
+ * written entirely.  Same results as n calls of gt_word_count. */
+gt_status gt_word_count_batch(gt_grammar* const* gs, uint64_t* const* d_counts, int n, void* stream);
+
 /* Word count that allocates no device memory: same result as gt_word_count
  * (bit-identical counts), for callers that cannot allocate at the time of the
  * call.  The paper has no counterpart.  Its only scratch, one uint64 weight

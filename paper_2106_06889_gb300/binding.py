@@ -73,6 +73,7 @@ def lib() -> ctypes.CDLL:
             "gt_rule_weights": [_P, _P, _P],
             "gt_word_count": [_P, _P, _P],
             "gt_word_count_noalloc": [_P, _P, _P],
+            "gt_word_count_batch": [_P, _P, ctypes.c_int, _P],
             "gt_sort": [_P, ctypes.c_int, _P, ctypes.POINTER(_P)],
             "gt_inverted_index": [_P, _P, ctypes.POINTER(_P)],
             "gt_term_vector": [_P, ctypes.c_int, _P, ctypes.POINTER(_P)],
@@ -214,6 +215,17 @@ def gt_rule_weights(g: GrammarHandle, d_weights, stream=None) -> None:
 
 def gt_word_count(g: GrammarHandle, d_counts, stream=None) -> None:
     _check(lib().gt_word_count(g.handle, _dptr(d_counts), _stream(stream)), g.ctx.handle)
+
+
+def gt_word_count_batch(gs, d_counts, stream=None) -> None:
+    """Word counts of several grammars (one context) in one fused launch sequence."""
+    n = len(gs)
+    if n == 0 or n != len(d_counts):
+        raise ValueError("need one output buffer per grammar")
+    hs = (ctypes.c_void_p * n)(*[g.handle.value for g in gs])
+    ps = (ctypes.c_void_p * n)(*[_dptr(t).value for t in d_counts])
+    _check(lib().gt_word_count_batch(ctypes.cast(hs, ctypes.c_void_p), ctypes.cast(ps, ctypes.c_void_p), n,
+                                     _stream(stream)), gs[0].ctx.handle)
 
 
 def gt_word_count_noalloc(g: GrammarHandle, d_counts, stream=None) -> None:

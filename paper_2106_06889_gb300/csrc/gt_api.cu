@@ -5,6 +5,8 @@
 #include <cstring>
 #include <new>
 
+#include <unordered_map>
+
 #include "gt_device.cuh"
 
 using gt::Buf;
@@ -382,6 +384,17 @@ GT_API gt_status gt_word_count(gt_grammar* g, uint64_t* d_counts, void* stream) 
   });
 }
 
+GT_API gt_status gt_word_count_batch(gt_grammar* const* gs, uint64_t* const* d_counts, int n, void* stream) {
+  if (!gs || !d_counts || n < 1) return GT_EINVAL;
+  for (int i = 0; i < n; ++i)
+    if (!gs[i] || !d_counts[i] || gs[i]->ctx != gs[0]->ctx) return GT_EINVAL;
+  return guard(gs[0]->ctx, [&] {
+    use_device(gs[0]->ctx);
+    for (int a = 0; a < n; a += 64)
+      gt::run_word_count_multi(const_cast<gt_grammar**>(gs) + a, d_counts + a, std::min(64, n - a), as_stream(stream));
+  });
+}
+
 GT_API gt_status gt_head_tail(gt_grammar* g, int32_t* d_head, int32_t* d_tail, void* stream) {
   if (!g || !d_head || !d_tail) return GT_EINVAL;
   return guard(g->ctx, [&] {
@@ -502,37 +515,51 @@ GT_API gt_status gt_run_batch(gt_ctx* ctx, const gt_query* q, int nq, void* stre
     use_device(ctx);
     cudaStream_t s = as_stream(stream);
     std::vector<bool> done(size_t(nq), false);
+    // ---- word counts (and the sorts built on them): one counts buffer per
+    // grammar, and the word counts of all grammars in one fused launch sequence ----
+    std::vector<gt_grammar*> wg;
+    std::vector<uint64_t*> wc;
+    std::vector<Buf> wscratch;
+    wscratch.reserve(size_t(nq));
+    std::unordered_map<gt_grammar*, uint64_t*> counts_of;
+    bool caller_buffer_only = true;
+    for (int i = 0; i < nq; ++i) {
+      if (q[i].kind != GT_Q_WORD_COUNT && q[i].kind != GT_Q_SORT) continue;
+      gt_grammar* g = q[i].grammar;
+      if (counts_of.count(g)) continue;
+      uint64_t* counts = nullptr;
+      for (int j = i; j < nq && !counts; ++j)
+        if (q[j].grammar == g && q[j].kind == GT_Q_WORD_COUNT) counts = q[j].d_counts;
+      if (!counts) {
+        wscratch.emplace_back(ctx, size_t(g->d.V) * 8, s);
+        counts = wscratch.back().as<uint64_t>();
+        caller_buffer_only = false;
+      }
+      counts_of[g] = counts;
+      wg.push_back(g);
+      wc.push_back(counts);
+    }
+    if (wg.size() == 1) {
+      if (caller_buffer_only)
+        word_count_any(wg[0], wc[0], s);  // caller buffer: graph-replayable
+      else
+        word_count_direct(wg[0], wc[0], s);
+    } else {
+      for (size_t a = 0; a < wg.size(); a += 64)
+        gt::run_word_count_multi(wg.data() + a, wc.data() + a, int(std::min<size_t>(64, wg.size() - a)), s);
+    }
+    for (int j = 0; j < nq; ++j) {
+      if (q[j].kind == GT_Q_WORD_COUNT && q[j].d_counts != counts_of[q[j].grammar])
+        GT_CUDA(cudaMemcpyAsync(q[j].d_counts, counts_of[q[j].grammar], size_t(q[j].grammar->d.V) * 8,
+                                cudaMemcpyDeviceToDevice, s));
+      if (q[j].kind == GT_Q_SORT) out[j] = sort_from_counts(q[j].grammar, counts_of[q[j].grammar], q[j].param, s);
+    }
     for (int i = 0; i < nq; ++i) {
       if (done[i]) continue;
       gt_grammar* g = q[i].grammar;
       std::vector<int> same;
       for (int j = i; j < nq; ++j)
         if (!done[j] && q[j].grammar == g) same.push_back(j);
-      // word count and sort share the weights and the counts
-      int first_wc = -1;
-      bool need_counts = false;
-      for (int j : same) {
-        if (q[j].kind == GT_Q_WORD_COUNT && first_wc < 0) first_wc = j;
-        if (q[j].kind == GT_Q_WORD_COUNT || q[j].kind == GT_Q_SORT) need_counts = true;
-      }
-      if (need_counts) {
-        Buf scratch;
-        uint64_t* counts = first_wc >= 0 ? q[first_wc].d_counts : nullptr;
-        if (!counts) {
-          scratch = Buf(ctx, size_t(g->d.V) * 8, s);
-          counts = scratch.as<uint64_t>();
-        }
-        if (first_wc >= 0) {
-          word_count_any(g, counts, s);  // caller buffer: graph-replayable
-        } else {
-          word_count_direct(g, counts, s);
-        }
-        for (int j : same) {
-          if (q[j].kind == GT_Q_WORD_COUNT && q[j].d_counts != counts)
-            GT_CUDA(cudaMemcpyAsync(q[j].d_counts, counts, size_t(g->d.V) * 8, cudaMemcpyDeviceToDevice, s));
-          if (q[j].kind == GT_Q_SORT) out[j] = sort_from_counts(g, counts, q[j].param, s);
-        }
-      }
       // term vectors and inverted index share the per-file traversal
       std::vector<int> tv_idx, tv_k;
       int ii = -1;

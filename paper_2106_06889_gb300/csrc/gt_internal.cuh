@@ -343,6 +343,8 @@ void csr_offsets_hi(const uint64_t* keys, int64_t n, int64_t nh, int64_t* off, c
 // gt_wc.cu
 void run_rule_weights(gt_grammar* g, uint64_t* d_wt, cudaStream_t s);
 void run_word_count(gt_grammar* g, const uint64_t* d_wt, uint64_t* d_counts, cudaStream_t s);
+// word counts of up to 64 grammars (one context) in one fused launch sequence
+void run_word_count_multi(gt_grammar* const* gs, uint64_t* const* counts, int n, cudaStream_t s);
 void run_head_tail(gt_grammar* g, int32_t* d_head, int32_t* d_tail, cudaStream_t s);
 
 // Sorted 3-word window rows: compact keys (kb bits per word, key_pad above
