@@ -98,7 +98,6 @@ class ClockSampler:
 # DRAM bytes (read + write) per launch from one `ncu --set full` capture of the
 # kernel as it stands (see the named profile); None once the kernel changes.
 NCU_TRAFFIC = {
-    "tv_hist_kernel": (211.35e6, "profiles/tv_hist_kernel_multi64_50m.md"),
     "wc_partition_kernel": (222.57e6, "profiles/wc_partition_kernel_multi64_50m.md"),
 }
 
@@ -221,6 +220,43 @@ def serving_bench(B, ctx, n_corpora=8, n_queries=1000, seed=7):
             "poisson": rates}
 
 
+def many_files(B, ctx, reps=3):
+    """100k small files in one grammar (files100k): ranked inverted index over
+    words and over 3-word keys, and term vector + inverted index, all by the
+    bottom-up per-file strategy (the top-down file masks hold 64 files).
+    Device time per query, results freed outside the timed region."""
+    import torch
+    from paper_2106_06889_gb300.corpus import load_config
+    g, _ = load_config("files100k")
+    gh = B.gt_load_grammar(ctx, g)
+    info = B.gt_grammar_info_get(gh)
+    N = info["num_tokens"]
+    st = torch.cuda.Stream()
+    out = {"tokens": N, "files": info["num_files"], "grammar_symbols": info["num_syms"]}
+    cases = {"ranked_index_words": lambda: [B.gt_ranked_index(gh, 1, st)],
+             "ranked_index_3grams": lambda: [B.gt_ranked_index(gh, 3, st)],
+             "term_vector_inverted_index": lambda: B.gt_run_batch(
+                 ctx, [(gh, B.GT_Q_TERM_VECTOR, 0, None), (gh, B.GT_Q_INVERTED_INDEX, 0, None)], st)}
+    with torch.cuda.stream(st):
+        for name, fn in cases.items():
+            for r in fn():  # warm-up
+                B.gt_free_result(r)
+            ts = []
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                res = fn()
+                e1.record(st)
+                st.synchronize()
+                ts.append(e0.elapsed_time(e1))
+                for r in res:
+                    B.gt_free_result(r)
+            ms = float(np.median(ts))
+            out[name] = {"ms_per_query": ms, "tokens_per_s": N / (ms / 1e3)}
+    B.gt_free_grammar(gh)
+    return out
+
+
 def small_word_count(B, ctx, reps=200):
     """Word count on the 200k-token single-file corpus, where launch latency
     dominates: per-query time with the launch sequence replayed from a CUDA
@@ -338,10 +374,6 @@ def main():
         kinds = {"word_count": B.GT_Q_WORD_COUNT, "inverted_index": B.GT_Q_INVERTED_INDEX,
                  "term_vector": B.GT_Q_TERM_VECTOR}
         tune = B.gt_autotune(gh, [kinds[a] for a in wl["analytics"]], reps=3, stream=stream)
-        # grammars loaded later in this run (the end-to-end leg) start from the same choice
-        for name in ("wc_aggregate", "wc_slices", "file_strategy"):
-            if tune[name]:
-                B.gt_set_param(ctx, name, tune[name])
 
     def barrier():
         if world > 1:
@@ -440,6 +472,7 @@ def main():
         ms3 = e0.elapsed_time(e1) / n3
         extras["sequence_count"] = {"tokens_per_s": N / (ms3 / 1e3), "ms_per_query": ms3}
         extras["small_word_count"] = small_word_count(B, ctx)
+        extras["many_files"] = many_files(B, ctx)
 
     # ---- end to end through the public API with host buffers ----
     e2e = None

@@ -233,6 +233,12 @@ def make_corpus(name: str, seed: int | None = None, scale: float = 1.0) -> Corpu
             files.append(inject(rng, base, pieces))
         toks = np.concatenate(files).astype(np.int32)
         lens = np.array([f.shape[0] for f in files], np.int64)
+    elif kind == "many_files":
+        # `scale` shrinks the number of files, not their lengths
+        F = max(2, int(round(spec["F"] * scale)))
+        lo, hi = spec["len_range"]
+        lens = np.round(np.exp(rng.uniform(np.log(lo), np.log(hi), size=F))).astype(np.int64)
+        toks = zipf_tokens(rng, int(lens.sum()), cdf, perm)
     elif kind == "nested":
         # passages of passages: level 0 phrases of Zipf words, level d items
         # are concatenations of `fanout` level d-1 items; pieces from every
@@ -269,6 +275,10 @@ CONFIGS = {
                            passages=50, passage_len=200, copies=4),
     "multi64_50m": dict(kind="files_passages", seed=20210614, N=50_000_000, F=64, len_range=(10_000, 2_000_000),
                         V=500_000, s=1.0, passages=500, passage_len=200, passage_frac=0.05),
+    # many small files: 100k files, Zipf 1.1 over 200k words; file lengths
+    # log-uniform in [100, 5000] tokens (a tenth of [1k, 50k], ~125M tokens,
+    # so that the CPU Sequitur build stays within minutes)
+    "files100k": dict(kind="many_files", seed=20210616, F=100_000, len_range=(100, 5_000), V=200_000, s=1.1),
     # one large file with nested repeats (like dataset E): a deep rule DAG
     "nested_500m": dict(kind="nested", seed=20210615, N=500_000_000, V=1_000_000, s=1.05, phrases=4096,
                         phrase_len=16, depth=6, fanout=4, pool=256, inject_frac=0.5),

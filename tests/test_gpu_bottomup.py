@@ -136,3 +136,12 @@ def test_batch_shares_bottom_up_rows(ctx):
                 B.gt_free_result(r)
     finally:
         B.gt_free_grammar(gh)
+
+
+def test_many_small_files(ctx):
+    """The many-small-files workload (Zipf 1.1 over 200k words), 2000 files:
+    ranked index (words and 3-word keys), term vector and inverted index."""
+    c = make_corpus("files100k", scale=0.02)
+    g = sequitur(c.tokens, c.file_lens, c.num_words)
+    assert g.num_files == 2000
+    check_all(ctx, g)
