@@ -217,6 +217,7 @@ __global__ void __launch_bounds__(kCsThreads) chunk_sort_kernel(Chunks ch, const
   __shared__ __align__(16) unsigned char stage_raw[kChunk * (kWeighted ? 8 : 2)];
   const int64_t nch = *ch.count;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nbits = nb > 1 ? 32 - __clz(nb - 1) : 0;  // bits of a bucket index
   for (int64_t c = blockIdx.x; c < nch; c += gridDim.x) {
     for (int i = tid; i < kCsWarps * (kMaxNb + 1); i += kCsThreads) (&wcnt[0][0])[i] = 0;
     __syncthreads();
@@ -228,7 +229,26 @@ __global__ void __launch_bounds__(kCsThreads) chunk_sort_kernel(Chunks ch, const
     for (int j = 0; j < kCsItems; ++j) {
       const int i = j * kCsThreads + tid;  // warp-contiguous: item order inside a warp is lane order
       w[j] = i < n ? items[base + i] : -1;
-      if (uint32_t(w[j]) < uint32_t(V)) rank[j] = atomicAdd(&wcnt[warp][w[j] >> kFBLog2], 1u);
+    }
+    // rank inside (warp, bucket): lanes with equal buckets found by one ballot
+    // per bucket bit; the lowest of them bumps the warp's counter once
+    const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+    for (int j = 0; j < kCsItems; ++j) {
+      const bool valid = uint32_t(w[j]) < uint32_t(V);
+      const uint32_t bk = valid ? uint32_t(w[j]) >> kFBLog2 : 0u;
+      unsigned peers = __ballot_sync(0xffffffffu, valid);
+      for (int bit = 0; bit < nbits; ++bit) {
+        const bool on = (bk >> bit) & 1u;
+        const unsigned bal = __ballot_sync(0xffffffffu, on);
+        peers &= on ? bal : ~bal;
+      }
+      const uint32_t before = wcnt[warp][bk];
+      const uint32_t r = __popc(peers & lt);
+      rank[j] = before + r;
+      __syncwarp();
+      if (valid && r == 0) wcnt[warp][bk] = before + __popc(peers);
+      __syncwarp();
     }
     __syncthreads();
     // exclusive prefix over (bucket, warp): warp b0.. scans bucket b over the 16 warps
@@ -341,12 +361,22 @@ __device__ __forceinline__ void tv_runs(uint32_t* hist, int64_t c0, int64_t c1, 
     for (int q = warp; q < nbatch; q += kTvThreads / 32) {
       const int64_t s0 = s_start[q];
       const int32_t n = s_len[q];
-      for (int i = lane; i < n; i += 32) {
-        const E e = ent[s0 + i];
-        if (sizeof(E) == 2)
-          atomicAdd(&hist[uint32_t(e)], 1u);
-        else
-          atomicAdd(&hist[uint32_t(e) & (kFBucket - 1)], uint32_t(uint64_t(e) >> 16));
+      // 4 independent loads per lane in flight before the histogram updates
+      for (int i0 = 0; i0 < n; i0 += 128) {
+        E e[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int i = i0 + k * 32 + lane;
+          e[k] = i < n ? ent[s0 + i] : E(0);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          if (i0 + k * 32 + lane >= n) break;
+          if (sizeof(E) == 2)
+            atomicAdd(&hist[uint32_t(e[k])], 1u);
+          else
+            atomicAdd(&hist[uint32_t(e[k]) & (kFBucket - 1)], uint32_t(uint64_t(e[k]) >> 16));
+        }
       }
     }
   }
