@@ -220,6 +220,37 @@ def serving_bench(B, ctx, n_corpora=8, n_queries=1000, seed=7):
             "poisson": rates}
 
 
+def word_count_alone(B, ctx, gh, out, stream, info, hbm, reps=20):
+    """The word count of the benchmark corpus on its own (one grammar, one
+    traversal: weights, partition, histogram, reduce), replayed from its CUDA
+    graph; then a profiled pass for the partition kernel's roofline (4 B per
+    body symbol, the symbol stream it must read)."""
+    import torch
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            B.gt_word_count(gh, out, stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            B.gt_word_count(gh, out, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        B.gt_profile_reset(ctx)
+        B.gt_profile_enable(ctx, True)
+        for _ in range(5):
+            B.gt_word_count(gh, out, stream)
+        torch.cuda.synchronize()
+        B.gt_profile_enable(ctx, False)
+    tot, spans, _ = B.gt_profile_read(ctx, "wc_partition")
+    part_ms = tot / max(spans, 1)
+    ach = 4 * info["num_syms"] / (part_ms / 1e3) / 1e9
+    return {"ms_per_query": ms, "tokens_per_s": info["num_tokens"] / (ms / 1e3),
+            "partition_kernel": {"ms_per_launch": part_ms, "achieved_gbs": ach, "frac_of_measured_hbm": ach / hbm,
+                                 "algorithmic_bytes_per_launch": 4 * info["num_syms"]}}
+
+
 def many_files(B, ctx, reps=3):
     """100k small files in one grammar (files100k): ranked inverted index over
     words and over 3-word keys, and term vector + inverted index, all by the
@@ -433,7 +464,7 @@ def main():
     # ---- dominant kernel: live CUDA-event time of its phase ----
     phases = {}
     for ph in ("weights", "wc_partition", "wc_hist", "sort_canon", "file_weights", "tv_hist", "tv_hist_kernel",
-               "tv_out", "ii_out"):
+               "tv_out", "ii_out", "wc_from_files"):
         tot, spans, la = B.gt_profile_read(ctx, ph)
         if spans:
             phases[ph] = {"ms_per_launch": tot / spans, "spans": spans, "launches": la}
@@ -471,6 +502,7 @@ def main():
             keep.clear()
         ms3 = e0.elapsed_time(e1) / n3
         extras["sequence_count"] = {"tokens_per_s": N / (ms3 / 1e3), "ms_per_query": ms3}
+        extras["word_count"] = word_count_alone(B, ctx, gh, bufs["counts"], stream, info, hbm)
         extras["small_word_count"] = small_word_count(B, ctx)
         extras["many_files"] = many_files(B, ctx)
 

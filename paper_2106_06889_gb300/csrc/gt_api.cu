@@ -522,7 +522,6 @@ GT_API gt_status gt_run_batch(gt_ctx* ctx, const gt_query* q, int nq, void* stre
     std::vector<Buf> wscratch;
     wscratch.reserve(size_t(nq));
     std::unordered_map<gt_grammar*, uint64_t*> counts_of;
-    bool caller_buffer_only = true;
     for (int i = 0; i < nq; ++i) {
       if (q[i].kind != GT_Q_WORD_COUNT && q[i].kind != GT_Q_SORT) continue;
       gt_grammar* g = q[i].grammar;
@@ -533,26 +532,38 @@ GT_API gt_status gt_run_batch(gt_ctx* ctx, const gt_query* q, int nq, void* stre
       if (!counts) {
         wscratch.emplace_back(ctx, size_t(g->d.V) * 8, s);
         counts = wscratch.back().as<uint64_t>();
-        caller_buffer_only = false;
       }
       counts_of[g] = counts;
       wg.push_back(g);
       wc.push_back(counts);
     }
-    if (wg.size() == 1) {
-      if (caller_buffer_only)
-        word_count_any(wg[0], wc[0], s);  // caller buffer: graph-replayable
-      else
-        word_count_direct(wg[0], wc[0], s);
-    } else {
-      for (size_t a = 0; a < wg.size(); a += 64)
-        gt::run_word_count_multi(wg.data() + a, wc.data() + a, int(std::min<size_t>(64, wg.size() - a)), s);
+    // a grammar that also has term-vector / inverted-index queries takes its
+    // counts from that traversal (the sum of the per-file counts, top-down)
+    std::unordered_map<gt_grammar*, bool> from_files;
+    for (int i = 0; i < nq; ++i) {
+      gt_grammar* g = q[i].grammar;
+      if ((q[i].kind == GT_Q_TERM_VECTOR || q[i].kind == GT_Q_INVERTED_INDEX) && counts_of.count(g) &&
+          gt::file_strategy(g) == 1)
+        from_files[g] = true;
     }
-    for (int j = 0; j < nq; ++j) {
-      if (q[j].kind == GT_Q_WORD_COUNT && q[j].d_counts != counts_of[q[j].grammar])
-        GT_CUDA(cudaMemcpyAsync(q[j].d_counts, counts_of[q[j].grammar], size_t(q[j].grammar->d.V) * 8,
-                                cudaMemcpyDeviceToDevice, s));
-      if (q[j].kind == GT_Q_SORT) out[j] = sort_from_counts(q[j].grammar, counts_of[q[j].grammar], q[j].param, s);
+    std::vector<gt_grammar*> fg;
+    std::vector<uint64_t*> fc;
+    for (size_t k = 0; k < wg.size(); ++k)
+      if (!from_files.count(wg[k])) {
+        fg.push_back(wg[k]);
+        fc.push_back(wc[k]);
+      }
+    if (fg.size() == 1) {
+      bool caller = false;
+      for (int i = 0; i < nq; ++i)
+        if (q[i].grammar == fg[0] && q[i].kind == GT_Q_WORD_COUNT && q[i].d_counts == fc[0]) caller = true;
+      if (caller)
+        word_count_any(fg[0], fc[0], s);  // caller buffer: graph-replayable
+      else
+        word_count_direct(fg[0], fc[0], s);
+    } else {
+      for (size_t a = 0; a < fg.size(); a += 64)
+        gt::run_word_count_multi(fg.data() + a, fc.data() + a, int(std::min<size_t>(64, fg.size() - a)), s);
     }
     for (int i = 0; i < nq; ++i) {
       if (done[i]) continue;
@@ -573,7 +584,8 @@ GT_API gt_status gt_run_batch(gt_ctx* ctx, const gt_query* q, int nq, void* stre
       if (!tv_idx.empty() || ii >= 0) {
         std::vector<gt_result*> tvr(tv_idx.size(), nullptr);
         gt_result* iir = nullptr;
-        gt::run_file_batch(g, tv_k.data(), int(tv_k.size()), tvr.data(), ii >= 0 ? &iir : nullptr, s);
+        gt::run_file_batch(g, tv_k.data(), int(tv_k.size()), tvr.data(), ii >= 0 ? &iir : nullptr, s,
+                           from_files.count(g) ? counts_of[g] : nullptr);
         for (size_t k = 0; k < tv_idx.size(); ++k) out[tv_idx[k]] = tvr[k];
         if (ii >= 0) out[ii] = iir;
         for (int j : same)  // a second inverted-index query on the same grammar gets its own copy
@@ -585,6 +597,13 @@ GT_API gt_status gt_run_batch(gt_ctx* ctx, const gt_query* q, int nq, void* stre
           out[j] = q[j].param == 3 ? gt::run_ranked_windows(g, s) : gt::run_ranked_words(g, s);
       }
       for (int j : same) done[j] = true;
+    }
+    // word-count copies and sorts, once every grammar's counts are enqueued
+    for (int j = 0; j < nq; ++j) {
+      if (q[j].kind == GT_Q_WORD_COUNT && q[j].d_counts != counts_of[q[j].grammar])
+        GT_CUDA(cudaMemcpyAsync(q[j].d_counts, counts_of[q[j].grammar], size_t(q[j].grammar->d.V) * 8,
+                                cudaMemcpyDeviceToDevice, s));
+      if (q[j].kind == GT_Q_SORT) out[j] = sort_from_counts(q[j].grammar, counts_of[q[j].grammar], q[j].param, s);
     }
   });
   if (st != GT_OK)

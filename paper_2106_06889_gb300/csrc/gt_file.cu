@@ -881,16 +881,72 @@ gt_result* tv_from_arrays(gt_ctx* ctx, const int32_t* word, const uint64_t* cnt,
   return rb.finish();
 }
 
-void run_file_batch(gt_grammar* g, const int* tv_topk, int n_tv, gt_result** tv_out, gt_result** ii_out,
-                    cudaStream_t s) {
+namespace {
+
+// Word counts as the sum of the per-file counts (top-down pieces): CTA
+// (bucket, file group) adds its files' compacted (word, count) entries of the
+// bucket into a dense shared histogram - words are distinct inside a piece,
+// so updates rarely collide - and stores it as one partial.
+constexpr int kWcFileGroup = 8;
+
+__global__ void __launch_bounds__(kTvThreads) tvwc_hist_kernel(TvSlots ts, int32_t F, int nb, int groups,
+                                                               uint32_t* __restrict__ partial) {
+  __shared__ uint32_t hist[kFBucket];
+  const int b = blockIdx.x / groups, grp = blockIdx.x % groups;
+  for (int i = threadIdx.x; i < kFBucket; i += kTvThreads) hist[i] = 0;
+  __syncthreads();
+  const int f1 = min(F, (grp + 1) * kWcFileGroup);
+  for (int f = grp * kWcFileGroup; f < f1; ++f) {
+    const int64_t piece = int64_t(f) * nb + b;
+    const int64_t n = ts.nnz[piece];
+    const int32_t* __restrict__ w = ts.word + piece * kFBucket;
+    const uint32_t* __restrict__ c = ts.cnt + piece * kFBucket;
+    for (int64_t i = threadIdx.x; i < n; i += kTvThreads) atomicAdd(&hist[w[i] & (kFBucket - 1)], c[i]);
+  }
+  __syncthreads();
+  uint32_t* dst = partial + int64_t(blockIdx.x) * kFBucket;
+  for (int i = threadIdx.x; i < kFBucket; i += kTvThreads) dst[i] = hist[i];
+}
+
+__global__ void tvwc_reduce_kernel(const uint32_t* __restrict__ partial, int groups, int32_t V,
+                                   unsigned long long* __restrict__ counts) {
+  for (int64_t w = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; w < V; w += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t b = w >> kFBLog2, l = w & (kFBucket - 1);
+    unsigned long long s = 0;
+    for (int k = 0; k < groups; ++k) s += partial[(b * groups + k) * kFBucket + l];
+    counts[w] = s;
+  }
+}
+
+}  // namespace
+
+bool run_file_batch(gt_grammar* g, const int* tv_topk, int n_tv, gt_result** tv_out, gt_result** ii_out,
+                    cudaStream_t s, uint64_t* wc_out) {
   if (file_strategy(g) == 2) {
     run_file_batch_bu(g, tv_topk, n_tv, tv_out, ii_out, s);
-    return;
+    return false;
   }
   FileHist fh;
   file_hist(g, s, fh);
   for (int i = 0; i < n_tv; ++i) tv_out[i] = term_vector_from(g, fh, tv_topk[i], s);
   if (ii_out) *ii_out = inverted_index_from(g, fh, s);
+  if (!wc_out) return false;
+  gt_ctx* ctx = g->ctx;
+  const DevGrammar& d = g->d;
+  Phase ph(ctx, "wc_from_files", s);
+  const int groups = (d.F + kWcFileGroup - 1) / kWcFileGroup;
+  if (groups == 0 || fh.nb == 0) {
+    GT_CUDA(cudaMemsetAsync(wc_out, 0, size_t(d.V) * 8, s));
+    return true;
+  }
+  TvSlots ts{fh.slot_word.as<int32_t>(), fh.slot_cnt.as<uint32_t>(), fh.nnz.as<int64_t>(), fh.bits.as<uint32_t>()};
+  Buf partial(ctx, size_t(fh.nb) * groups * kFBucket * 4, s);
+  tvwc_hist_kernel<<<unsigned(fh.nb * groups), kTvThreads, 0, s>>>(ts, d.F, fh.nb, groups, partial.as<uint32_t>());
+  GT_LAUNCH_CHECK();
+  tvwc_reduce_kernel<<<grid_for(d.V, 256, ctx->num_sms * 8), 256, 0, s>>>(
+      partial.as<uint32_t>(), groups, d.V, reinterpret_cast<unsigned long long*>(wc_out));
+  GT_LAUNCH_CHECK();
+  return true;
 }
 
 gt_result* run_term_vector(gt_grammar* g, int top_k, cudaStream_t s) {

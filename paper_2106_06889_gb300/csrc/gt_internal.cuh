@@ -400,8 +400,11 @@ void file_weights(gt_grammar* g, cudaStream_t s, FileWeights& fw);
 void file_sizes(gt_grammar* g, cudaStream_t s);
 // One shared traversal for several per-file queries on one grammar: n_tv term
 // vectors (top_k each) and, if ii_out is set, the inverted index.
-void run_file_batch(gt_grammar* g, const int* tv_topk, int n_tv, gt_result** tv_out, gt_result** ii_out,
-                    cudaStream_t s);
+// Term vectors / inverted index of one grammar from one traversal.  With
+// wc_out (top-down strategy only) the word counts are written too, as the sum
+// of the per-file counts; returns whether they were.
+bool run_file_batch(gt_grammar* g, const int* tv_topk, int n_tv, gt_result** tv_out, gt_result** ii_out,
+                    cudaStream_t s, uint64_t* wc_out = nullptr);
 gt_result* run_inverted_index(gt_grammar* g, cudaStream_t s);
 
 // gt_sort.cu: device primitives
