@@ -149,15 +149,21 @@ def owned_windows(g) -> np.ndarray:
 # The six analytics (Section VI)
 # ---------------------------------------------------------------------------
 
+# Each analytic is defined on the token arrays of the files (``*_text``); the
+# grammar versions apply that definition to the grammar's expansion.
+
+def word_count_text(files, num_words: int) -> np.ndarray:
+    toks = np.concatenate(files) if len(files) else np.zeros(0, np.int64)
+    return np.bincount(toks, minlength=num_words).astype(np.uint64)
+
+
 def word_count(g) -> np.ndarray:
-    files = expand_files(g)
-    toks = np.concatenate(files) if files else np.zeros(0, np.int64)
-    return np.bincount(toks, minlength=g.num_words).astype(np.uint64)
+    return word_count_text(expand_files(g), g.num_words)
 
 
-def sort_words(g, order: int = 0):
+def sort_words_text(files, num_words: int, order: int = 0):
     """(word, count) of every word that occurs; order 0 by word, 1 by count desc."""
-    cnt = word_count(g).astype(np.int64)
+    cnt = word_count_text(files, num_words).astype(np.int64)
     words = np.nonzero(cnt)[0]
     counts = cnt[words]
     if order == 1:
@@ -166,10 +172,14 @@ def sort_words(g, order: int = 0):
     return words.astype(np.int32), counts.astype(np.uint64)
 
 
-def term_vector(g, top_k: int = 0):
+def sort_words(g, order: int = 0):
+    return sort_words_text(expand_files(g), g.num_words, order)
+
+
+def term_vector_text(files, top_k: int = 0):
     """Per file: distinct words with in-file counts (CSR over files)."""
     offs, words, counts = [0], [], []
-    for toks in expand_files(g):
+    for toks in files:
         w, c = np.unique(toks, return_counts=True)
         if top_k > 0:
             idx = np.lexsort((w, -c))[:top_k]
@@ -181,10 +191,14 @@ def term_vector(g, top_k: int = 0):
     return np.array(offs, np.int64), cat(words, np.int32), cat(counts, np.uint64)
 
 
-def inverted_index(g):
+def term_vector(g, top_k: int = 0):
+    return term_vector_text(expand_files(g), top_k)
+
+
+def inverted_index_text(files, num_words: int):
     """Per word: ascending list of files containing it (CSR over words)."""
     pairs_w, pairs_f = [], []
-    for f, toks in enumerate(expand_files(g)):
+    for f, toks in enumerate(files):
         w = np.unique(toks)
         pairs_w.append(w)
         pairs_f.append(np.full(w.shape[0], f, np.int64))
@@ -192,9 +206,13 @@ def inverted_index(g):
     f = np.concatenate(pairs_f) if pairs_f else np.zeros(0, np.int64)
     idx = np.lexsort((f, w))
     w, f = w[idx], f[idx]
-    offs = np.zeros(g.num_words + 1, np.int64)
-    offs[1:] = np.cumsum(np.bincount(w, minlength=g.num_words))
+    offs = np.zeros(num_words + 1, np.int64)
+    offs[1:] = np.cumsum(np.bincount(w, minlength=num_words))
     return offs, f.astype(np.int32)
+
+
+def inverted_index(g):
+    return inverted_index_text(expand_files(g), g.num_words)
 
 
 def pack3(a, b, c) -> np.ndarray:
@@ -209,13 +227,12 @@ def file_windows(toks: np.ndarray) -> np.ndarray:
     return pack3(toks[:-2], toks[1:-1], toks[2:])
 
 
-def sequence_count(g, per_file: int = 0):
+def sequence_count_text(files, num_words: int, per_file: int = 0):
     """Counts of 3-word sequences (Section IV-D, l = 3), windows inside files only."""
-    if g.num_words > (1 << KEY_BITS):
+    if num_words > (1 << KEY_BITS):
         raise ValueError("3-word keys need num_words <= 2^21")
-    files = expand_files(g)
     if not per_file:
-        keys = np.concatenate([file_windows(t) for t in files]) if files else np.zeros(0, np.uint64)
+        keys = np.concatenate([file_windows(t) for t in files]) if len(files) else np.zeros(0, np.uint64)
         k, c = np.unique(keys, return_counts=True)
         return k.astype(np.uint64), c.astype(np.uint64)
     fs, ks, cs = [], [], []
@@ -226,6 +243,34 @@ def sequence_count(g, per_file: int = 0):
         cs.append(c)
     cat = (lambda xs, dt: np.concatenate(xs).astype(dt) if xs else np.zeros(0, dt))
     return cat(fs, np.int32), cat(ks, np.uint64), cat(cs, np.uint64)
+
+
+def sequence_count(g, per_file: int = 0):
+    return sequence_count_text(expand_files(g), g.num_words, per_file)
+
+
+def key_file_counts_text(files, keys, n: int = 3):
+    """For the given keys (words if n = 1, packed 3-word keys if n = 3): every
+    (key, file, count) with count = occurrences of the key in the file > 0,
+    in ranked order (key asc, count desc, file asc).  The rows of the ranked
+    inverted index restricted to those keys."""
+    keys = np.unique(np.asarray(keys, dtype=np.uint64))
+    ks, fs = [], []
+    for f, t in enumerate(files):
+        items = t.astype(np.uint64) if n == 1 else file_windows(t)
+        hit = items[np.isin(items, keys)]
+        ks.append(hit)
+        fs.append(np.full(hit.shape[0], f, np.int64))
+    k = np.concatenate(ks) if ks else np.zeros(0, np.uint64)
+    f = np.concatenate(fs) if fs else np.zeros(0, np.int64)
+    pairs = np.stack([k.astype(np.int64), f], axis=1) if k.shape[0] else np.zeros((0, 2), np.int64)
+    if pairs.shape[0]:
+        u, c = np.unique(pairs, axis=0, return_counts=True)
+    else:
+        u, c = pairs, np.zeros(0, np.int64)
+    kk, ff = u[:, 0].astype(np.uint64), u[:, 1]
+    idx = np.lexsort((ff, -c, kk))
+    return kk[idx], ff[idx].astype(np.int32), c[idx].astype(np.uint64)
 
 
 def ranked_index(g, n: int = 3):

@@ -109,6 +109,52 @@ def sequitur(tokens: np.ndarray, file_lens, num_words: int) -> Grammar:
     return Grammar(int(num_words), rule_off, sym, file_off)
 
 
+def sequitur_sharded(tokens: np.ndarray, file_lens, num_words: int, shards: int) -> Grammar:
+    """Sequitur on ``shards`` contiguous pieces of the text in parallel, the
+    piece grammars concatenated into one: the root is the pieces' roots back
+    to back, each piece keeps its own rules (renumbered; no rule is shared
+    across pieces).  Pieces end at file boundaries when there are several
+    files, else at equal token counts.  Used for corpora too large for one
+    single-threaded Sequitur run."""
+    from concurrent.futures import ThreadPoolExecutor
+    tokens = np.ascontiguousarray(tokens, dtype=np.int32)
+    file_lens = np.ascontiguousarray(file_lens, dtype=np.int64)
+    n = int(tokens.shape[0])
+    F = int(file_lens.shape[0])
+    shards = max(1, min(shards, F) if F > 1 else shards)
+    if F > 1:  # cut at the file boundary nearest to each equal share
+        ends = np.cumsum(file_lens)
+        cuts = sorted(set(int(np.searchsorted(ends, n * k / shards)) + 1 for k in range(1, shards)))
+        fcuts = [0] + [c for c in cuts if 0 < c < F] + [F]
+        pieces = [(int(ends[a - 1]) if a else 0, int(ends[b - 1]), file_lens[a:b]) for a, b in zip(fcuts, fcuts[1:])]
+    else:
+        bounds = [n * k // shards for k in range(shards + 1)]
+        pieces = [(a, b, None) for a, b in zip(bounds, bounds[1:]) if b > a]
+    with ThreadPoolExecutor(max_workers=len(pieces)) as ex:  # the builder releases the GIL
+        parts = list(ex.map(lambda p: sequitur(tokens[p[0]:p[1]], p[2] if p[2] is not None else [p[1] - p[0]],
+                                               num_words), pieces))
+    V = int(num_words)
+    roots, bodies, rule_lens = [], [], []
+    file_offs, base_sym, nrules = [], 0, 1
+    for part in parts:
+        shift = nrules - 1  # rule r >= 1 of the piece becomes rule r + shift
+        sym = part.sym.astype(np.int64)
+        sym = np.where(sym >= V, sym + shift, sym).astype(np.int32)
+        r0 = int(part.rule_off[1])
+        roots.append(sym[:r0])
+        bodies.append(sym[r0:])
+        rule_lens.append(np.diff(part.rule_off[1:]))
+        if F > 1:
+            file_offs.append(part.file_off[1:] + base_sym)
+        base_sym += r0
+        nrules += part.num_rules - 1
+    root = np.concatenate(roots)
+    lens = np.concatenate([[root.shape[0]]] + rule_lens).astype(np.int64)
+    rule_off = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    file_off = (np.concatenate([[0]] + file_offs) if F > 1 else np.array([0, root.shape[0]])).astype(np.int64)
+    return Grammar(V, rule_off, np.concatenate([root] + bodies).astype(np.int32), file_off)
+
+
 def root_only_grammar(tokens: np.ndarray, file_lens, num_words: int) -> Grammar:
     """The trivial encoding: no rules, the root is the raw text."""
     tokens = np.ascontiguousarray(tokens, dtype=np.int32)
@@ -325,6 +371,10 @@ def cache_dir() -> Path:
     return d
 
 
+# corpora above this many tokens are compressed by sequitur_sharded
+SHARD_ABOVE = 100_000_000
+
+
 def load_config(name: str, scale: float = 1.0, keep_tokens: bool = False):
     """Corpus + Sequitur grammar for a named config, cached on disk.
 
@@ -337,6 +387,8 @@ def load_config(name: str, scale: float = 1.0, keep_tokens: bool = False):
     corpus = make_corpus(name, scale=scale)
     if path.exists():
         g = Grammar.load(path)
+    elif corpus.tokens.shape[0] > SHARD_ABOVE:
+        g = sequitur_sharded(corpus.tokens, corpus.file_lens, corpus.num_words, shards=min(16, os.cpu_count() or 1))
     else:
         g = sequitur(corpus.tokens, corpus.file_lens, corpus.num_words)
         g.meta = dict(corpus.meta)

@@ -4,6 +4,7 @@ import numpy as np
 import pytest
 
 from paper_2106_06889_gb300.corpus import sequitur, make_corpus, Grammar
+import oracle
 from tests import brute
 
 
@@ -70,3 +71,17 @@ def test_sequitur_rejects_bad_input():
         sequitur(np.array([0, 5], np.int32), [2], 3)  # word id out of range
     with pytest.raises(ValueError):
         sequitur(np.array([0, 1], np.int32), [3], 3)  # lengths do not add up
+
+
+@pytest.mark.parametrize("name,scale", [("nested_500m", 0.001), ("files100k", 0.01), ("multi64_50m", 0.004)])
+@pytest.mark.parametrize("shards", [1, 3, 7])
+def test_sharded_sequitur_expands_to_source(name, scale, shards):
+    """The shard-parallel build used for the largest corpora encodes the same
+    text: expansion equals the source, file by file."""
+    from paper_2106_06889_gb300.corpus import sequitur_sharded
+    c = make_corpus(name, scale=scale)
+    g = sequitur_sharded(c.tokens, c.file_lens, c.num_words, shards)
+    files = oracle.expand_files(g)
+    assert g.num_files == c.file_lens.shape[0]
+    assert [len(f) for f in files] == list(c.file_lens)
+    assert np.array_equal(np.concatenate(files), c.tokens)

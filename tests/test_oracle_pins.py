@@ -402,3 +402,34 @@ def test_planted_swapped_key_fields():
     def patch(m):
         m.pack3 = lambda a, b, c: orc_impl.pack3(c, b, a)
     assert _fails(lambda: _pins(broken_oracle(patch)))
+
+
+@pytest.mark.parametrize("n", [1, 3])
+def test_key_file_counts_match_ranked_index(n):
+    """key_file_counts_text (the ranked rows of chosen keys, used for sampled
+    checks at full size) equals the ranked index restricted to those keys,
+    and is computed from the source text rather than the grammar."""
+    rng = np.random.default_rng(11)
+    checked = 0
+    for name, g, toks, lens in tiny_cases(seed=13, count=12):
+        if toks is None or g.num_words > (1 << 21):
+            continue
+        offs, keys, files, counts = oracle.ranked_index(g, n)
+        if keys.shape[0] == 0:
+            continue
+        pick = rng.choice(keys, size=min(5, keys.shape[0]), replace=False)
+        pick = np.append(pick, np.uint64((1 << 63) - 1))  # a key that never occurs
+        k, f, c = oracle.key_file_counts_text(split_files(toks, lens), pick, n)
+        want_k, want_f, want_c = [], [], []
+        for key in np.sort(pick):
+            i = np.searchsorted(keys, key)
+            if i < keys.shape[0] and keys[i] == key:
+                a, b = offs[i], offs[i + 1]
+                want_k.append(np.full(b - a, key, np.uint64))
+                want_f.append(files[a:b])
+                want_c.append(counts[a:b])
+        assert np.array_equal(k, np.concatenate(want_k)), name
+        assert np.array_equal(f, np.concatenate(want_f)), name
+        assert np.array_equal(c, np.concatenate(want_c)), name
+        checked += 1
+    assert checked >= 5
