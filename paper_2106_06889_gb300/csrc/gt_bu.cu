@@ -197,13 +197,14 @@ __global__ void file_offsets_kernel(const int32_t* __restrict__ file, const int6
 }
 
 // Inverted index from (file, word) rows: stable sort by word carrying the
-// row, then the files in that order; offsets per word.
-__global__ void word_keys_kernel(const int32_t* __restrict__ word, const int64_t* __restrict__ n_dev, int64_t bound,
-                                 int32_t V, uint64_t* __restrict__ k, uint32_t* __restrict__ idx) {
+// file, so the files come out ascending inside each word; offsets per word.
+__global__ void word_keys_kernel(const int32_t* __restrict__ word, const int32_t* __restrict__ file,
+                                 const int64_t* __restrict__ n_dev, int64_t bound, int32_t V, uint64_t* __restrict__ k,
+                                 uint32_t* __restrict__ f) {
   const int64_t n = *n_dev;
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < bound; i += int64_t(gridDim.x) * blockDim.x) {
     k[i] = i < n ? uint64_t(uint32_t(word[i])) : uint64_t(uint32_t(V));
-    idx[i] = uint32_t(i);
+    f[i] = i < n ? uint32_t(file[i]) : 0u;
   }
 }
 
@@ -212,13 +213,6 @@ __global__ void widen_i32_kernel(const int32_t* __restrict__ a, const int64_t* _
   const int64_t n = *n_dev;
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
     out[i] = uint64_t(uint32_t(a[i]));
-}
-
-__global__ void gather_i32_kernel(const int32_t* __restrict__ src, const uint32_t* __restrict__ idx,
-                                  const int64_t* __restrict__ n_dev, int32_t* __restrict__ dst) {
-  const int64_t n = *n_dev;
-  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
-    dst[i] = src[idx[i]];
 }
 
 __global__ void word_offsets_kernel(const uint64_t* __restrict__ sk, const int64_t* __restrict__ n_dev, int32_t V,
@@ -309,16 +303,14 @@ gt_result* bu_inverted_index(gt_grammar* g, WordRows& wr, cudaStream_t s) {
   auto* files = static_cast<int32_t*>(rb.alloc(size_t(n) * 4));
   int64_t* len = rb.new_len_slot();
   GT_CUDA(cudaMemcpyAsync(len, wr.total.p, 8, cudaMemcpyDeviceToDevice, s));
-  Buf k0(ctx, size_t(n) * 8, s), k1(ctx, size_t(n) * 8, s), i0(ctx, size_t(n) * 4, s), i1(ctx, size_t(n) * 4, s);
+  Buf k0(ctx, size_t(n) * 8, s), k1(ctx, size_t(n) * 8, s), f0(ctx, size_t(n) * 4, s);
   if (n > 0) {
     Buf rs(ctx, radix_scratch_bytes(n, true, 4), s);
-    word_keys_kernel<<<grid_for(n, threads, cap), threads, 0, s>>>(wr.word.as<int32_t>(), wr.total.as<int64_t>(), n,
-                                                                    d.V, k0.as<uint64_t>(), i0.as<uint32_t>());
+    word_keys_kernel<<<grid_for(n, threads, cap), threads, 0, s>>>(wr.word.as<int32_t>(), wr.file.as<int32_t>(),
+                                                                    wr.total.as<int64_t>(), n, d.V, k0.as<uint64_t>(),
+                                                                    f0.as<uint32_t>());
     GT_LAUNCH_CHECK();
-    radix_sort_u64(k0.as<uint64_t>(), k1.as<uint64_t>(), i0.p, i1.p, 4, n, 0, bits_for(d.V), rs.p, s);
-    gather_i32_kernel<<<grid_for(n, threads, cap), threads, 0, s>>>(wr.file.as<int32_t>(), i1.as<uint32_t>(),
-                                                                     wr.total.as<int64_t>(), files);
-    GT_LAUNCH_CHECK();
+    radix_sort_u64(k0.as<uint64_t>(), k1.as<uint64_t>(), f0.p, files, 4, n, 0, bits_for(d.V), rs.p, s);
   }
   word_offsets_kernel<<<grid_for(int64_t(d.V) + 1, threads, cap), threads, 0, s>>>(k1.as<uint64_t>(),
                                                                                     wr.total.as<int64_t>(), d.V, off);

@@ -183,23 +183,6 @@ __global__ void pad_tail_kernel(uint64_t* __restrict__ keys, uint64_t* __restric
   }
 }
 
-__global__ void gather_u64_kernel(const uint64_t* __restrict__ src, const uint32_t* __restrict__ idx, int64_t n,
-                                  uint64_t* __restrict__ dst) {
-  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
-    dst[i] = src[idx[i]];
-}
-
-__global__ void gather_u32_kernel(const uint32_t* __restrict__ src, const uint32_t* __restrict__ idx, int64_t n,
-                                  uint32_t* __restrict__ dst) {
-  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
-    dst[i] = src[idx[i]];
-}
-
-__global__ void iota_kernel(uint32_t* __restrict__ a, int64_t n) {
-  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
-    a[i] = uint32_t(i);
-}
-
 // Run heads of the sorted (file, key) sequence; entries whose key is the pad
 // (kNoKey-derived) are not heads.
 __global__ void run_heads_kernel(const uint64_t* __restrict__ keys, const uint64_t* __restrict__ fkeys, int64_t n,
@@ -256,6 +239,21 @@ __global__ void last_total2_kernel(const int64_t* __restrict__ ex, const int64_t
   if (out2) *out2 = t;
 }
 
+__global__ void pack_hi_lo_kernel(const uint64_t* __restrict__ hi, const uint32_t* __restrict__ lo, int64_t n,
+                                  uint64_t* __restrict__ out) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    out[i] = (hi[i] << 32) | lo[i];
+}
+
+__global__ void unpack_hi_lo_kernel(const uint64_t* __restrict__ in, int64_t n, uint64_t* __restrict__ hi,
+                                    uint32_t* __restrict__ lo) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    const uint64_t x = in[i];
+    hi[i] = x >> 32;
+    lo[i] = uint32_t(x);
+  }
+}
+
 int bits_for(int64_t x) {
   int b = 1;
   while ((int64_t(1) << b) <= x) ++b;
@@ -292,6 +290,9 @@ void reduce_rows(gt_ctx* ctx, uint64_t* keys, uint64_t* fkeys, uint32_t* vals, i
 
 }  // namespace
 
+// Rows sorted by (file, key): a stable sort by key carrying (file << 32 |
+// value) as a 64-bit payload, then a stable sort of that payload on its file
+// bits carrying the key - no permutation is applied afterwards.
 void sort_by_file_key(gt_ctx* ctx, Buf& k0, Buf& f0, Buf& v0, int64_t bound, int key_bits, int file_bits,
                       cudaStream_t s, Windows& out) {
   const int threads = 256, cap = ctx->num_sms * 16;
@@ -301,26 +302,16 @@ void sort_by_file_key(gt_ctx* ctx, Buf& k0, Buf& f0, Buf& v0, int64_t bound, int
   out.n = bound;
   if (bound == 0) return;
   Phase ph2(ctx, "seq_sort", s);
-  Buf pin(ctx, size_t(bound) * 4, s), pkey(ctx, size_t(bound) * 4, s), pfile(ctx, size_t(bound) * 4, s);
-  Buf k1(ctx, size_t(bound) * 8, s), fk(ctx, size_t(bound) * 8, s), comp(ctx, size_t(bound) * 4, s);
-  Buf rs(ctx, radix_scratch_bytes(bound, true, 4), s);
-  iota_kernel<<<grid_for(bound, threads, cap), threads, 0, s>>>(pin.as<uint32_t>(), bound);
+  Buf p0(ctx, size_t(bound) * 8, s), p1(ctx, size_t(bound) * 8, s), k1(ctx, size_t(bound) * 8, s);
+  Buf q(ctx, size_t(bound) * 8, s), rs(ctx, radix_scratch_bytes(bound, true, 8), s);
+  pack_hi_lo_kernel<<<grid_for(bound, threads, cap), threads, 0, s>>>(f0.as<uint64_t>(), v0.as<uint32_t>(), bound,
+                                                                       p0.as<uint64_t>());
   GT_LAUNCH_CHECK();
-  radix_sort_u64(k0.as<uint64_t>(), k1.as<uint64_t>(), pin.p, pkey.p, 4, bound, 0, key_bits, rs.p, s);
-  gather_u64_kernel<<<grid_for(bound, threads, cap), threads, 0, s>>>(f0.as<uint64_t>(), pkey.as<uint32_t>(), bound,
-                                                                       fk.as<uint64_t>());
-  GT_LAUNCH_CHECK();
-  iota_kernel<<<grid_for(bound, threads, cap), threads, 0, s>>>(pin.as<uint32_t>(), bound);
-  GT_LAUNCH_CHECK();
-  radix_sort_u64(fk.as<uint64_t>(), out.fkeys.as<uint64_t>(), pin.p, pfile.p, 4, bound, 0, file_bits, rs.p, s);
-  gather_u64_kernel<<<grid_for(bound, threads, cap), threads, 0, s>>>(k1.as<uint64_t>(), pfile.as<uint32_t>(), bound,
-                                                                       out.keys.as<uint64_t>());
-  GT_LAUNCH_CHECK();
-  gather_u32_kernel<<<grid_for(bound, threads, cap), threads, 0, s>>>(pkey.as<uint32_t>(), pfile.as<uint32_t>(), bound,
-                                                                       comp.as<uint32_t>());
-  GT_LAUNCH_CHECK();
-  gather_u32_kernel<<<grid_for(bound, threads, cap), threads, 0, s>>>(v0.as<uint32_t>(), comp.as<uint32_t>(), bound,
-                                                                       out.vals.as<uint32_t>());
+  radix_sort_u64(k0.as<uint64_t>(), k1.as<uint64_t>(), p0.p, p1.p, 8, bound, 0, key_bits, rs.p, s);
+  radix_sort_u64(p1.as<uint64_t>(), q.as<uint64_t>(), k1.p, out.keys.p, 8, bound, 32, 32 + file_bits, rs.p, s);
+  unpack_hi_lo_kernel<<<grid_for(bound, threads, cap), threads, 0, s>>>(q.as<uint64_t>(), bound,
+                                                                         out.fkeys.as<uint64_t>(),
+                                                                         out.vals.as<uint32_t>());
   GT_LAUNCH_CHECK();
 }
 
@@ -409,12 +400,19 @@ void sorted_windows(gt_grammar* g, bool per_file, cudaStream_t s, Windows& out) 
   sort_by_file_key(ctx, k0, f0, v0, bound, key_bits, bits_for(d.F), s, out);
 }
 
-__global__ void rank_keys_kernel(const uint64_t* __restrict__ cnt, const int64_t* __restrict__ n_dev, int64_t bound,
-                                 uint64_t* __restrict__ k, uint32_t* __restrict__ idx) {
+__global__ void rank_keys_kernel(const uint64_t* __restrict__ cnt, const int32_t* __restrict__ file,
+                                 const int64_t* __restrict__ n_dev, int64_t bound, uint64_t* __restrict__ k) {
   const int64_t n = *n_dev;
-  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < bound; i += int64_t(gridDim.x) * blockDim.x) {
-    k[i] = i < n ? uint64_t(0xffffffffu - uint32_t(cnt[i])) : 0xffffffffull;
-    idx[i] = uint32_t(i);
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < bound; i += int64_t(gridDim.x) * blockDim.x)
+    k[i] = i < n ? (uint64_t(0xffffffffu - uint32_t(cnt[i])) << 32) | uint32_t(file[i]) : 0xffffffff00000000ull;
+}
+
+__global__ void rank_unpack_kernel(const uint64_t* __restrict__ pay, int64_t n, int32_t* __restrict__ file,
+                                   uint64_t* __restrict__ cnt) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    const uint64_t x = pay[i];
+    file[i] = int32_t(uint32_t(x));
+    cnt[i] = uint64_t(0xffffffffu - uint32_t(x >> 32));
   }
 }
 
@@ -466,34 +464,23 @@ gt_result* ranked_from_rows(gt_ctx* ctx, Buf& rkey, Buf& rfile, Buf& rcnt, const
     const int64_t one = 1;
     GT_CUDA(cudaMemcpyAsync(len_off, &one, 8, cudaMemcpyHostToDevice, s));
   } else {
-    Buf k0(ctx, size_t(bound) * 8, s), k1(ctx, size_t(bound) * 8, s), i0(ctx, size_t(bound) * 4, s);
-    Buf p1(ctx, size_t(bound) * 4, s), p2(ctx, size_t(bound) * 4, s), comp(ctx, size_t(bound) * 4, s);
-    Buf rs(ctx, radix_scratch_bytes(bound, true, 4), s), skey(ctx, size_t(bound) * 8, s);
+    // sort 1: stable by count descending, key (~count << 32 | file), payload the
+    // row key; sort 2: stable by row key, payload (~count << 32 | file)
+    Buf k0(ctx, size_t(bound) * 8, s), k1(ctx, size_t(bound) * 8, s), v1(ctx, size_t(bound) * 8, s);
+    Buf pay(ctx, size_t(bound) * 8, s), rs(ctx, radix_scratch_bytes(bound, true, 8), s), skey(ctx, size_t(bound) * 8, s);
     Buf flag(ctx, size_t(bound) * 8, s), pos(ctx, size_t(bound) * 8, s), sc(ctx, scan_scratch_bytes(bound), s);
     // rows past n_dev must carry the pad key so they sort last
     pad_tail_kernel<<<grid_for(bound, threads, cap), threads, 0, s>>>(rkey.as<uint64_t>(), nullptr, nullptr, n_dev,
                                                                        bound, key_pad, 0);
     GT_LAUNCH_CHECK();
-    rank_keys_kernel<<<grid_for(bound, threads, cap), threads, 0, s>>>(rcnt.as<uint64_t>(), n_dev, bound,
-                                                                        k0.as<uint64_t>(), i0.as<uint32_t>());
+    rank_keys_kernel<<<grid_for(bound, threads, cap), threads, 0, s>>>(rcnt.as<uint64_t>(), rfile.as<int32_t>(), n_dev,
+                                                                        bound, k0.as<uint64_t>());
     GT_LAUNCH_CHECK();
-    radix_sort_u64(k0.as<uint64_t>(), k1.as<uint64_t>(), i0.p, p1.p, 4, bound, 0, 32, rs.p, s);
-    gather_u64_kernel<<<grid_for(bound, threads, cap), threads, 0, s>>>(rkey.as<uint64_t>(), p1.as<uint32_t>(), bound,
-                                                                         k0.as<uint64_t>());
-    GT_LAUNCH_CHECK();
-    iota_kernel<<<grid_for(bound, threads, cap), threads, 0, s>>>(i0.as<uint32_t>(), bound);
-    GT_LAUNCH_CHECK();
+    radix_sort_u64(k0.as<uint64_t>(), k1.as<uint64_t>(), rkey.p, v1.p, 8, bound, 32, 64, rs.p, s);
     int kbits = 1;
     while (kbits < 64 && (uint64_t(1) << kbits) <= key_pad) ++kbits;
-    radix_sort_u64(k0.as<uint64_t>(), skey.as<uint64_t>(), i0.p, p2.p, 4, bound, 0, kbits, rs.p, s);
-    gather_u32_kernel<<<grid_for(bound, threads, cap), threads, 0, s>>>(p1.as<uint32_t>(), p2.as<uint32_t>(), bound,
-                                                                         comp.as<uint32_t>());
-    GT_LAUNCH_CHECK();
-    gather_u32_kernel<<<grid_for(bound, threads, cap), threads, 0, s>>>(rfile.as<uint32_t>(), comp.as<uint32_t>(),
-                                                                         bound, reinterpret_cast<uint32_t*>(ofile));
-    GT_LAUNCH_CHECK();
-    gather_u64_kernel<<<grid_for(bound, threads, cap), threads, 0, s>>>(rcnt.as<uint64_t>(), comp.as<uint32_t>(),
-                                                                         bound, ocnt);
+    radix_sort_u64(v1.as<uint64_t>(), skey.as<uint64_t>(), k1.p, pay.p, 8, bound, 0, kbits, rs.p, s);
+    rank_unpack_kernel<<<grid_for(bound, threads, cap), threads, 0, s>>>(pay.as<uint64_t>(), bound, ofile, ocnt);
     GT_LAUNCH_CHECK();
     key_heads_kernel<<<grid_for(bound, threads, cap), threads, 0, s>>>(skey.as<uint64_t>(), n_dev, bound,
                                                                         flag.as<int64_t>());

@@ -117,11 +117,17 @@ __global__ void __launch_bounds__(kRsThreads) radix_upsweep_kernel(const uint64_
   for (int i = threadIdx.x; i < kRsWarps * 256; i += kRsThreads) h[i / 256][i % 256] = 0;
   __syncthreads();
   const int64_t wbase = int64_t(blockIdx.x) * kRsTile + int64_t(warp) * 32 * kRsItems;
-#pragma unroll 4
+  uint64_t key[kRsItems];  // every load issued before the first ballot
+#pragma unroll
+  for (int it = 0; it < kRsItems; ++it) {
+    const int64_t idx = wbase + it * 32 + lane;
+    key[it] = idx < n ? keys[idx] : 0;
+  }
+#pragma unroll
   for (int it = 0; it < kRsItems; ++it) {
     const int64_t idx = wbase + it * 32 + lane;
     const bool valid = idx < n;
-    const uint32_t d = valid ? uint32_t(keys[idx] >> shift) & mask : 0u;
+    const uint32_t d = valid ? uint32_t(key[it] >> shift) & mask : 0u;
     const unsigned peers = warp_digit_peers(d, __ballot_sync(0xffffffffu, valid));
     // the lowest lane of each digit group adds the group; the counters are warp-private
     if (valid && (peers & ((1u << lane) - 1u)) == 0) h[warp][d] += __popc(peers);
