@@ -98,6 +98,7 @@ class ClockSampler:
 # DRAM bytes (read + write) per launch from one `ncu --set full` capture of the
 # kernel as it stands (see the named profile); None once the kernel changes.
 NCU_TRAFFIC = {
+    "wc_partition_kernel": (221.78e6, "profiles/wc_partition_kernel_multi64_50m.md"),
     "tv_hist_kernel": (205.80e6, "profiles/tv_hist_kernel_multi64_50m.md"),
 }
 
@@ -248,7 +249,9 @@ def word_count_alone(B, ctx, gh, out, stream, info, hbm, reps=20):
     ach = 4 * info["num_syms"] / (part_ms / 1e3) / 1e9
     return {"ms_per_query": ms, "tokens_per_s": info["num_tokens"] / (ms / 1e3),
             "partition_kernel": {"ms_per_launch": part_ms, "achieved_gbs": ach, "frac_of_measured_hbm": ach / hbm,
-                                 "algorithmic_bytes_per_launch": 4 * info["num_syms"]}}
+                                 "algorithmic_bytes_per_launch": 4 * info["num_syms"],
+                                 "traffic": NCU_TRAFFIC.get("wc_partition_kernel", (None, None))[0],
+                                 "traffic_source": NCU_TRAFFIC.get("wc_partition_kernel", (None, None))[1]}}
 
 
 def many_files(B, ctx, reps=3):

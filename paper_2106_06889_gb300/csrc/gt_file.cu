@@ -464,23 +464,49 @@ __global__ void tv_file_off_kernel(const int64_t* __restrict__ off, int nb, int3
 }
 
 // Inverted index: files holding each word (bit set in that file's piece).
+// A warp takes 32 consecutive words - one 32-bit occupancy word per file -
+// lane f loads file f's (and file f + 32's) word, and one ballot per bit
+// position gives each word's set of files.
+__device__ __forceinline__ void ii_masks(const uint32_t* __restrict__ bits, int nb, int32_t F, int64_t w0, int lane,
+                                         uint32_t& m_lo, uint32_t& m_hi) {
+  const int64_t b = w0 >> kFBLog2, t = (w0 & (kFBucket - 1)) >> 5;
+  m_lo = lane < F ? bits[(int64_t(lane) * nb + b) * kTvThreads + t] : 0u;
+  m_hi = lane + 32 < F ? bits[(int64_t(lane + 32) * nb + b) * kTvThreads + t] : 0u;
+}
+
 __global__ void ii_count_kernel(const uint32_t* __restrict__ bits, int nb, int32_t F, int32_t V,
                                 int64_t* __restrict__ cnt) {
-  for (int64_t w = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; w < V; w += int64_t(gridDim.x) * blockDim.x) {
-    const int64_t b = w >> kFBLog2, l = w & (kFBucket - 1);
-    int c = 0;
-    for (int32_t f = 0; f < F; ++f) c += (bits[(int64_t(f) * nb + b) * kTvThreads + (l >> 5)] >> (l & 31)) & 1u;
-    cnt[w] = c;
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t w0 = ((blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5) * 32; w0 < V; w0 += nwarps * 32) {
+    uint32_t lo, hi;
+    ii_masks(bits, nb, F, w0, lane, lo, hi);
+    int mine = 0;
+#pragma unroll
+    for (int l = 0; l < 32; ++l) {
+      const int c = __popc(__ballot_sync(0xffffffffu, (lo >> l) & 1u)) + __popc(__ballot_sync(0xffffffffu, (hi >> l) & 1u));
+      if (lane == l) mine = c;
+    }
+    if (w0 + lane < V) cnt[w0 + lane] = mine;
   }
 }
 
 __global__ void ii_fill_kernel(const uint32_t* __restrict__ bits, int nb, int32_t F, int32_t V,
                                const int64_t* __restrict__ off, int32_t* __restrict__ files) {
-  for (int64_t w = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; w < V; w += int64_t(gridDim.x) * blockDim.x) {
-    const int64_t b = w >> kFBLog2, l = w & (kFBucket - 1);
-    int64_t o = off[w];
-    for (int32_t f = 0; f < F; ++f)
-      if ((bits[(int64_t(f) * nb + b) * kTvThreads + (l >> 5)] >> (l & 31)) & 1u) files[o++] = f;
+  const int lane = threadIdx.x & 31;
+  const unsigned below = (1u << lane) - 1u;
+  const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t w0 = ((blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5) * 32; w0 < V; w0 += nwarps * 32) {
+    uint32_t lo, hi;
+    ii_masks(bits, nb, F, w0, lane, lo, hi);
+    const int64_t my_off = w0 + lane < V ? off[w0 + lane] : 0;
+    for (int l = 0; l < 32 && w0 + l < V; ++l) {
+      const unsigned a = __ballot_sync(0xffffffffu, (lo >> l) & 1u);
+      const unsigned c = __ballot_sync(0xffffffffu, (hi >> l) & 1u);
+      const int64_t o = __shfl_sync(0xffffffffu, my_off, l);
+      if ((a >> lane) & 1u) files[o + __popc(a & below)] = lane;
+      if ((c >> lane) & 1u) files[o + __popc(a) + __popc(c & below)] = lane + 32;
+    }
   }
 }
 
