@@ -277,6 +277,9 @@ int64_t gt_kernel_launches(void);
  *                   not while profiling is enabled.  0: launch kernel by kernel.
  *   "wc_slices"     histogram CTAs per 16k-word bucket in the word count
  *                   (1..64); 0 (default): about 3 x SMs / buckets.
+ *   "bu_local"      1 (default): bottom-up word rows of grammars whose files
+ *                   all have at most 8192 tokens are built per file in shared
+ *                   memory; 0: always by the global (file, word) sort.
  *   "file_strategy" per-file analytics (term vector, inverted index, per-file
  *                   sequence count, ranked index): 0 (default) picks top-down
  *                   for at most 64 files and bottom-up otherwise (the paper's

@@ -704,7 +704,7 @@ GT_API int64_t gt_kernel_launches(void) { return gt::g_launches.load(); }
 
 GT_API gt_status gt_set_param(gt_ctx* ctx, const char* name, int64_t value) {
   if (!ctx || !name) return GT_EINVAL;
-  static const char* known[] = {"wc_aggregate", "use_graphs", "file_strategy", "wc_slices"};
+  static const char* known[] = {"wc_aggregate", "use_graphs", "file_strategy", "wc_slices", "bu_local"};
   for (const char* k : known)
     if (std::strcmp(k, name) == 0) {
       ctx->params[name] = value;

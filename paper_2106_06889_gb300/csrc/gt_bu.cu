@@ -229,11 +229,228 @@ __global__ void word_offsets_kernel(const uint64_t* __restrict__ sk, const int64
   }
 }
 
+// ---- small files: expanded and sorted in shared memory, one CTA per file ----
+//
+// When every file has at most kLocalMax tokens, a CTA expands one file into
+// shared memory (root symbols of the file, each rule reference walked), sorts
+// its words with an LSD radix sort in shared memory (8-bit digits, ranks by
+// ballot multisplit, stable), and run-length encodes them into the file's
+// (word, count) rows, written to a slot of the file's length.  A second pass
+// packs the slots.  No global sort is involved.
+
+constexpr int kLocalThreads = 256;
+constexpr int kLocalWarps = kLocalThreads / 32;
+constexpr int64_t kLocalMax = 8192;
+
+// Exclusive prefix over the CTA (kLocalThreads threads); *total gets the sum.
+__device__ __forceinline__ int local_scan(int v, int* total, int* warp_tot) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) warp_tot[warp] = incl;
+  __syncthreads();
+  int before = 0, all = 0;
+#pragma unroll
+  for (int w = 0; w < kLocalWarps; ++w) {
+    const int t = warp_tot[w];
+    before += w < warp ? t : 0;
+    all += t;
+  }
+  __syncthreads();
+  *total = all;
+  return before + incl - v;
+}
+
+__device__ __forceinline__ unsigned local_peers(uint32_t dg, unsigned active) {
+  unsigned peers = active;
+#pragma unroll
+  for (int b = 0; b < 8; ++b) {
+    const bool bit = (dg >> b) & 1u;
+    const unsigned bal = __ballot_sync(0xffffffffu, bit);
+    peers &= bit ? bal : ~bal;
+  }
+  return peers;
+}
+
+__global__ void __launch_bounds__(kLocalThreads) local_word_rows_kernel(const DevGrammar d, int cap, int kbw,
+                                                                        const int64_t* __restrict__ slot_off,
+                                                                        int32_t* __restrict__ slot_word,
+                                                                        uint32_t* __restrict__ slot_cnt,
+                                                                        int64_t* __restrict__ nrows) {
+  extern __shared__ __align__(16) uint32_t lsm[];
+  uint32_t* bufa = lsm;
+  uint32_t* bufb = lsm + cap;
+  __shared__ uint32_t wcnt[kLocalWarps][256];
+  __shared__ uint32_t dstart[256];
+  __shared__ uint32_t dtot[kLocalWarps];
+  __shared__ int warp_tot[kLocalWarps];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  for (int32_t f = blockIdx.x; f < d.F; f += gridDim.x) {
+    const int64_t r0 = d.file_off[f], r1 = d.file_off[f + 1];
+    const int n = int(d.file_len[f]);
+    // 1. expansion into bufa
+    int base = 0;
+    for (int64_t j0 = r0; j0 < r1; j0 += kLocalThreads) {
+      const int64_t j = j0 + tid;
+      const int32_t sy = j < r1 ? d.sym[j] : 0;
+      const int len = j < r1 ? (sy < d.V ? 1 : int(d.exp_len[sy - d.V])) : 0;
+      int chunk;
+      int o = base + local_scan(len, &chunk, warp_tot);
+      if (j < r1) {
+        if (sy < d.V) {
+          bufa[o] = uint32_t(sy);
+        } else {
+          walk_rule(d, sy - d.V, [&](int32_t w) { bufa[o++] = uint32_t(w); });
+        }
+      }
+      base += chunk;
+    }
+    __syncthreads();
+    // 2. radix sort of the n words, bufa <-> bufb
+    uint32_t* src = bufa;
+    uint32_t* dst = bufb;
+    const int per = (n + kLocalWarps * 32 - 1) / (kLocalWarps * 32) * 32;  // warp slice, a multiple of 32
+    const int lo = min(n, warp * per), hi = min(n, lo + per);
+    for (int shift = 0; shift < kbw; shift += 8) {
+      const uint32_t mask = kbw - shift >= 8 ? 0xffu : ((1u << (kbw - shift)) - 1u);
+      for (int q = lane; q < 256; q += 32) wcnt[warp][q] = 0;
+      __syncwarp();
+      for (int i0 = lo; i0 < hi; i0 += 32) {
+        const int i = i0 + lane;
+        const bool valid = i < hi;
+        const uint32_t dg = valid ? (src[i] >> shift) & mask : 0u;
+        const unsigned peers = local_peers(dg, __ballot_sync(0xffffffffu, valid));
+        if (valid && (peers & lt) == 0) wcnt[warp][dg] += __popc(peers);
+        __syncwarp();
+      }
+      __syncthreads();
+      {  // thread = digit: exclusive over warps, then over digits
+        const int dg = tid;
+        uint32_t run = 0;
+#pragma unroll
+        for (int w = 0; w < kLocalWarps; ++w) {
+          const uint32_t c = wcnt[w][dg];
+          wcnt[w][dg] = run;
+          run += c;
+        }
+        uint32_t incl = run;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += t;
+        }
+        if (lane == 31) dtot[warp] = incl;
+        __syncthreads();
+        uint32_t pre = 0;
+#pragma unroll
+        for (int w = 0; w < kLocalWarps; ++w) pre += w < warp ? dtot[w] : 0u;
+        dstart[dg] = pre + incl - run;
+      }
+      __syncthreads();
+      for (int i0 = lo; i0 < hi; i0 += 32) {
+        const int i = i0 + lane;
+        const bool valid = i < hi;
+        const uint32_t key = valid ? src[i] : 0u;
+        const uint32_t dg = (key >> shift) & mask;
+        const unsigned peers = local_peers(dg, __ballot_sync(0xffffffffu, valid));
+        const uint32_t before = wcnt[warp][dg];
+        const uint32_t r = __popc(peers & lt);
+        if (valid) dst[dstart[dg] + before + r] = key;
+        __syncwarp();
+        if (valid && r == 0) wcnt[warp][dg] = before + __popc(peers);
+        __syncwarp();
+      }
+      __syncthreads();
+      uint32_t* t = src;
+      src = dst;
+      dst = t;
+    }
+    // 3. run-length encoding: head positions into dst, then (word, count) rows
+    int rows = 0;
+    for (int i0 = 0; i0 < n; i0 += kLocalThreads) {
+      const int i = i0 + tid;
+      const int head = (i < n && (i == 0 || src[i] != src[i - 1])) ? 1 : 0;
+      int chunk;
+      const int at = rows + local_scan(head, &chunk, warp_tot);
+      if (head) dst[at] = uint32_t(i);
+      rows += chunk;
+    }
+    __syncthreads();
+    const int64_t so = slot_off[f];
+    for (int k = tid; k < rows; k += kLocalThreads) {
+      const uint32_t a = dst[k], b = k + 1 < rows ? dst[k + 1] : uint32_t(n);
+      slot_word[so + k] = int32_t(src[a]);
+      slot_cnt[so + k] = b - a;
+    }
+    if (tid == 0) nrows[f] = rows;
+    __syncthreads();
+  }
+}
+
+// Token offsets of the files (slots) from their lengths.
+__global__ void file_len_i64_kernel(const uint64_t* __restrict__ len, int32_t F, int64_t* __restrict__ out) {
+  for (int32_t f = blockIdx.x * blockDim.x + threadIdx.x; f <= F; f += gridDim.x * blockDim.x)
+    out[f] = f < F ? int64_t(len[f]) : 0;
+}
+
+// Pack the slots: warp per file.
+__global__ void local_pack_kernel(int32_t F, const int64_t* __restrict__ slot_off, const int64_t* __restrict__ row_off,
+                                  const int32_t* __restrict__ slot_word, const uint32_t* __restrict__ slot_cnt,
+                                  int32_t* __restrict__ word, int32_t* __restrict__ file, uint64_t* __restrict__ cnt) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t f = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5; f < F; f += nwarps) {
+    const int64_t so = slot_off[f], ro = row_off[f], n = row_off[f + 1] - ro;
+    for (int64_t k = lane; k < n; k += 32) {
+      word[ro + k] = slot_word[so + k];
+      file[ro + k] = int32_t(f);
+      cnt[ro + k] = slot_cnt[so + k];
+    }
+  }
+}
+
 // (file, word, count) rows of every file, sorted by (file, word).
 struct WordRows {
   Buf word, file, cnt, total;
   int64_t bound = 0;
 };
+
+void bu_local_word_rows(gt_grammar* g, int kbw, cudaStream_t s, WordRows& out) {
+  gt_ctx* ctx = g->ctx;
+  const DevGrammar& d = g->d;
+  const int64_t N = int64_t(d.N);
+  const int cap = int(std::max<int64_t>(256, (g->max_file_len + 255) / 256 * 256));
+  Phase ph(ctx, "bu_local", s);
+  Buf soff(ctx, size_t(d.F + 1) * 8, s), flen(ctx, size_t(d.F + 1) * 8, s), sc(ctx, scan_scratch_bytes(d.F + 1), s);
+  Buf sw(ctx, size_t(N) * 4, s), scn(ctx, size_t(N) * 4, s), nr(ctx, size_t(d.F + 1) * 8, s);
+  Buf roff(ctx, size_t(d.F + 1) * 8, s);
+  out.bound = N;
+  out.word = Buf(ctx, size_t(N) * 4, s);
+  out.file = Buf(ctx, size_t(N) * 4, s);
+  out.cnt = Buf(ctx, size_t(N) * 8, s);
+  out.total = Buf(ctx, 8, s);
+  file_len_i64_kernel<<<grid_for(int64_t(d.F) + 1, 256, ctx->num_sms * 8), 256, 0, s>>>(d.file_len, d.F,
+                                                                                     flen.as<int64_t>());
+  GT_LAUNCH_CHECK();
+  exclusive_scan_i64(flen.as<int64_t>(), soff.as<int64_t>(), d.F + 1, sc.p, s);
+  const size_t smem = size_t(cap) * 8;
+  GT_CUDA(cudaFuncSetAttribute(local_word_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+  GT_CUDA(cudaMemsetAsync(nr.as<int64_t>() + d.F, 0, 8, s));
+  local_word_rows_kernel<<<unsigned(std::min<int64_t>(d.F, 65535)), kLocalThreads, smem, s>>>(
+      d, cap, kbw, soff.as<int64_t>(), sw.as<int32_t>(), scn.as<uint32_t>(), nr.as<int64_t>());
+  GT_LAUNCH_CHECK();
+  exclusive_scan_i64(nr.as<int64_t>(), roff.as<int64_t>(), d.F + 1, sc.p, s);
+  GT_CUDA(cudaMemcpyAsync(out.total.p, roff.as<int64_t>() + d.F, 8, cudaMemcpyDeviceToDevice, s));
+  local_pack_kernel<<<grid_for(int64_t(d.F) * 32, 256, ctx->num_sms * 16), 256, 0, s>>>(
+      d.F, soff.as<int64_t>(), roff.as<int64_t>(), sw.as<int32_t>(), scn.as<uint32_t>(), out.word.as<int32_t>(),
+      out.file.as<int32_t>(), out.cnt.as<uint64_t>());
+  GT_LAUNCH_CHECK();
+}
 
 void bu_word_rows(gt_grammar* g, cudaStream_t s, WordRows& out) {
   gt_ctx* ctx = g->ctx;
@@ -243,6 +460,10 @@ void bu_word_rows(gt_grammar* g, cudaStream_t s, WordRows& out) {
   if (d.N >= (uint64_t(1) << 32)) fail(GT_EOVERFLOW, "per-file analytics need fewer than 2^32 tokens per grammar");
   const int kbw = bits_for(d.V);
   const int fb = bits_for(d.F);
+  if (g->max_file_len <= kLocalMax && gparam(g, "bu_local", 1)) {
+    bu_local_word_rows(g, kbw, s, out);
+    return;
+  }
   if (kbw + fb > 63) fail(GT_EOVERFLOW, "too many files x words for 64-bit (file, word) keys");
   const uint64_t pad = uint64_t(uint32_t(d.F)) << kbw;
   const int64_t n = d.root_len + g->bu_words;

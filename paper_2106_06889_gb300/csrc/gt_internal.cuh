@@ -179,6 +179,7 @@ struct gt_grammar {
   int64_t fsym_bound = 0;         // rule body symbols visited once per such pair
   int64_t bu_words = 0;           // sum over distinct (file, root child) pairs of the child's length
   int64_t bu_windows = 0;         // ... and of the child's 3-word windows
+  int64_t max_file_len = 0;       // tokens of the longest file
   std::vector<void*> owned;      // device allocations to free with the grammar
   // word-count launch sequences captured as CUDA graphs, keyed by output buffer
   struct WcGraph {

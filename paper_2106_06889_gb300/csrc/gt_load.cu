@@ -311,6 +311,14 @@ __global__ void root_file_final_kernel(const int64_t* __restrict__ file_off, int
   }
 }
 
+__global__ void max_u64_kernel(const uint64_t* __restrict__ x, int64_t n, unsigned long long* __restrict__ out) {
+  unsigned long long m = 0;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    m = max(m, (unsigned long long)x[i]);
+  for (int o = 16; o; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
+}
+
 // Rule of every symbol from the tile holding the end of the root onwards.
 __global__ void sym_rule_kernel(const int64_t* __restrict__ rule_off, int32_t R, int64_t G, int64_t root_len,
                                 int64_t base, int64_t n, int32_t* __restrict__ out) {
@@ -656,18 +664,23 @@ void load_build_dag(gt_grammar* g, cudaStream_t s) {
     GT_CUDA(cudaStreamSynchronize(s));
   }
 
-  // ---- sizes of the bottom-up per-file rows ----
+  // ---- sizes of the bottom-up per-file rows, longest file ----
   {
-    GT_CUDA(cudaMemsetAsync(ctr + 12, 0, 16, s));
+    GT_CUDA(cudaMemsetAsync(ctr + 12, 0, 24, s));
     if (d.ER > 0) {
       bu_sizes_kernel<<<grid_for(d.ER, threads, cap), threads, 0, s>>>(d.redge_child, d.ER, d.exp_len, ctr + 12);
       GT_LAUNCH_CHECK();
     }
-    unsigned long long hb[2];
-    GT_CUDA(cudaMemcpyAsync(hb, ctr + 12, 16, cudaMemcpyDeviceToHost, s));
+    if (F > 0) {
+      max_u64_kernel<<<grid_for(F, threads, cap), threads, 0, s>>>(d.file_len, F, ctr + 14);
+      GT_LAUNCH_CHECK();
+    }
+    unsigned long long hb[3];
+    GT_CUDA(cudaMemcpyAsync(hb, ctr + 12, 24, cudaMemcpyDeviceToHost, s));
     GT_CUDA(cudaStreamSynchronize(s));
     g->bu_words = int64_t(hb[0]);
     g->bu_windows = int64_t(hb[1]);
+    g->max_file_len = int64_t(hb[2]);
   }
 
   // ---- tiles ----

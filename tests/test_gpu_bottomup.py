@@ -84,13 +84,18 @@ def check_all(ctx, g):
         B.gt_free_grammar(gh)
 
 
+@pytest.mark.parametrize("local", [1, 0], ids=["smem_files", "global_sort"])
 @pytest.mark.parametrize("name,g", GRAMMARS, ids=IDS)
-def test_forced_bottom_up(ctx, name, g):
+def test_forced_bottom_up(ctx, name, g, local):
+    """Bottom-up forced; word rows either per file in shared memory (files of
+    at most 8192 tokens) or by the global (file, word) sort."""
     B.gt_set_param(ctx, "file_strategy", 2)
+    B.gt_set_param(ctx, "bu_local", local)
     try:
         check_all(ctx, g)
     finally:
         B.gt_set_param(ctx, "file_strategy", 0)
+        B.gt_set_param(ctx, "bu_local", 1)
 
 
 @pytest.mark.parametrize("name,g", [x for x in GRAMMARS if x[0].startswith("nested_")],
