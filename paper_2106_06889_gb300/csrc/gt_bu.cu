@@ -276,6 +276,117 @@ __device__ __forceinline__ unsigned local_peers(uint32_t dg, unsigned active) {
   return peers;
 }
 
+// Stable LSD radix sort of keys[0, n) over bits [0, key_bits) in shared
+// memory, 8-bit digits, ping-ponging between a and b; returns the buffer that
+// holds the result.  Warp w ranks its contiguous slice 32 keys at a time.
+template <typename K>
+__device__ K* local_sort(K* a, K* b, int n, int key_bits, uint32_t (*wcnt)[256], uint32_t* dstart, uint32_t* dtot) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  K* src = a;
+  K* dst = b;
+  const int per = (n + kLocalWarps * 32 - 1) / (kLocalWarps * 32) * 32;  // warp slice, a multiple of 32
+  const int lo = min(n, warp * per), hi = min(n, lo + per);
+  for (int shift = 0; shift < key_bits; shift += 8) {
+    const uint32_t mask = key_bits - shift >= 8 ? 0xffu : ((1u << (key_bits - shift)) - 1u);
+    for (int q = lane; q < 256; q += 32) wcnt[warp][q] = 0;
+    __syncwarp();
+    for (int i0 = lo; i0 < hi; i0 += 32) {
+      const int i = i0 + lane;
+      const bool valid = i < hi;
+      const uint32_t dg = valid ? uint32_t(src[i] >> shift) & mask : 0u;
+      const unsigned peers = local_peers(dg, __ballot_sync(0xffffffffu, valid));
+      if (valid && (peers & lt) == 0) wcnt[warp][dg] += __popc(peers);
+      __syncwarp();
+    }
+    __syncthreads();
+    {  // thread = digit: exclusive over warps, then over digits
+      const int dg = tid;
+      uint32_t run = 0;
+#pragma unroll
+      for (int w = 0; w < kLocalWarps; ++w) {
+        const uint32_t c = wcnt[w][dg];
+        wcnt[w][dg] = run;
+        run += c;
+      }
+      uint32_t incl = run;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+      }
+      if (lane == 31) dtot[warp] = incl;
+      __syncthreads();
+      uint32_t pre = 0;
+#pragma unroll
+      for (int w = 0; w < kLocalWarps; ++w) pre += w < warp ? dtot[w] : 0u;
+      dstart[dg] = pre + incl - run;
+    }
+    __syncthreads();
+    for (int i0 = lo; i0 < hi; i0 += 32) {
+      const int i = i0 + lane;
+      const bool valid = i < hi;
+      const K key = valid ? src[i] : K(0);
+      const uint32_t dg = uint32_t(key >> shift) & mask;
+      const unsigned peers = local_peers(dg, __ballot_sync(0xffffffffu, valid));
+      const uint32_t before = wcnt[warp][dg];
+      const uint32_t r = __popc(peers & lt);
+      if (valid) dst[dstart[dg] + before + r] = key;
+      __syncwarp();
+      if (valid && r == 0) wcnt[warp][dg] = before + __popc(peers);
+      __syncwarp();
+    }
+    __syncthreads();
+    K* t = src;
+    src = dst;
+    dst = t;
+  }
+  return src;
+}
+
+// Expand file f into words[0, n) (its root symbols, each reference walked);
+// returns n.
+__device__ __forceinline__ int local_expand(const DevGrammar& d, int32_t f, uint32_t* words, int* warp_tot) {
+  const int tid = threadIdx.x;
+  const int64_t r0 = d.file_off[f], r1 = d.file_off[f + 1];
+  int base = 0;
+  for (int64_t j0 = r0; j0 < r1; j0 += kLocalThreads) {
+    const int64_t j = j0 + tid;
+    const int32_t sy = j < r1 ? d.sym[j] : 0;
+    const int len = j < r1 ? (sy < d.V ? 1 : int(d.exp_len[sy - d.V])) : 0;
+    int chunk;
+    int o = base + local_scan(len, &chunk, warp_tot);
+    if (j < r1) {
+      if (sy < d.V) {
+        words[o] = uint32_t(sy);
+      } else {
+        walk_rule(d, sy - d.V, [&](int32_t w) { words[o++] = uint32_t(w); });
+      }
+    }
+    base += chunk;
+  }
+  __syncthreads();
+  return base;
+}
+
+// Run-length encoding of sorted keys[0, n): head positions go to heads[];
+// returns the number of distinct keys.
+template <typename K>
+__device__ __forceinline__ int local_heads(const K* keys, int n, uint32_t* heads, int* warp_tot) {
+  const int tid = threadIdx.x;
+  int rows = 0;
+  for (int i0 = 0; i0 < n; i0 += kLocalThreads) {
+    const int i = i0 + tid;
+    const int head = (i < n && (i == 0 || keys[i] != keys[i - 1])) ? 1 : 0;
+    int chunk;
+    const int at = rows + local_scan(head, &chunk, warp_tot);
+    if (head) heads[at] = uint32_t(i);
+    rows += chunk;
+  }
+  __syncthreads();
+  return rows;
+}
+
 __global__ void __launch_bounds__(kLocalThreads) local_word_rows_kernel(const DevGrammar d, int cap, int kbw,
                                                                         const int64_t* __restrict__ slot_off,
                                                                         int32_t* __restrict__ slot_word,
@@ -288,99 +399,12 @@ __global__ void __launch_bounds__(kLocalThreads) local_word_rows_kernel(const De
   __shared__ uint32_t dstart[256];
   __shared__ uint32_t dtot[kLocalWarps];
   __shared__ int warp_tot[kLocalWarps];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const unsigned lt = (1u << lane) - 1u;
+  const int tid = threadIdx.x;
   for (int32_t f = blockIdx.x; f < d.F; f += gridDim.x) {
-    const int64_t r0 = d.file_off[f], r1 = d.file_off[f + 1];
-    const int n = int(d.file_len[f]);
-    // 1. expansion into bufa
-    int base = 0;
-    for (int64_t j0 = r0; j0 < r1; j0 += kLocalThreads) {
-      const int64_t j = j0 + tid;
-      const int32_t sy = j < r1 ? d.sym[j] : 0;
-      const int len = j < r1 ? (sy < d.V ? 1 : int(d.exp_len[sy - d.V])) : 0;
-      int chunk;
-      int o = base + local_scan(len, &chunk, warp_tot);
-      if (j < r1) {
-        if (sy < d.V) {
-          bufa[o] = uint32_t(sy);
-        } else {
-          walk_rule(d, sy - d.V, [&](int32_t w) { bufa[o++] = uint32_t(w); });
-        }
-      }
-      base += chunk;
-    }
-    __syncthreads();
-    // 2. radix sort of the n words, bufa <-> bufb
-    uint32_t* src = bufa;
-    uint32_t* dst = bufb;
-    const int per = (n + kLocalWarps * 32 - 1) / (kLocalWarps * 32) * 32;  // warp slice, a multiple of 32
-    const int lo = min(n, warp * per), hi = min(n, lo + per);
-    for (int shift = 0; shift < kbw; shift += 8) {
-      const uint32_t mask = kbw - shift >= 8 ? 0xffu : ((1u << (kbw - shift)) - 1u);
-      for (int q = lane; q < 256; q += 32) wcnt[warp][q] = 0;
-      __syncwarp();
-      for (int i0 = lo; i0 < hi; i0 += 32) {
-        const int i = i0 + lane;
-        const bool valid = i < hi;
-        const uint32_t dg = valid ? (src[i] >> shift) & mask : 0u;
-        const unsigned peers = local_peers(dg, __ballot_sync(0xffffffffu, valid));
-        if (valid && (peers & lt) == 0) wcnt[warp][dg] += __popc(peers);
-        __syncwarp();
-      }
-      __syncthreads();
-      {  // thread = digit: exclusive over warps, then over digits
-        const int dg = tid;
-        uint32_t run = 0;
-#pragma unroll
-        for (int w = 0; w < kLocalWarps; ++w) {
-          const uint32_t c = wcnt[w][dg];
-          wcnt[w][dg] = run;
-          run += c;
-        }
-        uint32_t incl = run;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
-          if (lane >= o) incl += t;
-        }
-        if (lane == 31) dtot[warp] = incl;
-        __syncthreads();
-        uint32_t pre = 0;
-#pragma unroll
-        for (int w = 0; w < kLocalWarps; ++w) pre += w < warp ? dtot[w] : 0u;
-        dstart[dg] = pre + incl - run;
-      }
-      __syncthreads();
-      for (int i0 = lo; i0 < hi; i0 += 32) {
-        const int i = i0 + lane;
-        const bool valid = i < hi;
-        const uint32_t key = valid ? src[i] : 0u;
-        const uint32_t dg = (key >> shift) & mask;
-        const unsigned peers = local_peers(dg, __ballot_sync(0xffffffffu, valid));
-        const uint32_t before = wcnt[warp][dg];
-        const uint32_t r = __popc(peers & lt);
-        if (valid) dst[dstart[dg] + before + r] = key;
-        __syncwarp();
-        if (valid && r == 0) wcnt[warp][dg] = before + __popc(peers);
-        __syncwarp();
-      }
-      __syncthreads();
-      uint32_t* t = src;
-      src = dst;
-      dst = t;
-    }
-    // 3. run-length encoding: head positions into dst, then (word, count) rows
-    int rows = 0;
-    for (int i0 = 0; i0 < n; i0 += kLocalThreads) {
-      const int i = i0 + tid;
-      const int head = (i < n && (i == 0 || src[i] != src[i - 1])) ? 1 : 0;
-      int chunk;
-      const int at = rows + local_scan(head, &chunk, warp_tot);
-      if (head) dst[at] = uint32_t(i);
-      rows += chunk;
-    }
-    __syncthreads();
+    const int n = local_expand(d, f, bufa, warp_tot);
+    uint32_t* src = local_sort(bufa, bufb, n, kbw, wcnt, dstart, dtot);
+    uint32_t* dst = src == bufa ? bufb : bufa;
+    const int rows = local_heads(src, n, dst, warp_tot);
     const int64_t so = slot_off[f];
     for (int k = tid; k < rows; k += kLocalThreads) {
       const uint32_t a = dst[k], b = k + 1 < rows ? dst[k + 1] : uint32_t(n);
@@ -389,6 +413,72 @@ __global__ void __launch_bounds__(kLocalThreads) local_word_rows_kernel(const De
     }
     if (tid == 0) nrows[f] = rows;
     __syncthreads();
+  }
+}
+
+// Per-file 3-word windows of small files: the file expanded in shared memory,
+// its window keys built and sorted there, one (key, count) row per distinct
+// window.  The words alias the second key buffer until the keys are built.
+__global__ void __launch_bounds__(kLocalThreads) local_window_rows_kernel(const DevGrammar d, int cap, int kb,
+                                                                          int key_bits,
+                                                                          const int64_t* __restrict__ slot_off,
+                                                                          uint64_t* __restrict__ slot_key,
+                                                                          uint32_t* __restrict__ slot_cnt,
+                                                                          int64_t* __restrict__ nrows) {
+  extern __shared__ __align__(16) uint32_t lsm[];
+  uint64_t* ka = reinterpret_cast<uint64_t*>(lsm);
+  uint64_t* kz = ka + cap;
+  uint32_t* words = reinterpret_cast<uint32_t*>(kz);
+  __shared__ uint32_t wcnt[kLocalWarps][256];
+  __shared__ uint32_t dstart[256];
+  __shared__ uint32_t dtot[kLocalWarps];
+  __shared__ int warp_tot[kLocalWarps];
+  const int tid = threadIdx.x;
+  for (int32_t f = blockIdx.x; f < d.F; f += gridDim.x) {
+    const int n = local_expand(d, f, words, warp_tot);
+    const int nk = n >= 3 ? n - 2 : 0;
+    for (int i = tid; i < nk; i += kLocalThreads)
+      ka[i] = pack_compact(int32_t(words[i]), int32_t(words[i + 1]), int32_t(words[i + 2]), kb);
+    __syncthreads();
+    uint64_t* src = local_sort(ka, kz, nk, key_bits, wcnt, dstart, dtot);
+    uint32_t* heads = reinterpret_cast<uint32_t*>(src == ka ? kz : ka);
+    const int rows = local_heads(src, nk, heads, warp_tot);
+    const int64_t so = slot_off[f];
+    for (int k = tid; k < rows; k += kLocalThreads) {
+      const uint32_t a = heads[k], b = k + 1 < rows ? heads[k + 1] : uint32_t(nk);
+      slot_key[so + k] = src[a];
+      slot_cnt[so + k] = b - a;
+    }
+    if (tid == 0) nrows[f] = rows;
+    __syncthreads();
+  }
+}
+
+// Pack window slots into (key, file, count) rows; rows past the total get
+// the pad key.
+__global__ void local_pack_windows_kernel(int32_t F, const int64_t* __restrict__ slot_off,
+                                          const int64_t* __restrict__ row_off, const uint64_t* __restrict__ slot_key,
+                                          const uint32_t* __restrict__ slot_cnt, uint64_t* __restrict__ key,
+                                          uint64_t* __restrict__ file, uint32_t* __restrict__ cnt) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t f = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5; f < F; f += nwarps) {
+    const int64_t so = slot_off[f], ro = row_off[f], n = row_off[f + 1] - ro;
+    for (int64_t k = lane; k < n; k += 32) {
+      key[ro + k] = slot_key[so + k];
+      file[ro + k] = uint64_t(f);
+      cnt[ro + k] = slot_cnt[so + k];
+    }
+  }
+}
+
+__global__ void pad_rows_kernel(uint64_t* __restrict__ key, uint64_t* __restrict__ file, uint32_t* __restrict__ cnt,
+                                const int64_t* __restrict__ n_dev, int64_t bound, uint64_t key_pad, uint64_t file_pad) {
+  const int64_t n = *n_dev;
+  for (int64_t i = n + blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < bound; i += int64_t(gridDim.x) * blockDim.x) {
+    key[i] = key_pad;
+    file[i] = file_pad;
+    cnt[i] = 0;
   }
 }
 
@@ -575,7 +665,43 @@ gt_result* run_ranked_words_bu(gt_grammar* g, cudaStream_t s) {
                                                                           rkey.as<uint64_t>());
     GT_LAUNCH_CHECK();
   }
-  return ranked_from_rows(ctx, rkey, wr.file, wr.cnt, wr.total.as<int64_t>(), n, 0, false, uint64_t(g->d.V), s);
+  return ranked_from_rows(ctx, rkey, wr.file, wr.cnt, wr.total.as<int64_t>(), n, 0, false, uint64_t(g->d.V),
+                          uint64_t(g->max_file_len), s);
+}
+
+// Per-file window rows of small files, built per file in shared memory.
+void bu_local_window_rows(gt_grammar* g, int kb, uint64_t key_pad, cudaStream_t s, Windows& out) {
+  gt_ctx* ctx = g->ctx;
+  const DevGrammar& d = g->d;
+  const int64_t N = int64_t(d.N);
+  const int cap = int(std::max<int64_t>(256, (g->max_file_len + 255) / 256 * 256));
+  Phase ph(ctx, "bu_local", s);
+  Buf soff(ctx, size_t(d.F + 1) * 8, s), flen(ctx, size_t(d.F + 1) * 8, s), sc(ctx, scan_scratch_bytes(d.F + 1), s);
+  Buf sk(ctx, size_t(N) * 8, s), scn(ctx, size_t(N) * 4, s), nr(ctx, size_t(d.F + 1) * 8, s);
+  Buf roff(ctx, size_t(d.F + 1) * 8, s);
+  out.n = N;
+  out.keys = Buf(ctx, size_t(N) * 8, s);
+  out.fkeys = Buf(ctx, size_t(N) * 8, s);
+  out.vals = Buf(ctx, size_t(N) * 4, s);
+  file_len_i64_kernel<<<grid_for(int64_t(d.F) + 1, 256, ctx->num_sms * 8), 256, 0, s>>>(d.file_len, d.F,
+                                                                                     flen.as<int64_t>());
+  GT_LAUNCH_CHECK();
+  exclusive_scan_i64(flen.as<int64_t>(), soff.as<int64_t>(), d.F + 1, sc.p, s);
+  const size_t smem = size_t(cap) * 16;
+  GT_CUDA(cudaFuncSetAttribute(local_window_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+  GT_CUDA(cudaMemsetAsync(nr.as<int64_t>() + d.F, 0, 8, s));
+  local_window_rows_kernel<<<unsigned(std::min<int64_t>(d.F, 65535)), kLocalThreads, smem, s>>>(
+      d, cap, kb, 3 * kb, soff.as<int64_t>(), sk.as<uint64_t>(), scn.as<uint32_t>(), nr.as<int64_t>());
+  GT_LAUNCH_CHECK();
+  exclusive_scan_i64(nr.as<int64_t>(), roff.as<int64_t>(), d.F + 1, sc.p, s);
+  local_pack_windows_kernel<<<grid_for(int64_t(d.F) * 32, 256, ctx->num_sms * 16), 256, 0, s>>>(
+      d.F, soff.as<int64_t>(), roff.as<int64_t>(), sk.as<uint64_t>(), scn.as<uint32_t>(), out.keys.as<uint64_t>(),
+      out.fkeys.as<uint64_t>(), out.vals.as<uint32_t>());
+  GT_LAUNCH_CHECK();
+  pad_rows_kernel<<<grid_for(N, 256, ctx->num_sms * 16), 256, 0, s>>>(out.keys.as<uint64_t>(), out.fkeys.as<uint64_t>(),
+                                                                       out.vals.as<uint32_t>(), roff.as<int64_t>() + d.F,
+                                                                       N, key_pad, uint64_t(uint32_t(d.F)));
+  GT_LAUNCH_CHECK();
 }
 
 // Per-file window rows: windows owned by the root in each file, plus every
@@ -585,6 +711,10 @@ void bu_window_rows(gt_grammar* g, Buf& head, Buf& tail, int kb, uint64_t key_pa
   const DevGrammar& d = g->d;
   const int threads = 256, cap = ctx->num_sms * 16;
   if (d.depth > kMaxStack) fail(GT_EOVERFLOW, "bottom-up expansion supports DAG depth <= 64");
+  if (g->max_file_len <= kLocalMax && gparam(g, "bu_local", 1)) {
+    bu_local_window_rows(g, kb, key_pad, s, out);
+    return;
+  }
   const int64_t n = 2 * d.root_len + g->bu_windows;
   Phase ph(ctx, "bu_rows", s);
   Buf k0(ctx, size_t(n) * 8, s), f0(ctx, size_t(n) * 8, s), v0(ctx, size_t(n) * 4, s);

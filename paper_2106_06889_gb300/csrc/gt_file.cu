@@ -843,7 +843,8 @@ gt_result* run_ranked_words(gt_grammar* g, cudaStream_t s) {
                                                                       rkey.as<uint64_t>(), rfile.as<int32_t>());
     GT_LAUNCH_CHECK();
   }
-  return ranked_from_rows(ctx, rkey, rfile, tc, fh.total.as<int64_t>(), bound, 0, false, uint64_t(d.V), s);
+  return ranked_from_rows(ctx, rkey, rfile, tc, fh.total.as<int64_t>(), bound, 0, false, uint64_t(d.V),
+                          uint64_t(g->max_file_len), s);
 }
 
 __global__ void copy_rows_kernel(const int32_t* __restrict__ w, const uint64_t* __restrict__ c,

@@ -382,7 +382,7 @@ gt_result* run_ranked_windows(gt_grammar* g, cudaStream_t s);
 // rows (key, file, count) -> ranked index; keys are compact 3-word keys
 // (windows = true, kb bits per word) or word ids (windows = false)
 gt_result* ranked_from_rows(gt_ctx* ctx, Buf& rkey, Buf& rfile, Buf& rcnt, const int64_t* n_dev, int64_t bound,
-                            int kb, bool windows, uint64_t key_pad, cudaStream_t s);
+                            int kb, bool windows, uint64_t key_pad, uint64_t max_count, cudaStream_t s);
 // gt_file.cu: ranked index over words (rows from the term vector)
 gt_result* run_ranked_words(gt_grammar* g, cudaStream_t s);
 

@@ -400,19 +400,22 @@ void sorted_windows(gt_grammar* g, bool per_file, cudaStream_t s, Windows& out) 
   sort_by_file_key(ctx, k0, f0, v0, bound, key_bits, bits_for(d.F), s, out);
 }
 
+// (max_count - count) << 32 | file: ascending = count descending (counts of a
+// key in a file never exceed max_count, the longest file's length).
 __global__ void rank_keys_kernel(const uint64_t* __restrict__ cnt, const int32_t* __restrict__ file,
-                                 const int64_t* __restrict__ n_dev, int64_t bound, uint64_t* __restrict__ k) {
+                                 const int64_t* __restrict__ n_dev, int64_t bound, uint64_t max_count,
+                                 uint64_t* __restrict__ k) {
   const int64_t n = *n_dev;
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < bound; i += int64_t(gridDim.x) * blockDim.x)
-    k[i] = i < n ? (uint64_t(0xffffffffu - uint32_t(cnt[i])) << 32) | uint32_t(file[i]) : 0xffffffff00000000ull;
+    k[i] = i < n ? ((max_count - cnt[i]) << 32) | uint32_t(file[i]) : (max_count << 32);
 }
 
-__global__ void rank_unpack_kernel(const uint64_t* __restrict__ pay, int64_t n, int32_t* __restrict__ file,
-                                   uint64_t* __restrict__ cnt) {
+__global__ void rank_unpack_kernel(const uint64_t* __restrict__ pay, int64_t n, uint64_t max_count,
+                                   int32_t* __restrict__ file, uint64_t* __restrict__ cnt) {
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
     const uint64_t x = pay[i];
     file[i] = int32_t(uint32_t(x));
-    cnt[i] = uint64_t(0xffffffffu - uint32_t(x >> 32));
+    cnt[i] = max_count - (x >> 32);
   }
 }
 
@@ -446,7 +449,7 @@ __global__ void key_offsets_kernel(const uint64_t* __restrict__ key, const int64
 // Rows (key, file, count), n_dev of them (bound allocated) -> ranked index:
 // keys ascending; inside a key, count descending then file ascending.
 gt_result* ranked_from_rows(gt_ctx* ctx, Buf& rkey, Buf& rfile, Buf& rcnt, const int64_t* n_dev, int64_t bound,
-                            int kb, bool windows, uint64_t key_pad, cudaStream_t s) {
+                            int kb, bool windows, uint64_t key_pad, uint64_t max_count, cudaStream_t s) {
   const int threads = 256, cap = ctx->num_sms * 16;
   ResultBuilder rb(ctx, s);
   Phase ph(ctx, "ranked", s);
@@ -464,8 +467,8 @@ gt_result* ranked_from_rows(gt_ctx* ctx, Buf& rkey, Buf& rfile, Buf& rcnt, const
     const int64_t one = 1;
     GT_CUDA(cudaMemcpyAsync(len_off, &one, 8, cudaMemcpyHostToDevice, s));
   } else {
-    // sort 1: stable by count descending, key (~count << 32 | file), payload the
-    // row key; sort 2: stable by row key, payload (~count << 32 | file)
+    // sort 1: stable by count descending, key ((max_count - count) << 32 |
+    // file), payload the row key; sort 2: stable by row key, payload sort 1's key
     Buf k0(ctx, size_t(bound) * 8, s), k1(ctx, size_t(bound) * 8, s), v1(ctx, size_t(bound) * 8, s);
     Buf pay(ctx, size_t(bound) * 8, s), rs(ctx, radix_scratch_bytes(bound, true, 8), s), skey(ctx, size_t(bound) * 8, s);
     Buf flag(ctx, size_t(bound) * 8, s), pos(ctx, size_t(bound) * 8, s), sc(ctx, scan_scratch_bytes(bound), s);
@@ -473,14 +476,18 @@ gt_result* ranked_from_rows(gt_ctx* ctx, Buf& rkey, Buf& rfile, Buf& rcnt, const
     pad_tail_kernel<<<grid_for(bound, threads, cap), threads, 0, s>>>(rkey.as<uint64_t>(), nullptr, nullptr, n_dev,
                                                                        bound, key_pad, 0);
     GT_LAUNCH_CHECK();
+    if (max_count >= (uint64_t(1) << 31)) fail(GT_EOVERFLOW, "ranked index counts need files below 2^31 tokens");
     rank_keys_kernel<<<grid_for(bound, threads, cap), threads, 0, s>>>(rcnt.as<uint64_t>(), rfile.as<int32_t>(), n_dev,
-                                                                        bound, k0.as<uint64_t>());
+                                                                        bound, max_count, k0.as<uint64_t>());
     GT_LAUNCH_CHECK();
-    radix_sort_u64(k0.as<uint64_t>(), k1.as<uint64_t>(), rkey.p, v1.p, 8, bound, 32, 64, rs.p, s);
+    int cbits = 1;
+    while (cbits < 32 && (uint64_t(1) << cbits) <= max_count) ++cbits;
+    radix_sort_u64(k0.as<uint64_t>(), k1.as<uint64_t>(), rkey.p, v1.p, 8, bound, 32, 32 + cbits, rs.p, s);
     int kbits = 1;
     while (kbits < 64 && (uint64_t(1) << kbits) <= key_pad) ++kbits;
     radix_sort_u64(v1.as<uint64_t>(), skey.as<uint64_t>(), k1.p, pay.p, 8, bound, 0, kbits, rs.p, s);
-    rank_unpack_kernel<<<grid_for(bound, threads, cap), threads, 0, s>>>(pay.as<uint64_t>(), bound, ofile, ocnt);
+    rank_unpack_kernel<<<grid_for(bound, threads, cap), threads, 0, s>>>(pay.as<uint64_t>(), bound, max_count, ofile,
+                                                                          ocnt);
     GT_LAUNCH_CHECK();
     key_heads_kernel<<<grid_for(bound, threads, cap), threads, 0, s>>>(skey.as<uint64_t>(), n_dev, bound,
                                                                         flag.as<int64_t>());
@@ -507,7 +514,8 @@ gt_result* run_ranked_windows(gt_grammar* g, cudaStream_t s) {
   Buf rkey(ctx, size_t(w.n) * 8, s), rfile(ctx, size_t(w.n) * 4, s), rcnt(ctx, size_t(w.n) * 8, s), nd(ctx, 8, s);
   reduce_rows(ctx, w.keys.as<uint64_t>(), w.fkeys.as<uint64_t>(), w.vals.as<uint32_t>(), w.n, w.kb, w.key_pad,
               rkey.as<uint64_t>(), rfile.as<int32_t>(), rcnt.as<uint64_t>(), nd.as<int64_t>(), s, false);
-  return ranked_from_rows(ctx, rkey, rfile, rcnt, nd.as<int64_t>(), w.n, w.kb, true, w.key_pad, s);
+  return ranked_from_rows(ctx, rkey, rfile, rcnt, nd.as<int64_t>(), w.n, w.kb, true, w.key_pad,
+                          uint64_t(g->max_file_len), s);
 }
 
 gt_result* run_sequence_count(gt_grammar* g, int per_file, cudaStream_t s) {
