@@ -454,31 +454,20 @@ __global__ void __launch_bounds__(kLocalThreads) local_window_rows_kernel(const 
   }
 }
 
-// Pack window slots into (key, file, count) rows; rows past the total get
-// the pad key.
+// Pack window slots into (key, file, count) rows.
 __global__ void local_pack_windows_kernel(int32_t F, const int64_t* __restrict__ slot_off,
                                           const int64_t* __restrict__ row_off, const uint64_t* __restrict__ slot_key,
                                           const uint32_t* __restrict__ slot_cnt, uint64_t* __restrict__ key,
-                                          uint64_t* __restrict__ file, uint32_t* __restrict__ cnt) {
+                                          int32_t* __restrict__ file, uint64_t* __restrict__ cnt) {
   const int lane = threadIdx.x & 31;
   const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
   for (int64_t f = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5; f < F; f += nwarps) {
     const int64_t so = slot_off[f], ro = row_off[f], n = row_off[f + 1] - ro;
     for (int64_t k = lane; k < n; k += 32) {
       key[ro + k] = slot_key[so + k];
-      file[ro + k] = uint64_t(f);
+      file[ro + k] = int32_t(f);
       cnt[ro + k] = slot_cnt[so + k];
     }
-  }
-}
-
-__global__ void pad_rows_kernel(uint64_t* __restrict__ key, uint64_t* __restrict__ file, uint32_t* __restrict__ cnt,
-                                const int64_t* __restrict__ n_dev, int64_t bound, uint64_t key_pad, uint64_t file_pad) {
-  const int64_t n = *n_dev;
-  for (int64_t i = n + blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < bound; i += int64_t(gridDim.x) * blockDim.x) {
-    key[i] = key_pad;
-    file[i] = file_pad;
-    cnt[i] = 0;
   }
 }
 
@@ -680,9 +669,11 @@ void bu_local_window_rows(gt_grammar* g, int kb, uint64_t key_pad, cudaStream_t 
   Buf sk(ctx, size_t(N) * 8, s), scn(ctx, size_t(N) * 4, s), nr(ctx, size_t(d.F + 1) * 8, s);
   Buf roff(ctx, size_t(d.F + 1) * 8, s);
   out.n = N;
+  out.reduced = true;
   out.keys = Buf(ctx, size_t(N) * 8, s);
-  out.fkeys = Buf(ctx, size_t(N) * 8, s);
-  out.vals = Buf(ctx, size_t(N) * 4, s);
+  out.rfile = Buf(ctx, size_t(N) * 4, s);
+  out.rcnt = Buf(ctx, size_t(N) * 8, s);
+  out.total = Buf(ctx, 8, s);
   file_len_i64_kernel<<<grid_for(int64_t(d.F) + 1, 256, ctx->num_sms * 8), 256, 0, s>>>(d.file_len, d.F,
                                                                                      flen.as<int64_t>());
   GT_LAUNCH_CHECK();
@@ -694,13 +685,10 @@ void bu_local_window_rows(gt_grammar* g, int kb, uint64_t key_pad, cudaStream_t 
       d, cap, kb, 3 * kb, soff.as<int64_t>(), sk.as<uint64_t>(), scn.as<uint32_t>(), nr.as<int64_t>());
   GT_LAUNCH_CHECK();
   exclusive_scan_i64(nr.as<int64_t>(), roff.as<int64_t>(), d.F + 1, sc.p, s);
+  GT_CUDA(cudaMemcpyAsync(out.total.p, roff.as<int64_t>() + d.F, 8, cudaMemcpyDeviceToDevice, s));
   local_pack_windows_kernel<<<grid_for(int64_t(d.F) * 32, 256, ctx->num_sms * 16), 256, 0, s>>>(
       d.F, soff.as<int64_t>(), roff.as<int64_t>(), sk.as<uint64_t>(), scn.as<uint32_t>(), out.keys.as<uint64_t>(),
-      out.fkeys.as<uint64_t>(), out.vals.as<uint32_t>());
-  GT_LAUNCH_CHECK();
-  pad_rows_kernel<<<grid_for(N, 256, ctx->num_sms * 16), 256, 0, s>>>(out.keys.as<uint64_t>(), out.fkeys.as<uint64_t>(),
-                                                                       out.vals.as<uint32_t>(), roff.as<int64_t>() + d.F,
-                                                                       N, key_pad, uint64_t(uint32_t(d.F)));
+      out.rfile.as<int32_t>(), out.rcnt.as<uint64_t>());
   GT_LAUNCH_CHECK();
 }
 

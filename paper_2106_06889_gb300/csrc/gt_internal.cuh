@@ -355,6 +355,10 @@ struct Windows {
   int64_t n = 0;
   int kb = 1;
   uint64_t key_pad = 0;
+  // already one row per distinct (file, key): keys[0, *total) with rfile
+  // (int32) and rcnt (uint64) instead of fkeys / vals
+  bool reduced = false;
+  Buf rfile, rcnt, total;
 };
 
 // per-file strategy: 1 top-down (file masks, <= 64 files), 2 bottom-up

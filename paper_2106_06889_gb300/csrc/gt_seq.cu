@@ -203,6 +203,19 @@ __device__ __forceinline__ uint64_t to_output_key(uint64_t k, int kb) {
   return ((k >> (2 * kb)) << 42) | (((k >> kb) & m) << 21) | (k & m);
 }
 
+// Rows that are already one per (file, key): keys to 21-bit fields, copied.
+__global__ void reduced_rows_out_kernel(const uint64_t* __restrict__ keys, const int32_t* __restrict__ file,
+                                        const uint64_t* __restrict__ cnt, const int64_t* __restrict__ n_dev, int kb,
+                                        uint64_t* __restrict__ okey, int32_t* __restrict__ ofile,
+                                        uint64_t* __restrict__ ocnt) {
+  const int64_t n = *n_dev;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    okey[i] = to_output_key(keys[i], kb);
+    if (ofile) ofile[i] = file[i];
+    ocnt[i] = cnt[i];
+  }
+}
+
 // One output row per run: key (21-bit fields), file, summed count.
 __global__ void run_write_kernel(const uint64_t* __restrict__ keys, const uint64_t* __restrict__ fkeys, int64_t n,
                                  const int64_t* __restrict__ flag, const int64_t* __restrict__ pos,
@@ -510,6 +523,9 @@ gt_result* run_ranked_windows(gt_grammar* g, cudaStream_t s) {
   gt_ctx* ctx = g->ctx;
   Windows w;
   sorted_windows(g, true, s, w);
+  if (w.reduced)
+    return ranked_from_rows(ctx, w.keys, w.rfile, w.rcnt, w.total.as<int64_t>(), w.n, w.kb, true, w.key_pad,
+                            uint64_t(g->max_file_len), s);
   // per-file 3-gram rows (file, key, count) in (file, key) order
   Buf rkey(ctx, size_t(w.n) * 8, s), rfile(ctx, size_t(w.n) * 4, s), rcnt(ctx, size_t(w.n) * 8, s), nd(ctx, 8, s);
   reduce_rows(ctx, w.keys.as<uint64_t>(), w.fkeys.as<uint64_t>(), w.vals.as<uint32_t>(), w.n, w.kb, w.key_pad,
@@ -528,8 +544,18 @@ gt_result* run_sequence_count(gt_grammar* g, int per_file, cudaStream_t s) {
   auto* count = static_cast<uint64_t*>(rb.alloc(size_t(w.n) * 8));
   int32_t* file = per_file ? static_cast<int32_t*>(rb.alloc(size_t(w.n) * 4)) : nullptr;
   int64_t* len = rb.new_len_slot();
-  reduce_rows(ctx, w.keys.as<uint64_t>(), per_file ? w.fkeys.as<uint64_t>() : nullptr, w.vals.as<uint32_t>(), w.n,
-              w.kb, w.key_pad, key, file, count, len, s);
+  if (w.reduced) {
+    GT_CUDA(cudaMemcpyAsync(len, w.total.p, 8, cudaMemcpyDeviceToDevice, s));
+    if (w.n > 0) {
+      reduced_rows_out_kernel<<<grid_for(w.n, 256, ctx->num_sms * 16), 256, 0, s>>>(
+          w.keys.as<uint64_t>(), w.rfile.as<int32_t>(), w.rcnt.as<uint64_t>(), w.total.as<int64_t>(), w.kb, key, file,
+          count);
+      GT_LAUNCH_CHECK();
+    }
+  } else {
+    reduce_rows(ctx, w.keys.as<uint64_t>(), per_file ? w.fkeys.as<uint64_t>() : nullptr, w.vals.as<uint32_t>(), w.n,
+                w.kb, w.key_pad, key, file, count, len, s);
+  }
   if (per_file) rb.field_dyn("file", file, len);
   rb.field_dyn("key", key, len);
   rb.field_dyn("count", count, len);
