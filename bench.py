@@ -127,14 +127,17 @@ def run_step(B, gh, bufs, analytics, stream, keep):
     keep.extend(r for r in B.gt_run_batch(gh.ctx, qs, stream) if r is not None)
 
 
-def serving_bench(B, ctx, n_corpora=8, n_queries=1000, seed=7):
+SERVING_TOKENS = (1_000_000, 32_000_000)
+
+
+def serving_bench(B, ctx, n_corpora=32, n_queries=1000, seed=7):
     """Continuous-batching server vs the plain one-query-at-a-time path on a set
     of resident corpora; mix 40% word count / 30% inverted index / 30% 3-gram
     count, corpus chosen uniformly; Poisson arrivals at 50/80/95% of the
     measured saturated capacity."""
     import torch
-    from paper_2106_06889_gb300.corpus import load_serving
-    gs = [load_serving(i) for i in range(n_corpora)]
+    from paper_2106_06889_gb300.corpus import load_serving_set
+    gs = load_serving_set(n_corpora, SERVING_TOKENS)
     hs = [B.gt_load_grammar(ctx, g) for g in gs]
     ntok = [int(g.meta["N"]) for g in gs]
     rng = np.random.default_rng(seed)
@@ -194,8 +197,8 @@ def serving_bench(B, ctx, n_corpora=8, n_queries=1000, seed=7):
                       "p50_ms": float(np.percentile(lats, 50)), "p99_ms": float(np.percentile(lats, 99))})
     stats = B.gt_server_stats(sv)
     B.gt_server_destroy(sv)
-    # word counts of every resident corpus: one fused launch sequence against
-    # one call per corpus (both device-timed on one stream)
+    # word counts of every resident corpus: fused launch sequences (64 grammars
+    # each at most) against one call per corpus (both device-timed on one stream)
     fused = {}
     with torch.cuda.stream(st):
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

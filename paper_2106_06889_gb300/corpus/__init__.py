@@ -24,7 +24,8 @@ import numpy as np
 from .._build import build_corpus, CORPUS_SO, ROOT
 
 __all__ = ["Grammar", "sequitur", "zipf_tokens", "Corpus", "make_corpus", "CONFIGS", "load_config",
-           "root_only_grammar", "refactor_grammar", "prefix_files", "serving_corpus", "load_serving"]
+           "root_only_grammar", "refactor_grammar", "prefix_files", "serving_corpus", "load_serving",
+           "load_serving_set"]
 
 
 @dataclass
@@ -363,6 +364,15 @@ def load_serving(i: int, **kw) -> Grammar:
     g.save(tmp)
     os.replace(tmp, path)
     return g
+
+
+def load_serving_set(n: int, tokens_range=(1_000_000, 32_000_000), workers: int | None = None) -> list:
+    """Grammars of serving corpora 0..n-1, built in parallel threads (the
+    generator's numpy work and the Sequitur builder release the GIL)."""
+    from concurrent.futures import ThreadPoolExecutor
+    workers = workers or min(16, os.cpu_count() or 1)
+    with ThreadPoolExecutor(max_workers=workers) as ex:
+        return list(ex.map(lambda i: load_serving(i, tokens_range=tokens_range), range(n)))
 
 
 def cache_dir() -> Path:
