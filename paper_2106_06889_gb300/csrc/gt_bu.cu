@@ -291,14 +291,7 @@ __device__ K* local_sort(K* a, K* b, int n, int key_bits, uint32_t (*wcnt)[256],
     const uint32_t mask = key_bits - shift >= 8 ? 0xffu : ((1u << (key_bits - shift)) - 1u);
     for (int q = lane; q < 256; q += 32) wcnt[warp][q] = 0;
     __syncwarp();
-    for (int i0 = lo; i0 < hi; i0 += 32) {
-      const int i = i0 + lane;
-      const bool valid = i < hi;
-      const uint32_t dg = valid ? uint32_t(src[i] >> shift) & mask : 0u;
-      const unsigned peers = local_peers(dg, __ballot_sync(0xffffffffu, valid));
-      if (valid && (peers & lt) == 0) wcnt[warp][dg] += __popc(peers);
-      __syncwarp();
-    }
+    for (int i = lo + lane; i < hi; i += 32) atomicAdd(&wcnt[warp][uint32_t(src[i] >> shift) & mask], 1u);
     __syncthreads();
     {  // thread = digit: exclusive over warps, then over digits
       const int dg = tid;

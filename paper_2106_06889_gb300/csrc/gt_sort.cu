@@ -107,38 +107,64 @@ __device__ __forceinline__ unsigned warp_digit_peers(uint32_t d, unsigned active
   return peers;
 }
 
-// Per-tile digit counts, stored digit-major (hist[d * ntiles + tile]) so that
-// one exclusive scan gives every (digit, tile) its output offset.
+// Per-tile digit counts, stored tile-major (hist[tile * 256 + d]) so that
+// each CTA writes one contiguous row.
 __global__ void __launch_bounds__(kRsThreads) radix_upsweep_kernel(const uint64_t* __restrict__ keys, int64_t n,
-                                                                   int shift, uint32_t mask, int64_t ntiles,
-                                                                   int64_t* __restrict__ hist) {
+                                                                   int shift, uint32_t mask,
+                                                                   uint32_t* __restrict__ hist) {
   __shared__ uint32_t h[kRsWarps][256];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int i = threadIdx.x; i < kRsWarps * 256; i += kRsThreads) h[i / 256][i % 256] = 0;
   __syncthreads();
   const int64_t wbase = int64_t(blockIdx.x) * kRsTile + int64_t(warp) * 32 * kRsItems;
-  uint64_t key[kRsItems];  // every load issued before the first ballot
+  uint64_t key[kRsItems];  // every load issued before the first update
 #pragma unroll
   for (int it = 0; it < kRsItems; ++it) {
     const int64_t idx = wbase + it * 32 + lane;
     key[it] = idx < n ? keys[idx] : 0;
   }
+  // counting only: one shared atomic per key into the warp's own counters
+  // (measured faster than ballot multisplit, also when all keys share a digit)
 #pragma unroll
   for (int it = 0; it < kRsItems; ++it) {
     const int64_t idx = wbase + it * 32 + lane;
-    const bool valid = idx < n;
-    const uint32_t d = valid ? uint32_t(key[it] >> shift) & mask : 0u;
-    const unsigned peers = warp_digit_peers(d, __ballot_sync(0xffffffffu, valid));
-    // the lowest lane of each digit group adds the group; the counters are warp-private
-    if (valid && (peers & ((1u << lane) - 1u)) == 0) h[warp][d] += __popc(peers);
-    __syncwarp();
+    if (idx < n) atomicAdd(&h[warp][uint32_t(key[it] >> shift) & mask], 1u);
   }
   __syncthreads();
   const int d = threadIdx.x;
   uint32_t t = 0;
 #pragma unroll
   for (int w = 0; w < kRsWarps; ++w) t += h[w][d];
-  hist[int64_t(d) * ntiles + blockIdx.x] = t;
+  hist[int64_t(blockIdx.x) * 256 + d] = t;
+}
+
+// Output offsets of every (tile, digit): offs[tile * 256 + d] = (keys of
+// smaller digits) + (keys of digit d in earlier tiles).  Tiles are grouped in
+// chunks of kRsChunk: per-chunk digit sums (digit-major, so one scan orders
+// them by digit, then chunk), then a running sum inside each chunk.
+constexpr int kRsChunk = 64;
+
+__global__ void __launch_bounds__(256) radix_chunk_sum_kernel(const uint32_t* __restrict__ hist, int64_t ntiles,
+                                                               int64_t nchunks, int64_t* __restrict__ csum) {
+  const int64_t c = blockIdx.x;
+  const int d = threadIdx.x;
+  const int64_t t1 = min(ntiles, (c + 1) * kRsChunk);
+  int64_t sum = 0;
+  for (int64_t t = c * kRsChunk; t < t1; ++t) sum += hist[t * 256 + d];
+  csum[int64_t(d) * nchunks + c] = sum;
+}
+
+__global__ void __launch_bounds__(256) radix_chunk_offsets_kernel(const uint32_t* __restrict__ hist,
+                                                                   const int64_t* __restrict__ cpre, int64_t ntiles,
+                                                                   int64_t nchunks, int64_t* __restrict__ offs) {
+  const int64_t c = blockIdx.x;
+  const int d = threadIdx.x;
+  const int64_t t1 = min(ntiles, (c + 1) * kRsChunk);
+  int64_t run = cpre[int64_t(d) * nchunks + c];
+  for (int64_t t = c * kRsChunk; t < t1; ++t) {
+    offs[t * 256 + d] = run;
+    run += hist[t * 256 + d];
+  }
 }
 
 // Stable scatter of one tile.  Warp w owns the w-th slice of the tile and
@@ -151,7 +177,7 @@ constexpr int kRsMinBlocks = 4;
 template <int VB>
 __global__ void __launch_bounds__(kRsThreads, kRsMinBlocks) radix_downsweep_kernel(
     const uint64_t* __restrict__ kin, uint64_t* __restrict__ kout, const void* __restrict__ vin,
-    void* __restrict__ vout, int64_t n, int shift, uint32_t mask, int64_t ntiles, const int64_t* __restrict__ offs) {
+    void* __restrict__ vout, int64_t n, int shift, uint32_t mask, const int64_t* __restrict__ offs) {
   __shared__ uint32_t wcnt[kRsWarps][256];
   __shared__ uint32_t dstart[256];
   __shared__ uint32_t wsum[kRsWarps];
@@ -161,7 +187,7 @@ __global__ void __launch_bounds__(kRsThreads, kRsMinBlocks) radix_downsweep_kern
   unsigned char* sval = rs_smem + kRsTile * 8;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int i = threadIdx.x; i < kRsWarps * 256; i += kRsThreads) wcnt[i / 256][i % 256] = 0;
-  goff[threadIdx.x] = offs[int64_t(threadIdx.x) * ntiles + blockIdx.x];
+  goff[threadIdx.x] = offs[int64_t(blockIdx.x) * 256 + threadIdx.x];
   __syncthreads();
   const unsigned lt_mask = (1u << lane) - 1u;
   const int64_t tbase = int64_t(blockIdx.x) * kRsTile;
@@ -235,7 +261,7 @@ void launch_downsweep(const uint64_t* ka, uint64_t* kb, const void* va, void* vb
                       int64_t ntiles, const int64_t* offs, cudaStream_t s) {
   constexpr size_t smem = size_t(kRsTile) * (8 + VB);
   GT_CUDA(cudaFuncSetAttribute(radix_downsweep_kernel<VB>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
-  radix_downsweep_kernel<VB><<<unsigned(ntiles), kRsThreads, smem, s>>>(ka, kb, va, vb, n, shift, mask, ntiles, offs);
+  radix_downsweep_kernel<VB><<<unsigned(ntiles), kRsThreads, smem, s>>>(ka, kb, va, vb, n, shift, mask, offs);
   GT_LAUNCH_CHECK();
 }
 
@@ -265,30 +291,37 @@ void exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, void* scratc
 }
 
 size_t radix_scratch_bytes(int64_t n, bool, int) {
-  int64_t ntiles = (n + kRsTile - 1) / kRsTile;
-  int64_t m = 256 * ntiles;
-  return size_t(2 * m) * sizeof(int64_t) + scan_scratch_bytes(m) + 256;
+  const int64_t ntiles = (n + kRsTile - 1) / kRsTile;
+  const int64_t nchunks = (ntiles + kRsChunk - 1) / kRsChunk;
+  const int64_t m = 256 * ntiles, mc = 256 * nchunks;
+  return size_t(m) * 4 + size_t(m) * 8 + size_t(2 * mc) * 8 + scan_scratch_bytes(mc) + 256;
 }
 
 void radix_sort_u64(uint64_t* keys_in, uint64_t* keys_out, void* vals_in, void* vals_out, int value_bytes,
                     int64_t n, int begin_bit, int end_bit, void* scratch, cudaStream_t s) {
   if (n <= 0) return;
   const int64_t ntiles = (n + kRsTile - 1) / kRsTile;
-  const int64_t m = 256 * ntiles;
-  int64_t* hist = static_cast<int64_t*>(scratch);
-  int64_t* offs = hist + m;
-  void* sscratch = offs + m;
+  const int64_t nchunks = (ntiles + kRsChunk - 1) / kRsChunk;
+  const int64_t m = 256 * ntiles, mc = 256 * nchunks;
+  uint32_t* hist = static_cast<uint32_t*>(scratch);
+  int64_t* offs = reinterpret_cast<int64_t*>(static_cast<char*>(scratch) + ((size_t(m) * 4 + 15) / 16 * 16));
+  int64_t* csum = offs + m;
+  int64_t* cpre = csum + mc;
+  void* sscratch = cpre + mc;
   uint64_t* ka = keys_in;
   uint64_t* kb = keys_out;
   void* va = vals_in;
   void* vb = vals_out;
-  int passes = 0;
-  for (int shift = begin_bit; shift < end_bit; shift += 8, ++passes) {
+  for (int shift = begin_bit; shift < end_bit; shift += 8) {
     const int bits = end_bit - shift < 8 ? end_bit - shift : 8;
     const uint32_t mask = (1u << bits) - 1u;
-    radix_upsweep_kernel<<<unsigned(ntiles), kRsThreads, 0, s>>>(ka, n, shift, mask, ntiles, hist);
+    radix_upsweep_kernel<<<unsigned(ntiles), kRsThreads, 0, s>>>(ka, n, shift, mask, hist);
     GT_LAUNCH_CHECK();
-    exclusive_scan_i64(hist, offs, m, sscratch, s);
+    radix_chunk_sum_kernel<<<unsigned(nchunks), 256, 0, s>>>(hist, ntiles, nchunks, csum);
+    GT_LAUNCH_CHECK();
+    exclusive_scan_i64(csum, cpre, mc, sscratch, s);
+    radix_chunk_offsets_kernel<<<unsigned(nchunks), 256, 0, s>>>(hist, cpre, ntiles, nchunks, offs);
+    GT_LAUNCH_CHECK();
     if (value_bytes == 4)
       launch_downsweep<4>(ka, kb, va, vb, n, shift, mask, ntiles, offs, s);
     else if (value_bytes == 8)
