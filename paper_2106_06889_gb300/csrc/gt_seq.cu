@@ -183,19 +183,6 @@ __global__ void pad_tail_kernel(uint64_t* __restrict__ keys, uint64_t* __restric
   }
 }
 
-// Run heads of the sorted (file, key) sequence; entries whose key is the pad
-// (kNoKey-derived) are not heads.
-__global__ void run_heads_kernel(const uint64_t* __restrict__ keys, const uint64_t* __restrict__ fkeys, int64_t n,
-                                 uint64_t key_pad, int64_t* __restrict__ flag, int64_t* __restrict__ v64,
-                                 const uint32_t* __restrict__ vals) {
-  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
-    const bool real = keys[i] != key_pad;
-    const bool head = real && (i == 0 || keys[i] != keys[i - 1] || (fkeys && fkeys[i] != fkeys[i - 1]));
-    flag[i] = head;
-    v64[i] = real ? int64_t(vals[i]) : 0;
-  }
-}
-
 // compact key (kb bits per word) -> w1 << 42 | w2 << 21 | w3; kb == 0 keeps it
 __device__ __forceinline__ uint64_t to_output_key(uint64_t k, int kb) {
   if (kb == 0) return k;
@@ -213,35 +200,6 @@ __global__ void reduced_rows_out_kernel(const uint64_t* __restrict__ keys, const
     okey[i] = to_output_key(keys[i], kb);
     if (ofile) ofile[i] = file[i];
     ocnt[i] = cnt[i];
-  }
-}
-
-// One output row per run: key (21-bit fields), file, summed count.
-__global__ void run_write_kernel(const uint64_t* __restrict__ keys, const uint64_t* __restrict__ fkeys, int64_t n,
-                                 const int64_t* __restrict__ flag, const int64_t* __restrict__ pos,
-                                 const int64_t* __restrict__ wsum, const int64_t* __restrict__ v64, int kb,
-                                 int64_t* __restrict__ run_start, uint64_t* __restrict__ out_key,
-                                 int32_t* __restrict__ out_file) {
-  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
-    if (flag[i]) {
-      const int64_t u = pos[i];
-      out_key[u] = to_output_key(keys[i], kb);
-      if (out_file) out_file[u] = int32_t(fkeys[i]);
-      run_start[u] = i;
-    }
-}
-
-__global__ void run_sum_kernel(const int64_t* __restrict__ run_start, const int64_t* __restrict__ nruns_d,
-                               const int64_t* __restrict__ wsum, const int64_t* __restrict__ v64, int64_t n,
-                               uint64_t* __restrict__ out_count) {
-  const int64_t nr = *nruns_d;
-  for (int64_t u = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; u < nr; u += int64_t(gridDim.x) * blockDim.x) {
-    const int64_t a = run_start[u];
-    int64_t b;
-    if (u + 1 < nr) b = run_start[u + 1];
-    else b = n;  // past the last run only pads follow, and they add 0
-    const int64_t end_sum = b < n ? wsum[b] : wsum[n - 1] + v64[n - 1];
-    out_count[u] = uint64_t(end_sum - wsum[a]);
   }
 }
 
@@ -273,31 +231,102 @@ int bits_for(int64_t x) {
   return b;
 }
 
-// Sorted rows -> result (key, [file], count); nrows_slot receives the row count.
+// Segmented sum over sorted rows: one output row per run of equal (file, key),
+// pad-key rows skipped.  Pass 1 counts run heads per tile; after a scan over
+// tiles, pass 2 gives each head its output index (a scan inside the tile) and
+// the head's thread adds up its run, reading forward (runs are short).
+constexpr int kRedThreads = 256;
+constexpr int kRedItems = 8;
+constexpr int kRedTile = kRedThreads * kRedItems;
+
+__device__ __forceinline__ bool red_head(const uint64_t* __restrict__ keys, const uint64_t* __restrict__ fkeys,
+                                         int64_t i, uint64_t key_pad) {
+  const uint64_t k = keys[i];
+  if (k == key_pad) return false;
+  if (i == 0) return true;
+  return k != keys[i - 1] || (fkeys && fkeys[i] != fkeys[i - 1]);
+}
+
+__device__ __forceinline__ int red_block_scan(int v, int* total) {
+  __shared__ int warp_tot[kRedThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) warp_tot[warp] = incl;
+  __syncthreads();
+  int before = 0, all = 0;
+#pragma unroll
+  for (int w = 0; w < kRedThreads / 32; ++w) {
+    const int t = warp_tot[w];
+    before += w < warp ? t : 0;
+    all += t;
+  }
+  __syncthreads();
+  *total = all;
+  return before + incl - v;
+}
+
+__global__ void __launch_bounds__(kRedThreads) red_count_kernel(const uint64_t* __restrict__ keys,
+                                                                const uint64_t* __restrict__ fkeys, int64_t n,
+                                                                uint64_t key_pad, int64_t* __restrict__ tcnt) {
+  const int64_t base = int64_t(blockIdx.x) * kRedTile;
+  int c = 0;
+#pragma unroll
+  for (int k = 0; k < kRedItems; ++k) {  // consecutive threads, consecutive rows
+    const int64_t i = base + k * kRedThreads + threadIdx.x;
+    if (i < n) c += red_head(keys, fkeys, i, key_pad);
+  }
+  int total;
+  red_block_scan(c, &total);
+  if (threadIdx.x == 0) tcnt[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(kRedThreads) red_write_kernel(const uint64_t* __restrict__ keys,
+                                                                const uint64_t* __restrict__ fkeys,
+                                                                const uint32_t* __restrict__ vals, int64_t n,
+                                                                uint64_t key_pad, const int64_t* __restrict__ toff,
+                                                                int kb, uint64_t* __restrict__ out_key,
+                                                                int32_t* __restrict__ out_file,
+                                                                uint64_t* __restrict__ out_count) {
+  const int64_t base = int64_t(blockIdx.x) * kRedTile;
+  int64_t o0 = toff[blockIdx.x];
+  for (int k = 0; k < kRedItems; ++k) {  // one 256-row step at a time, in row order
+    const int64_t i = base + k * kRedThreads + threadIdx.x;
+    const bool h = i < n && red_head(keys, fkeys, i, key_pad);
+    int step;
+    const int64_t o = o0 + red_block_scan(h ? 1 : 0, &step);
+    o0 += step;
+    if (!h) continue;
+    const uint64_t key = keys[i];
+    const uint64_t f = fkeys ? fkeys[i] : 0;
+    uint64_t sum = vals[i];
+    for (int64_t j = i + 1; j < n && keys[j] == key && (!fkeys || fkeys[j] == f); ++j) sum += vals[j];
+    out_key[o] = to_output_key(key, kb);
+    if (out_file) out_file[o] = int32_t(f);
+    out_count[o] = sum;
+  }
+}
+
 void reduce_rows(gt_ctx* ctx, uint64_t* keys, uint64_t* fkeys, uint32_t* vals, int64_t n, int kb, uint64_t key_pad,
                  uint64_t* out_key, int32_t* out_file, uint64_t* out_count, int64_t* nrows_slot, cudaStream_t s,
                  bool output_keys = true) {
-  const int threads = 256, cap = ctx->num_sms * 16;
-  Buf flag(ctx, size_t(n) * 8, s), pos(ctx, size_t(n) * 8, s), v64(ctx, size_t(n) * 8, s), wsum(ctx, size_t(n) * 8, s);
-  Buf sc(ctx, scan_scratch_bytes(n), s), rstart(ctx, size_t(n) * 8, s), nr(ctx, 8, s);
   if (n == 0) {
     GT_CUDA(cudaMemsetAsync(nrows_slot, 0, 8, s));
     return;
   }
-  run_heads_kernel<<<grid_for(n, threads, cap), threads, 0, s>>>(keys, fkeys, n, key_pad, flag.as<int64_t>(),
-                                                                  v64.as<int64_t>(), vals);
+  const int64_t tiles = (n + kRedTile - 1) / kRedTile;
+  Buf tcnt(ctx, size_t(tiles + 1) * 8, s), toff(ctx, size_t(tiles + 1) * 8, s), sc(ctx, scan_scratch_bytes(tiles + 1), s);
+  GT_CUDA(cudaMemsetAsync(tcnt.as<int64_t>() + tiles, 0, 8, s));
+  red_count_kernel<<<unsigned(tiles), kRedThreads, 0, s>>>(keys, fkeys, n, key_pad, tcnt.as<int64_t>());
   GT_LAUNCH_CHECK();
-  exclusive_scan_i64(flag.as<int64_t>(), pos.as<int64_t>(), n, sc.p, s);
-  exclusive_scan_i64(v64.as<int64_t>(), wsum.as<int64_t>(), n, sc.p, s);
-  last_total2_kernel<<<1, 1, 0, s>>>(pos.as<int64_t>(), flag.as<int64_t>(), n, nr.as<int64_t>(), nrows_slot);
-  GT_LAUNCH_CHECK();
-  run_write_kernel<<<grid_for(n, threads, cap), threads, 0, s>>>(keys, fkeys, n, flag.as<int64_t>(), pos.as<int64_t>(),
-                                                                  wsum.as<int64_t>(), v64.as<int64_t>(),
-                                                                  output_keys ? kb : 0, rstart.as<int64_t>(), out_key,
-                                                                  out_file);
-  GT_LAUNCH_CHECK();
-  run_sum_kernel<<<grid_for(n, threads, cap), threads, 0, s>>>(rstart.as<int64_t>(), nr.as<int64_t>(),
-                                                                wsum.as<int64_t>(), v64.as<int64_t>(), n, out_count);
+  exclusive_scan_i64(tcnt.as<int64_t>(), toff.as<int64_t>(), tiles + 1, sc.p, s);
+  GT_CUDA(cudaMemcpyAsync(nrows_slot, toff.as<int64_t>() + tiles, 8, cudaMemcpyDeviceToDevice, s));
+  red_write_kernel<<<unsigned(tiles), kRedThreads, 0, s>>>(keys, fkeys, vals, n, key_pad, toff.as<int64_t>(),
+                                                            output_keys ? kb : 0, out_key, out_file, out_count);
   GT_LAUNCH_CHECK();
 }
 
