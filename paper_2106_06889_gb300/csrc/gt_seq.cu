@@ -232,19 +232,20 @@ int bits_for(int64_t x) {
 }
 
 // Segmented sum over sorted rows: one output row per run of equal (file, key),
-// pad-key rows skipped.  Pass 1 counts run heads per tile; after a scan over
-// tiles, pass 2 gives each head its output index (a scan inside the tile) and
-// the head's thread adds up its run, reading forward (runs are short).
+// pad-key rows skipped.  Pass 1, per tile of 2048 rows: the number of run
+// heads, the sum of the rows before the first head (the tail of a run that
+// started in an earlier tile) and whether the whole tile continues such a run.
+// After a scan of the head counts, pass 2 stages the tile in shared memory,
+// gives each head its output index and sums its run up to the tile end, then
+// adds the leading sums of the following tiles while the run continues - so a
+// hot key's long run costs one pass over its tiles, not one thread per row.
 constexpr int kRedThreads = 256;
 constexpr int kRedItems = 8;
 constexpr int kRedTile = kRedThreads * kRedItems;
 
-__device__ __forceinline__ bool red_head(const uint64_t* __restrict__ keys, const uint64_t* __restrict__ fkeys,
-                                         int64_t i, uint64_t key_pad) {
-  const uint64_t k = keys[i];
-  if (k == key_pad) return false;
-  if (i == 0) return true;
-  return k != keys[i - 1] || (fkeys && fkeys[i] != fkeys[i - 1]);
+__device__ __forceinline__ bool red_same(const uint64_t* __restrict__ keys, const uint64_t* __restrict__ fkeys,
+                                         int64_t i, int64_t j) {
+  return keys[i] == keys[j] && (!fkeys || fkeys[i] == fkeys[j]);
 }
 
 __device__ __forceinline__ int red_block_scan(int v, int* total) {
@@ -271,40 +272,94 @@ __device__ __forceinline__ int red_block_scan(int v, int* total) {
 }
 
 __global__ void __launch_bounds__(kRedThreads) red_count_kernel(const uint64_t* __restrict__ keys,
-                                                                const uint64_t* __restrict__ fkeys, int64_t n,
-                                                                uint64_t key_pad, int64_t* __restrict__ tcnt) {
+                                                                const uint64_t* __restrict__ fkeys,
+                                                                const uint32_t* __restrict__ vals, int64_t n,
+                                                                uint64_t key_pad, int64_t* __restrict__ tcnt,
+                                                                unsigned long long* __restrict__ lead,
+                                                                int* __restrict__ passes) {
+  __shared__ int first_head, any_pad;
+  __shared__ unsigned long long lsum;
   const int64_t base = int64_t(blockIdx.x) * kRedTile;
+  const int64_t end = min(n, base + kRedTile);
+  if (threadIdx.x == 0) {
+    first_head = kRedTile;
+    any_pad = 0;
+    lsum = 0;
+  }
+  __syncthreads();
   int c = 0;
 #pragma unroll
   for (int k = 0; k < kRedItems; ++k) {  // consecutive threads, consecutive rows
     const int64_t i = base + k * kRedThreads + threadIdx.x;
-    if (i < n) c += red_head(keys, fkeys, i, key_pad);
+    if (i >= end) continue;
+    const bool pad = keys[i] == key_pad;
+    const bool head = !pad && (i == 0 || !red_same(keys, fkeys, i, i - 1));
+    c += head;
+    if (head) atomicMin(&first_head, int(i - base));
+    if (pad) any_pad = 1;
   }
   int total;
-  red_block_scan(c, &total);
-  if (threadIdx.x == 0) tcnt[blockIdx.x] = total;
+  red_block_scan(c, &total);  // also orders the shared updates above
+  unsigned long long part = 0;
+#pragma unroll
+  for (int k = 0; k < kRedItems; ++k) {
+    const int64_t i = base + k * kRedThreads + threadIdx.x;
+    if (i < end && i - base < first_head && keys[i] != key_pad) part += vals[i];
+  }
+  if (part) atomicAdd(&lsum, part);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    tcnt[blockIdx.x] = total;
+    lead[blockIdx.x] = lsum;
+    passes[blockIdx.x] = (total == 0 && !any_pad && end - base == kRedTile) ? 1 : 0;
+  }
 }
 
 __global__ void __launch_bounds__(kRedThreads) red_write_kernel(const uint64_t* __restrict__ keys,
                                                                 const uint64_t* __restrict__ fkeys,
                                                                 const uint32_t* __restrict__ vals, int64_t n,
                                                                 uint64_t key_pad, const int64_t* __restrict__ toff,
-                                                                int kb, uint64_t* __restrict__ out_key,
+                                                                const unsigned long long* __restrict__ lead,
+                                                                const int* __restrict__ passes, int64_t tiles, int kb,
+                                                                uint64_t* __restrict__ out_key,
                                                                 int32_t* __restrict__ out_file,
                                                                 uint64_t* __restrict__ out_count) {
+  __shared__ uint64_t sk[kRedTile];
+  __shared__ uint32_t sv[kRedTile];
+  __shared__ uint32_t sf[kRedTile];  // files fit 32 bits
   const int64_t base = int64_t(blockIdx.x) * kRedTile;
+  const int len = int(min(n - base, int64_t(kRedTile)));
+  for (int r = threadIdx.x; r < len; r += kRedThreads) {
+    sk[r] = keys[base + r];
+    sv[r] = vals[base + r];
+    if (fkeys) sf[r] = uint32_t(fkeys[base + r]);
+  }
+  __syncthreads();
   int64_t o0 = toff[blockIdx.x];
   for (int k = 0; k < kRedItems; ++k) {  // one 256-row step at a time, in row order
-    const int64_t i = base + k * kRedThreads + threadIdx.x;
-    const bool h = i < n && red_head(keys, fkeys, i, key_pad);
+    const int r = k * kRedThreads + threadIdx.x;
+    const int64_t i = base + r;
+    bool h = false;
+    if (r < len && sk[r] != key_pad) {
+      if (r > 0)
+        h = sk[r] != sk[r - 1] || (fkeys && sf[r] != sf[r - 1]);
+      else
+        h = i == 0 || !red_same(keys, fkeys, i, i - 1);
+    }
     int step;
     const int64_t o = o0 + red_block_scan(h ? 1 : 0, &step);
     o0 += step;
     if (!h) continue;
-    const uint64_t key = keys[i];
-    const uint64_t f = fkeys ? fkeys[i] : 0;
-    uint64_t sum = vals[i];
-    for (int64_t j = i + 1; j < n && keys[j] == key && (!fkeys || fkeys[j] == f); ++j) sum += vals[j];
+    const uint64_t key = sk[r];
+    const uint32_t f = fkeys ? sf[r] : 0u;
+    unsigned long long sum = sv[r];
+    int q = r + 1;
+    while (q < len && sk[q] == key && (!fkeys || sf[q] == f)) sum += sv[q++];
+    if (q == len)  // the run reaches the tile end: add the leading sums of the next tiles
+      for (int64_t t = int64_t(blockIdx.x) + 1; t < tiles; ++t) {
+        sum += lead[t];
+        if (!passes[t]) break;
+      }
     out_key[o] = to_output_key(key, kb);
     if (out_file) out_file[o] = int32_t(f);
     out_count[o] = sum;
@@ -320,12 +375,15 @@ void reduce_rows(gt_ctx* ctx, uint64_t* keys, uint64_t* fkeys, uint32_t* vals, i
   }
   const int64_t tiles = (n + kRedTile - 1) / kRedTile;
   Buf tcnt(ctx, size_t(tiles + 1) * 8, s), toff(ctx, size_t(tiles + 1) * 8, s), sc(ctx, scan_scratch_bytes(tiles + 1), s);
+  Buf lead(ctx, size_t(tiles) * 8, s), pass(ctx, size_t(tiles) * 4, s);
   GT_CUDA(cudaMemsetAsync(tcnt.as<int64_t>() + tiles, 0, 8, s));
-  red_count_kernel<<<unsigned(tiles), kRedThreads, 0, s>>>(keys, fkeys, n, key_pad, tcnt.as<int64_t>());
+  red_count_kernel<<<unsigned(tiles), kRedThreads, 0, s>>>(keys, fkeys, vals, n, key_pad, tcnt.as<int64_t>(),
+                                                            lead.as<unsigned long long>(), pass.as<int>());
   GT_LAUNCH_CHECK();
   exclusive_scan_i64(tcnt.as<int64_t>(), toff.as<int64_t>(), tiles + 1, sc.p, s);
   GT_CUDA(cudaMemcpyAsync(nrows_slot, toff.as<int64_t>() + tiles, 8, cudaMemcpyDeviceToDevice, s));
   red_write_kernel<<<unsigned(tiles), kRedThreads, 0, s>>>(keys, fkeys, vals, n, key_pad, toff.as<int64_t>(),
+                                                            lead.as<unsigned long long>(), pass.as<int>(), tiles,
                                                             output_keys ? kb : 0, out_key, out_file, out_count);
   GT_LAUNCH_CHECK();
 }

@@ -98,3 +98,23 @@ def test_full_size_multifile_sequence_count(ctx):
     assert np.array_equal(B.result_numpy(r, "count"), c)
     B.gt_free_result(r)
     B.gt_free_grammar(gh)
+
+
+@pytest.mark.parametrize("per_file", [0, 1])
+def test_long_runs_across_tiles(ctx, per_file):
+    """Runs of one key spanning many 2048-row tiles: a root-only text that
+    repeats one word (every window the same key) in three files, plus a
+    stretch of other words, so runs end inside, at and past tile edges."""
+    rng = np.random.default_rng(77)
+    toks = np.concatenate([np.full(20000, 3, np.int32), rng.integers(0, 9, 5000).astype(np.int32),
+                           np.full(4096 + 2, 5, np.int32), np.full(9000, 3, np.int32)])
+    lens = np.array([20000, 9098, 9000], np.int64)
+    g = root_only_grammar(toks, lens, 10)
+    gh = B.gt_load_grammar(ctx, g)
+    r = B.gt_sequence_count(gh, per_file)
+    want = oracle.sequence_count(g, per_file)
+    got = [B.result_numpy(r, k) for k in (("file", "key", "count") if per_file else ("key", "count"))]
+    for a, b in zip(got, want):
+        assert np.array_equal(a, b)
+    B.gt_free_result(r)
+    B.gt_free_grammar(gh)
