@@ -583,8 +583,15 @@ void file_sizes(gt_grammar* g, cudaStream_t s) {
   g->fentry_bound = g->fword_bound = g->fsym_bound = 0;
   if (d.F > 64) return;
   const int threads = 256, cap = ctx->num_sms * 16;
-  Buf mask(ctx, size_t(d.R) * 8, s), tot(ctx, 32, s);
-  auto* M = mask.as<unsigned long long>();
+  // persistent: masks, slot offsets and the pair count (freed with the grammar)
+  void* p = nullptr;
+  GT_CUDA(cudaMalloc(&p, size_t(d.R) * 16 + 16));
+  g->owned.push_back(p);
+  g->info.device_bytes += int64_t(d.R) * 16 + 16;
+  auto* M = static_cast<unsigned long long*>(p);
+  auto* off = reinterpret_cast<int64_t*>(M + d.R);
+  auto* nnz = off + d.R;
+  Buf tot(ctx, 32, s), cnt(ctx, size_t(d.R) * 8, s), sc(ctx, scan_scratch_bytes(d.R), s);
   fmask_root_kernel<<<grid_for(d.R, threads, cap), threads, 0, s>>>(d.rfile_off, d.rfile_f, d.R, M);
   GT_LAUNCH_CHECK();
   for (int lv = 2; lv < d.depth; ++lv) {
@@ -594,6 +601,11 @@ void file_sizes(gt_grammar* g, cudaStream_t s) {
       GT_LAUNCH_CHECK();
     }
   }
+  popc_kernel<<<grid_for(d.R, threads, cap), threads, 0, s>>>(M, d.R, cnt.as<int64_t>());
+  GT_LAUNCH_CHECK();
+  exclusive_scan_i64(cnt.as<int64_t>(), off, d.R, sc.p, s);
+  last_total_kernel<<<1, 1, 0, s>>>(off, cnt.as<int64_t>(), d.R, nnz, nullptr);
+  GT_LAUNCH_CHECK();
   GT_CUDA(cudaMemsetAsync(tot.p, 0, 32, s));
   mask_totals_kernel<<<grid_for(d.R, threads, cap), threads, 0, s>>>(M, d.nwords, d.nrefs, d.R,
                                                                       tot.as<unsigned long long>());
@@ -604,6 +616,9 @@ void file_sizes(gt_grammar* g, cudaStream_t s) {
   g->fentry_bound = int64_t(h[0]);
   g->fword_bound = int64_t(h[1]);
   g->fsym_bound = int64_t(h[2]);
+  g->fmask = M;
+  g->foff = off;
+  g->fnnz = nnz;
 }
 
 void file_weights(gt_grammar* g, cudaStream_t s, FileWeights& fw) {
@@ -614,36 +629,21 @@ void file_weights(gt_grammar* g, cudaStream_t s, FileWeights& fw) {
   if (F > 64) fail(GT_EOVERFLOW, "the top-down per-file strategy holds at most 64 files (file_strategy 0 or 2 selects bottom-up)");
   if (d.N >= (uint64_t(1) << 32)) fail(GT_EOVERFLOW, "per-file analytics need fewer than 2^32 tokens per grammar");
   if (V > (1 << 21)) fail(GT_EOVERFLOW, "per-file analytics support num_words <= 2^21");
+  if (!g->fmask) fail(GT_EINVAL, "per-file layout missing");
   const int64_t EB = g->fentry_bound;
-  fw.mask = Buf(ctx, size_t(R) * 8, s);
-  fw.off = Buf(ctx, size_t(R) * 8, s);
-  fw.nnz = Buf(ctx, 8, s);
-  Buf cnt(ctx, size_t(R) * 8, s), sc(ctx, scan_scratch_bytes(R), s);
-  auto* M = fw.mask.as<unsigned long long>();
-  fmask_root_kernel<<<grid_for(R, threads, cap), threads, 0, s>>>(d.rfile_off, d.rfile_f, R, M);
-  GT_LAUNCH_CHECK();
-  for (int lv = 2; lv < d.depth; ++lv) {
-    const int64_t a = g->ledge_off[lv], b = g->ledge_off[lv + 1];
-    if (b > a) {
-      fmask_edges_kernel<<<grid_for(b - a, threads, cap), threads, 0, s>>>(d.ledge_child, d.ledge_par, a, b, M);
-      GT_LAUNCH_CHECK();
-    }
-  }
-  popc_kernel<<<grid_for(R, threads, cap), threads, 0, s>>>(M, R, cnt.as<int64_t>());
-  GT_LAUNCH_CHECK();
-  exclusive_scan_i64(cnt.as<int64_t>(), fw.off.as<int64_t>(), R, sc.p, s);
-  last_total_kernel<<<1, 1, 0, s>>>(fw.off.as<int64_t>(), cnt.as<int64_t>(), R, fw.nnz.as<int64_t>(), nullptr);
-  GT_LAUNCH_CHECK();
+  fw.mask = g->fmask;
+  fw.off = g->foff;
+  fw.nnz = g->fnnz;
   fw.w = Buf(ctx, size_t(EB) * 4, s);
   if (EB > 0) GT_CUDA(cudaMemsetAsync(fw.w.p, 0, size_t(EB) * 4, s));
-  fweight_root_kernel<<<grid_for(R, threads, cap), threads, 0, s>>>(d.rfile_off, d.rfile_f, d.rfile_m, R,
-                                                                     fw.off.as<int64_t>(), M, fw.w.as<uint32_t>());
+  fweight_root_kernel<<<grid_for(R, threads, cap), threads, 0, s>>>(d.rfile_off, d.rfile_f, d.rfile_m, R, fw.off,
+                                                                     fw.mask, fw.w.as<uint32_t>());
   GT_LAUNCH_CHECK();
   for (int lv = 2; lv < d.depth; ++lv) {
     const int64_t a = g->ledge_off[lv], b = g->ledge_off[lv + 1];
     if (b > a) {
       fweight_edges_kernel<<<grid_for(b - a, threads, cap), threads, 0, s>>>(
-          d.ledge_child, d.ledge_par, d.ledge_mult, a, b, fw.off.as<int64_t>(), M, fw.w.as<uint32_t>());
+          d.ledge_child, d.ledge_par, d.ledge_mult, a, b, fw.off, fw.mask, fw.w.as<uint32_t>());
       GT_LAUNCH_CHECK();
     }
   }
@@ -660,11 +660,11 @@ void file_hist(gt_grammar* g, cudaStream_t s, FileHist& fh) {
   Phase ph(ctx, "file_weights", s);
   FileWeights fwt;
   file_weights(g, s, fwt);
-  auto* M = fwt.mask.as<unsigned long long>();
+  const unsigned long long* M = fwt.mask;
   Buf dev(ctx, 8, s);
-  int64_t* nnz_d = fwt.nnz.as<int64_t>();
+  const int64_t* nnz_d = fwt.nnz;
   int64_t* nx_d = dev.as<int64_t>();  // emitted rule words
-  Buf& off = fwt.off;
+  const int64_t* off = fwt.off;
   Buf& w = fwt.w;
   // ---- rule words per file (file-major) ----
   Buf keys(ctx, size_t(EB) * 8, s), skeys(ctx, size_t(EB) * 8, s), swt(ctx, size_t(EB) * 4, s);
@@ -673,7 +673,7 @@ void file_hist(gt_grammar* g, cudaStream_t s, FileHist& fh) {
   Buf fstart(ctx, size_t(F + 1) * 8, s), xoff(ctx, size_t(F + 1) * 8, s);
   GT_CUDA(cudaMemsetAsync(nx_d, 0, 8, s));
   if (EB > 0) {
-    fentry_keys_kernel<<<grid_for(R, threads, cap), threads, 0, s>>>(M, off.as<int64_t>(), R, keys.as<uint64_t>());
+    fentry_keys_kernel<<<grid_for(R, threads, cap), threads, 0, s>>>(M, off, R, keys.as<uint64_t>());
     GT_LAUNCH_CHECK();
     pad_keys_kernel<<<grid_for(EB, threads, cap), threads, 0, s>>>(keys.as<uint64_t>(), nnz_d, EB, F);
     GT_LAUNCH_CHECK();

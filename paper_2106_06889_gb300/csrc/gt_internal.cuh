@@ -177,6 +177,11 @@ struct gt_grammar {
   int64_t fentry_bound = 0;       // (rule, file) pairs with a nonzero per-file weight (<= 64 files)
   int64_t fword_bound = 0;        // rule words emitted once per such pair
   int64_t fsym_bound = 0;         // rule body symbols visited once per such pair
+  // top-down per-file layout (<= 64 files), built at load: the set of files
+  // holding each rule (64-bit mask) and each rule's first (rule, file) slot
+  const unsigned long long* fmask = nullptr;
+  const int64_t* foff = nullptr;
+  const int64_t* fnnz = nullptr;
   int64_t bu_words = 0;           // sum over distinct (file, root child) pairs of the child's length
   int64_t bu_windows = 0;         // ... and of the child's 3-word windows
   int64_t max_file_len = 0;       // tokens of the longest file
@@ -395,10 +400,10 @@ gt_result* run_term_vector(gt_grammar* g, int top_k, cudaStream_t s);
 // Top-down per-file weights (<= 64 files): rule r's files are the set bits of
 // mask[r]; its weight in its k-th file (ascending) is w[off[r] + k].
 struct FileWeights {
-  Buf mask;  // uint64 [R]
-  Buf off;   // int64  [R]
-  Buf w;     // uint32 [bound]
-  Buf nnz;   // int64: number of (rule, file) pairs
+  const unsigned long long* mask = nullptr;  // [R] files holding each rule (the grammar's, from load)
+  const int64_t* off = nullptr;              // [R] first (rule, file) slot of each rule (from load)
+  const int64_t* nnz = nullptr;              // number of (rule, file) pairs (from load)
+  Buf w;                                     // uint32 [pairs]: per-file weights of this query
 };
 void file_weights(gt_grammar* g, cudaStream_t s, FileWeights& fw);
 // at load: exact sizes of the per-file buffers (<= 64 files)

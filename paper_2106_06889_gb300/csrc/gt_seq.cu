@@ -483,13 +483,13 @@ void sorted_windows(gt_grammar* g, bool per_file, cudaStream_t s, Windows& out) 
   Buf k0(ctx, size_t(bound) * 8, s), f0(ctx, size_t(bound) * 8, s), v0(ctx, size_t(bound) * 4, s);
   if (d.G > 0) {
     win_count_file_kernel<<<grid_for(d.G, threads, cap), threads, 0, s>>>(
-        d, head.as<int32_t>(), tail.as<int32_t>(), fw.mask.as<unsigned long long>(), kb, cnt.as<int64_t>());
+        d, head.as<int32_t>(), tail.as<int32_t>(), fw.mask, kb, cnt.as<int64_t>());
     GT_LAUNCH_CHECK();
     exclusive_scan_i64(cnt.as<int64_t>(), pos.as<int64_t>(), d.G, sc.p, s);
     last_total2_kernel<<<1, 1, 0, s>>>(pos.as<int64_t>(), cnt.as<int64_t>(), d.G, nd.as<int64_t>(), nullptr);
     GT_LAUNCH_CHECK();
     win_emit_file_kernel<<<grid_for(d.G, threads, cap), threads, 0, s>>>(
-        d, head.as<int32_t>(), tail.as<int32_t>(), fw.mask.as<unsigned long long>(), fw.off.as<int64_t>(),
+        d, head.as<int32_t>(), tail.as<int32_t>(), fw.mask, fw.off,
         fw.w.as<uint32_t>(), kb, pos.as<int64_t>(), k0.as<uint64_t>(), f0.as<uint64_t>(), v0.as<uint32_t>());
     GT_LAUNCH_CHECK();
   }
