@@ -137,14 +137,6 @@ __global__ void fentry_keys_kernel(const unsigned long long* __restrict__ mask, 
   }
 }
 
-// Keys past the real entries (n_dev) carry file F so they sort last.
-__global__ void pad_keys_kernel(uint64_t* __restrict__ keys, const int64_t* __restrict__ n_dev, int64_t bound,
-                                int32_t F) {
-  const int64_t n = *n_dev;
-  for (int64_t i = n + blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < bound; i += int64_t(gridDim.x) * blockDim.x)
-    keys[i] = uint64_t(uint32_t(F)) << 32;
-}
-
 __global__ void entry_words_kernel(const uint64_t* __restrict__ keys, int64_t n, const int32_t* __restrict__ W,
                                    int32_t F, int64_t* __restrict__ cnt) {
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
@@ -169,6 +161,17 @@ __global__ void expand_words_kernel(const uint64_t* __restrict__ keys, const uin
       }
     }
   }
+}
+
+__global__ void iota_u32_kernel(uint32_t* __restrict__ x, int64_t n) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    x[i] = uint32_t(i);
+}
+
+__global__ void gather_w_kernel(const uint32_t* __restrict__ w, const uint32_t* __restrict__ slot, int64_t n,
+                                uint32_t* __restrict__ out) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    out[i] = w[slot[i]];
 }
 
 // xoff[f] = position of file f's first emitted word.
@@ -619,6 +622,41 @@ void file_sizes(gt_grammar* g, cudaStream_t s) {
   g->fmask = M;
   g->foff = off;
   g->fnnz = nnz;
+  // the pairs in file-major order with their word offsets (persistent)
+  const int64_t EB = g->fentry_bound;
+  void* q = nullptr;
+  const size_t qbytes = size_t(EB) * 8 + size_t(EB) * 4 + size_t(EB + 1) * 8 + size_t(d.F + 1) * 8 + 64;
+  GT_CUDA(cudaMalloc(&q, qbytes));
+  g->owned.push_back(q);
+  g->info.device_bytes += int64_t(qbytes);
+  auto* fkeys = static_cast<uint64_t*>(q);
+  auto* fslot = reinterpret_cast<uint32_t*>(fkeys + EB);
+  auto* fpos = reinterpret_cast<int64_t*>(reinterpret_cast<char*>(fslot) + (size_t(EB) * 4 + 15) / 16 * 16);
+  auto* fxoff = fpos + EB + 1;
+  Buf keys(ctx, size_t(EB) * 8, s), slot0(ctx, size_t(EB) * 4, s), rs(ctx, radix_scratch_bytes(EB, true, 4), s);
+  Buf wcnt(ctx, size_t(EB) * 8, s), sc2(ctx, scan_scratch_bytes(EB), s), fstart(ctx, size_t(d.F + 1) * 8, s);
+  if (EB > 0) {
+    fentry_keys_kernel<<<grid_for(d.R, threads, cap), threads, 0, s>>>(M, off, d.R, keys.as<uint64_t>());
+    GT_LAUNCH_CHECK();
+    iota_u32_kernel<<<grid_for(EB, threads, cap), threads, 0, s>>>(slot0.as<uint32_t>(), EB);
+    GT_LAUNCH_CHECK();
+    radix_sort_u64(keys.as<uint64_t>(), fkeys, slot0.p, fslot, 4, EB, 32, 32 + bits_for(d.F), rs.p, s);
+    entry_words_kernel<<<grid_for(EB, threads, cap), threads, 0, s>>>(fkeys, EB, d.nwords, d.F, wcnt.as<int64_t>());
+    GT_LAUNCH_CHECK();
+    exclusive_scan_i64(wcnt.as<int64_t>(), fpos, EB, sc2.p, s);
+    last_total_kernel<<<1, 1, 0, s>>>(fpos, wcnt.as<int64_t>(), EB, fpos + EB, nullptr);
+    GT_LAUNCH_CHECK();
+  } else {
+    GT_CUDA(cudaMemsetAsync(fpos, 0, 8, s));
+  }
+  csr_offsets_hi(fkeys, EB, d.F, fstart.as<int64_t>(), s);
+  file_starts_kernel<<<1, 128, 0, s>>>(fstart.as<int64_t>(), fpos, wcnt.as<int64_t>(), EB, d.F, fxoff);
+  GT_LAUNCH_CHECK();
+  GT_CUDA(cudaStreamSynchronize(s));
+  g->fe_keys = fkeys;
+  g->fe_slot = fslot;
+  g->fe_pos = fpos;
+  g->fe_xoff = fxoff;
 }
 
 void file_weights(gt_grammar* g, cudaStream_t s, FileWeights& fw) {
@@ -660,40 +698,18 @@ void file_hist(gt_grammar* g, cudaStream_t s, FileHist& fh) {
   Phase ph(ctx, "file_weights", s);
   FileWeights fwt;
   file_weights(g, s, fwt);
-  const unsigned long long* M = fwt.mask;
-  Buf dev(ctx, 8, s);
-  const int64_t* nnz_d = fwt.nnz;
-  int64_t* nx_d = dev.as<int64_t>();  // emitted rule words
-  const int64_t* off = fwt.off;
   Buf& w = fwt.w;
-  // ---- rule words per file (file-major) ----
-  Buf keys(ctx, size_t(EB) * 8, s), skeys(ctx, size_t(EB) * 8, s), swt(ctx, size_t(EB) * 4, s);
-  Buf rs(ctx, radix_scratch_bytes(EB, true, 4), s);
-  Buf wcnt(ctx, size_t(EB) * 8, s), pos(ctx, size_t(EB) * 8, s), sc2(ctx, scan_scratch_bytes(EB), s);
-  Buf fstart(ctx, size_t(F + 1) * 8, s), xoff(ctx, size_t(F + 1) * 8, s);
-  GT_CUDA(cudaMemsetAsync(nx_d, 0, 8, s));
+  // ---- rule words per file (file-major): the pairs' order comes from load,
+  // each pair's weight is gathered from its rule-major slot ----
+  Buf swt(ctx, size_t(EB) * 4, s), xw(ctx, size_t(XB) * 4, s), xwt(ctx, size_t(XB) * 4, s);
+  const int64_t* pos = g->fe_pos;
+  const int64_t* xoff = g->fe_xoff;
   if (EB > 0) {
-    fentry_keys_kernel<<<grid_for(R, threads, cap), threads, 0, s>>>(M, off, R, keys.as<uint64_t>());
+    gather_w_kernel<<<grid_for(EB, threads, cap), threads, 0, s>>>(w.as<uint32_t>(), g->fe_slot, EB,
+                                                                    swt.as<uint32_t>());
     GT_LAUNCH_CHECK();
-    pad_keys_kernel<<<grid_for(EB, threads, cap), threads, 0, s>>>(keys.as<uint64_t>(), nnz_d, EB, F);
-    GT_LAUNCH_CHECK();
-    radix_sort_u64(keys.as<uint64_t>(), skeys.as<uint64_t>(), w.p, swt.p, 4, EB, 32, 32 + bits_for(F), rs.p, s);
-    entry_words_kernel<<<grid_for(EB, threads, cap), threads, 0, s>>>(skeys.as<uint64_t>(), EB, d.nwords, F,
-                                                                       wcnt.as<int64_t>());
-    GT_LAUNCH_CHECK();
-    exclusive_scan_i64(wcnt.as<int64_t>(), pos.as<int64_t>(), EB, sc2.p, s);
-    last_total_kernel<<<1, 1, 0, s>>>(pos.as<int64_t>(), wcnt.as<int64_t>(), EB, nx_d, nullptr);
-    GT_LAUNCH_CHECK();
-  }
-  csr_offsets_hi(skeys.as<uint64_t>(), EB, F, fstart.as<int64_t>(), s);
-  file_starts_kernel<<<1, 128, 0, s>>>(fstart.as<int64_t>(), pos.as<int64_t>(), wcnt.as<int64_t>(), EB, F,
-                                       xoff.as<int64_t>());
-  GT_LAUNCH_CHECK();
-  Buf xw(ctx, size_t(XB) * 4, s), xwt(ctx, size_t(XB) * 4, s);
-  if (EB > 0) {
-    expand_words_kernel<<<grid_for(EB, threads, cap), threads, 0, s>>>(skeys.as<uint64_t>(), swt.as<uint32_t>(), EB,
-                                                                        pos.as<int64_t>(), d, xw.as<int32_t>(),
-                                                                        xwt.as<uint32_t>());
+    expand_words_kernel<<<grid_for(EB, threads, cap), threads, 0, s>>>(g->fe_keys, swt.as<uint32_t>(), EB, pos, d,
+                                                                        xw.as<int32_t>(), xwt.as<uint32_t>());
     GT_LAUNCH_CHECK();
   }
   // ---- bucket-sorted chunks, then dense (file, bucket) histograms ----
@@ -721,7 +737,7 @@ void file_hist(gt_grammar* g, cudaStream_t s, FileHist& fh) {
     const int64_t nxc = XB / kChunk + F + 1;  // bound on the rule-word chunks
     Buf xcs(ctx, size_t(nxc) * 8, s), xcl(ctx, size_t(nxc) * 4, s), xcf(ctx, size_t(F + 1) * 8, s), xcn(ctx, 8, s);
     Buf xent(ctx, size_t(XB) * 8 + 16, s), xrs(ctx, size_t(nxc) * nb * 8, s), xrl(ctx, size_t(nxc) * nb * 4, s);
-    rule_chunks_kernel<<<1, 128, 0, s>>>(xoff.as<int64_t>(), F, xcs.as<int64_t>(), xcl.as<int32_t>(), xcf.as<int64_t>(),
+    rule_chunks_kernel<<<1, 128, 0, s>>>(xoff, F, xcs.as<int64_t>(), xcl.as<int32_t>(), xcf.as<int64_t>(),
                                         xcn.as<int64_t>());
     GT_LAUNCH_CHECK();
     Chunks xc{xcs.as<int64_t>(), xcl.as<int32_t>(), xcf.as<int64_t>(), xcn.as<int64_t>()};

@@ -182,6 +182,12 @@ struct gt_grammar {
   const unsigned long long* fmask = nullptr;
   const int64_t* foff = nullptr;
   const int64_t* fnnz = nullptr;
+  // the (rule, file) pairs in file-major order: (file << 32 | rule), the
+  // rule-major slot of each, the offset of its rule words, file starts
+  const uint64_t* fe_keys = nullptr;
+  const uint32_t* fe_slot = nullptr;
+  const int64_t* fe_pos = nullptr;
+  const int64_t* fe_xoff = nullptr;
   int64_t bu_words = 0;           // sum over distinct (file, root child) pairs of the child's length
   int64_t bu_windows = 0;         // ... and of the child's 3-word windows
   int64_t max_file_len = 0;       // tokens of the longest file
