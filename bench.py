@@ -99,7 +99,6 @@ class ClockSampler:
 # kernel as it stands (see the named profile); None once the kernel changes.
 NCU_TRAFFIC = {
     "wc_partition_kernel": (221.78e6, "profiles/wc_partition_kernel_multi64_50m.md"),
-    "tv_hist_kernel": (205.80e6, "profiles/tv_hist_kernel_multi64_50m.md"),
 }
 
 

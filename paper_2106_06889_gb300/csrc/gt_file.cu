@@ -20,6 +20,8 @@
 //      the bits are turned into ascending file lists for the inverted index.
 #include <algorithm>
 
+#include <vector>
+
 #include "gt_device.cuh"
 
 namespace gt {
@@ -390,12 +392,15 @@ __global__ void __launch_bounds__(kTvThreads) tv_hist_kernel(int32_t F, int nb, 
                                                              const uint16_t* __restrict__ rent, Chunks xc,
                                                              const int64_t* __restrict__ xrs,
                                                              const int32_t* __restrict__ xrl,
-                                                             const uint64_t* __restrict__ xent, TvSlots out) {
+                                                             const uint64_t* __restrict__ xent, const int32_t* __restrict__ order,
+                                                             TvSlots out) {
   __shared__ uint32_t hist[kFBucket];
   __shared__ int64_t warp_tot[kTvThreads / 32 + 1];
   __shared__ int64_t s_start[kTvBatch];
   __shared__ int32_t s_len[kTvBatch];
-  const int f = blockIdx.x / nb, b = blockIdx.x % nb;
+  // pieces of the longest files first (order: files by length, descending)
+  const int f = order[blockIdx.x / nb], b = blockIdx.x % nb;
+  const int64_t piece = int64_t(f) * nb + b;
   const int tid = threadIdx.x;
   for (int i = tid; i < kFBucket; i += kTvThreads) hist[i] = 0;
   tv_runs<uint16_t>(hist, rc.foff[f], rc.foff[f + 1], nb, b, rrs, rrl, rent, s_start, s_len);
@@ -416,7 +421,7 @@ __global__ void __launch_bounds__(kTvThreads) tv_hist_kernel(int32_t F, int nb, 
     if (lane == r) my_mask = m;
     wcount += __popc(m);
   }
-  out.bits[int64_t(blockIdx.x) * kTvThreads + warp * 32 + lane] = my_mask;
+  out.bits[piece * kTvThreads + warp * 32 + lane] = my_mask;
   if (lane == 0) warp_tot[warp] = wcount;
   __syncthreads();
   if (warp == 0) {
@@ -431,7 +436,7 @@ __global__ void __launch_bounds__(kTvThreads) tv_hist_kernel(int32_t F, int nb, 
     if (lane == kTvThreads / 32 - 1) warp_tot[kTvThreads / 32] = wi;
   }
   __syncthreads();
-  const int64_t slot = int64_t(blockIdx.x) * kFBucket;
+  const int64_t slot = piece * kFBucket;
   const int32_t wbase = b << kFBLog2;
   int64_t o = slot + warp_tot[warp];
   const uint32_t below = (1u << lane) - 1u;
@@ -446,7 +451,7 @@ __global__ void __launch_bounds__(kTvThreads) tv_hist_kernel(int32_t F, int nb, 
     }
     o += __popc(m);
   }
-  if (tid == 0) out.nnz[blockIdx.x] = warp_tot[kTvThreads / 32];
+  if (tid == 0) out.nnz[piece] = warp_tot[kTvThreads / 32];
 }
 
 // Copy every (file, bucket) piece to its place in the term vector.
@@ -657,6 +662,18 @@ void file_sizes(gt_grammar* g, cudaStream_t s) {
   g->fe_slot = fslot;
   g->fe_pos = fpos;
   g->fe_xoff = fxoff;
+  // files by length, longest first (launch order of per-file work)
+  std::vector<uint64_t> hl(size_t(d.F));
+  if (d.F > 0) GT_CUDA(cudaMemcpy(hl.data(), d.file_len, size_t(d.F) * 8, cudaMemcpyDeviceToHost));
+  std::vector<int32_t> ord(size_t(d.F));
+  for (int32_t f = 0; f < d.F; ++f) ord[size_t(f)] = f;
+  std::stable_sort(ord.begin(), ord.end(), [&](int32_t a, int32_t b) { return hl[size_t(a)] > hl[size_t(b)]; });
+  void* po = nullptr;
+  GT_CUDA(cudaMalloc(&po, size_t(d.F) * 4 + 16));
+  g->owned.push_back(po);
+  g->info.device_bytes += int64_t(d.F) * 4 + 16;
+  if (d.F > 0) GT_CUDA(cudaMemcpy(po, ord.data(), size_t(d.F) * 4, cudaMemcpyHostToDevice));
+  g->file_order = static_cast<const int32_t*>(po);
 }
 
 void file_weights(gt_grammar* g, cudaStream_t s, FileWeights& fw) {
@@ -747,7 +764,7 @@ void file_hist(gt_grammar* g, cudaStream_t s, FileHist& fh) {
     Phase ph3(ctx, "tv_hist_kernel", s);
     tv_hist_kernel<<<unsigned(pieces), kTvThreads, 0, s>>>(F, nb, rc, rrs.as<int64_t>(), rrl.as<int32_t>(),
                                                            rent.as<uint16_t>(), xc, xrs.as<int64_t>(),
-                                                           xrl.as<int32_t>(), xent.as<uint64_t>(), ts);
+                                                           xrl.as<int32_t>(), xent.as<uint64_t>(), g->file_order, ts);
     GT_LAUNCH_CHECK();
   }
   Buf sc3(ctx, scan_scratch_bytes(pieces), s);

@@ -188,6 +188,7 @@ struct gt_grammar {
   const uint32_t* fe_slot = nullptr;
   const int64_t* fe_pos = nullptr;
   const int64_t* fe_xoff = nullptr;
+  const int32_t* file_order = nullptr;  // files by length, longest first
   int64_t bu_words = 0;           // sum over distinct (file, root child) pairs of the child's length
   int64_t bu_windows = 0;         // ... and of the child's 3-word windows
   int64_t max_file_len = 0;       // tokens of the longest file
