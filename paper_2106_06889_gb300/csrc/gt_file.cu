@@ -97,8 +97,14 @@ __device__ __forceinline__ int64_t slot_of(const int64_t* off, const unsigned lo
 __global__ void fweight_root_kernel(const int64_t* __restrict__ rfile_off, const int32_t* __restrict__ rfile_f,
                                     const uint32_t* __restrict__ rfile_m, int32_t R, const int64_t* __restrict__ off,
                                     const unsigned long long* __restrict__ mask, uint32_t* __restrict__ w) {
-  for (int64_t c = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; c < R; c += int64_t(gridDim.x) * blockDim.x)
-    for (int64_t e = rfile_off[c]; e < rfile_off[c + 1]; ++e) w[slot_of(off, mask, int32_t(c), rfile_f[e])] = rfile_m[e];
+  for (int64_t c = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; c < R; c += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t e1 = rfile_off[c + 1];
+    const int64_t o = off[c];
+    const unsigned long long cm = mask[c];
+#pragma unroll 4
+    for (int64_t e = rfile_off[c]; e < e1; ++e)
+      w[o + __popcll(cm & ((1ull << rfile_f[e]) - 1ull))] = rfile_m[e];
+  }
 }
 
 // One level: every non-root parent edge adds mult * (parent's weight in file f)
@@ -116,11 +122,20 @@ __global__ void fweight_edges_kernel(const int32_t* __restrict__ lchild, const i
     const unsigned long long cm = mask[c];
     const int64_t po = off[p], co = off[c];
     int k = 0;
-    while (pm) {
-      const int f = __ffsll(pm) - 1;
-      pm &= pm - 1;
-      atomicAdd(&w[co + __popcll(cm & ((1ull << f) - 1ull))], m * w[po + k]);
-      ++k;
+    while (pm) {  // 4 files at a time: their parent weights are loaded together
+      int f[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        f[u] = pm ? __ffsll(pm) - 1 : -1;
+        pm &= pm - 1;
+      }
+      uint32_t pw[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) pw[u] = f[u] >= 0 ? w[po + k + u] : 0u;
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (f[u] >= 0) atomicAdd(&w[co + __popcll(cm & ((1ull << f[u]) - 1ull))], m * pw[u]);
+      k += 4;
     }
   }
 }
