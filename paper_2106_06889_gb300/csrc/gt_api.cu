@@ -188,10 +188,19 @@ GT_API gt_status gt_load_grammar(gt_ctx* ctx, const gt_grammar_desc* desc, void*
     if (V < 1 || R < 1 || F < 1) fail(GT_EINVAL, "num_words, num_rules and num_files must be >= 1");
     if (int64_t(V) + int64_t(R) >= (int64_t(1) << 31)) fail(GT_EOVERFLOW, "num_words + num_rules must be < 2^31");
     if (!desc->rule_off || !desc->file_off) fail(GT_EINVAL, "null offsets");
-    const cudaMemcpyKind kind = desc->on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
-    std::vector<int64_t> roff(size_t(R) + 1), foff(size_t(F) + 1);
-    GT_CUDA(cudaMemcpy(roff.data(), desc->rule_off, roff.size() * 8, kind));
-    GT_CUDA(cudaMemcpy(foff.data(), desc->file_off, foff.size() * 8, kind));
+    // validate the offsets on the host: the caller's arrays in place, or a
+    // copy when they live on the device
+    std::vector<int64_t> roff_copy, foff_copy;
+    const int64_t* roff = desc->rule_off;
+    const int64_t* foff = desc->file_off;
+    if (desc->on_device) {
+      roff_copy.resize(size_t(R) + 1);
+      foff_copy.resize(size_t(F) + 1);
+      GT_CUDA(cudaMemcpy(roff_copy.data(), desc->rule_off, roff_copy.size() * 8, cudaMemcpyDeviceToHost));
+      GT_CUDA(cudaMemcpy(foff_copy.data(), desc->file_off, foff_copy.size() * 8, cudaMemcpyDeviceToHost));
+      roff = roff_copy.data();
+      foff = foff_copy.data();
+    }
     if (roff[0] != 0) fail(GT_EINVAL, "rule_off[0] must be 0");
     for (int32_t r = 0; r < R; ++r) {
       if (roff[r + 1] < roff[r]) fail(GT_EINVAL, "rule_off must be non-decreasing");
@@ -210,28 +219,23 @@ GT_API gt_status gt_load_grammar(gt_ctx* ctx, const gt_grammar_desc* desc, void*
     d.F = F;
     d.G = G;
     d.root_len = root_len;
-    // symbols padded to whole tiles with -1 (never a word, never a rule)
+    // symbols padded to whole tiles with -1 (never a word, never a rule);
+    // uploads go straight from the caller's arrays (DMA when they are pinned)
+    const cudaMemcpyKind up = desc->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     const int64_t Gp = std::max<int64_t>((G + gt::kTile - 1) / gt::kTile, 1) * gt::kTile;
-    void* p;
-    GT_CUDA(cudaMalloc(&p, size_t(Gp) * 4));
-    g->owned.push_back(p);
-    GT_CUDA(cudaMemsetAsync(p, 0xff, size_t(Gp) * 4, s));
-    if (G > 0)
-      GT_CUDA(cudaMemcpyAsync(p, desc->sym, size_t(G) * 4,
-                              desc->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    void* p = gt::grammar_alloc(g, size_t(Gp) * 4, s);
+    if (Gp > G) GT_CUDA(cudaMemsetAsync(static_cast<int32_t*>(p) + G, 0xff, size_t(Gp - G) * 4, s));
+    if (G > 0) GT_CUDA(cudaMemcpyAsync(p, desc->sym, size_t(G) * 4, up, s));
     d.sym = static_cast<int32_t*>(p);
-    GT_CUDA(cudaMalloc(&p, roff.size() * 8));
-    g->owned.push_back(p);
-    GT_CUDA(cudaMemcpyAsync(p, roff.data(), roff.size() * 8, cudaMemcpyHostToDevice, s));
+    p = gt::grammar_alloc(g, size_t(R + 1) * 8, s);
+    GT_CUDA(cudaMemcpyAsync(p, desc->rule_off, size_t(R + 1) * 8, up, s));
     d.rule_off = static_cast<int64_t*>(p);
-    GT_CUDA(cudaMalloc(&p, foff.size() * 8));
-    g->owned.push_back(p);
-    GT_CUDA(cudaMemcpyAsync(p, foff.data(), foff.size() * 8, cudaMemcpyHostToDevice, s));
+    p = gt::grammar_alloc(g, size_t(F + 1) * 8, s);
+    GT_CUDA(cudaMemcpyAsync(p, desc->file_off, size_t(F + 1) * 8, up, s));
     d.file_off = static_cast<int64_t*>(p);
-    g->info.device_bytes = Gp * 4 + int64_t(roff.size() + foff.size()) * 8;
     {
-      // file-pure chunks of the root (per-file analytics)
-      std::vector<int64_t> cs, cf(size_t(F) + 1);
+      // file-pure chunks of the root (per-file analytics), one upload
+      std::vector<int64_t> cs, cf(size_t(F) + 2);
       std::vector<int32_t> cl;
       for (int32_t f = 0; f < F; ++f) {
         cf[f] = int64_t(cs.size());
@@ -240,24 +244,22 @@ GT_API gt_status gt_load_grammar(gt_ctx* ctx, const gt_grammar_desc* desc, void*
           cl.push_back(int32_t(std::min<int64_t>(gt::kFileChunk, foff[f + 1] - q)));
         }
       }
-      cf[F] = int64_t(cs.size());
       const int64_t nc = int64_t(cs.size());
+      cf[F] = nc;
+      cf[F + 1] = nc;
       g->root_chunks = nc;
-      void* q;
-      GT_CUDA(cudaMalloc(&q, size_t(nc + 1) * 8));
-      g->owned.push_back(q);
-      if (nc) GT_CUDA(cudaMemcpy(q, cs.data(), size_t(nc) * 8, cudaMemcpyHostToDevice));
-      d.rch_start = static_cast<int64_t*>(q);
-      GT_CUDA(cudaMalloc(&q, size_t(nc + 1) * 4));
-      g->owned.push_back(q);
-      if (nc) GT_CUDA(cudaMemcpy(q, cl.data(), size_t(nc) * 4, cudaMemcpyHostToDevice));
-      d.rch_len = static_cast<int32_t*>(q);
-      GT_CUDA(cudaMalloc(&q, size_t(F + 2) * 8));
-      g->owned.push_back(q);
-      GT_CUDA(cudaMemcpy(q, cf.data(), size_t(F + 1) * 8, cudaMemcpyHostToDevice));
-      GT_CUDA(cudaMemcpy(static_cast<int64_t*>(q) + F + 1, &nc, 8, cudaMemcpyHostToDevice));
-      d.rch_foff = static_cast<int64_t*>(q);
-      d.rch_count = static_cast<int64_t*>(q) + F + 1;
+      std::vector<char> blob(size_t(nc + 1) * 8 + size_t(F + 2) * 8 + size_t(nc + 1) * 4);
+      char* bp = blob.data();
+      std::memcpy(bp, cs.data(), size_t(nc) * 8);
+      std::memcpy(bp + size_t(nc + 1) * 8, cf.data(), size_t(F + 2) * 8);
+      std::memcpy(bp + size_t(nc + 1) * 8 + size_t(F + 2) * 8, cl.data(), size_t(nc) * 4);
+      char* q = static_cast<char*>(gt::grammar_alloc(g, blob.size(), s));
+      GT_CUDA(cudaMemcpyAsync(q, blob.data(), blob.size(), cudaMemcpyHostToDevice, s));
+      GT_CUDA(cudaStreamSynchronize(s));  // blob is a host temporary
+      d.rch_start = reinterpret_cast<int64_t*>(q);
+      d.rch_foff = reinterpret_cast<int64_t*>(q + size_t(nc + 1) * 8);
+      d.rch_count = d.rch_foff + F + 1;
+      d.rch_len = reinterpret_cast<int32_t*>(q + size_t(nc + 1) * 8 + size_t(F + 2) * 8);
     }
     gt::load_build_dag(g, s);
     gt::file_sizes(g, s);
@@ -282,7 +284,7 @@ GT_API gt_status gt_free_grammar(gt_grammar* g) {
   cudaDeviceSynchronize();
   for (auto& e : g->wc_graphs)
     if (e.exec) cudaGraphExecDestroy(e.exec);
-  for (void* p : g->owned) cudaFree(p);
+  for (void* p : g->owned) cudaFreeAsync(p, nullptr);  // grammar memory comes from the context pool
   delete g;
   return GT_OK;
 }

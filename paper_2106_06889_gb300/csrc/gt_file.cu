@@ -607,10 +607,7 @@ void file_sizes(gt_grammar* g, cudaStream_t s) {
   if (d.F > 64) return;
   const int threads = 256, cap = ctx->num_sms * 16;
   // persistent: masks, slot offsets and the pair count (freed with the grammar)
-  void* p = nullptr;
-  GT_CUDA(cudaMalloc(&p, size_t(d.R) * 16 + 16));
-  g->owned.push_back(p);
-  g->info.device_bytes += int64_t(d.R) * 16 + 16;
+  void* p = grammar_alloc(g, size_t(d.R) * 16 + 16, s);
   auto* M = static_cast<unsigned long long*>(p);
   auto* off = reinterpret_cast<int64_t*>(M + d.R);
   auto* nnz = off + d.R;
@@ -644,11 +641,8 @@ void file_sizes(gt_grammar* g, cudaStream_t s) {
   g->fnnz = nnz;
   // the pairs in file-major order with their word offsets (persistent)
   const int64_t EB = g->fentry_bound;
-  void* q = nullptr;
   const size_t qbytes = size_t(EB) * 8 + size_t(EB) * 4 + size_t(EB + 1) * 8 + size_t(d.F + 1) * 8 + 64;
-  GT_CUDA(cudaMalloc(&q, qbytes));
-  g->owned.push_back(q);
-  g->info.device_bytes += int64_t(qbytes);
+  void* q = grammar_alloc(g, qbytes, s);
   auto* fkeys = static_cast<uint64_t*>(q);
   auto* fslot = reinterpret_cast<uint32_t*>(fkeys + EB);
   auto* fpos = reinterpret_cast<int64_t*>(reinterpret_cast<char*>(fslot) + (size_t(EB) * 4 + 15) / 16 * 16);
@@ -679,15 +673,16 @@ void file_sizes(gt_grammar* g, cudaStream_t s) {
   g->fe_xoff = fxoff;
   // files by length, longest first (launch order of per-file work)
   std::vector<uint64_t> hl(size_t(d.F));
-  if (d.F > 0) GT_CUDA(cudaMemcpy(hl.data(), d.file_len, size_t(d.F) * 8, cudaMemcpyDeviceToHost));
+  if (d.F > 0) {
+    GT_CUDA(cudaMemcpyAsync(hl.data(), d.file_len, size_t(d.F) * 8, cudaMemcpyDeviceToHost, s));
+    GT_CUDA(cudaStreamSynchronize(s));
+  }
   std::vector<int32_t> ord(size_t(d.F));
   for (int32_t f = 0; f < d.F; ++f) ord[size_t(f)] = f;
   std::stable_sort(ord.begin(), ord.end(), [&](int32_t a, int32_t b) { return hl[size_t(a)] > hl[size_t(b)]; });
-  void* po = nullptr;
-  GT_CUDA(cudaMalloc(&po, size_t(d.F) * 4 + 16));
-  g->owned.push_back(po);
-  g->info.device_bytes += int64_t(d.F) * 4 + 16;
-  if (d.F > 0) GT_CUDA(cudaMemcpy(po, ord.data(), size_t(d.F) * 4, cudaMemcpyHostToDevice));
+  void* po = grammar_alloc(g, size_t(d.F) * 4 + 16, s);
+  if (d.F > 0) GT_CUDA(cudaMemcpyAsync(po, ord.data(), size_t(d.F) * 4, cudaMemcpyHostToDevice, s));
+  GT_CUDA(cudaStreamSynchronize(s));  // ord is a host temporary
   g->file_order = static_cast<const int32_t*>(po);
 }
 

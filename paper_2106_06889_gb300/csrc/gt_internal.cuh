@@ -386,6 +386,17 @@ void bu_window_rows(gt_grammar* g, Buf& head, Buf& tail, int kb, uint64_t key_pa
 void run_file_batch_bu(gt_grammar* g, const int* tv_topk, int n_tv, gt_result** tv_out, gt_result** ii_out,
                        cudaStream_t s);
 gt_result* run_ranked_words_bu(gt_grammar* g, cudaStream_t s);
+// A device allocation that lives as long as the grammar: taken from the
+// context's stream-ordered pool (which keeps freed memory for reuse, so
+// loading and freeing grammars does not go back to the driver).
+inline void* grammar_alloc(gt_grammar* g, size_t bytes, cudaStream_t s) {
+  void* p = nullptr;
+  GT_CUDA(cudaMallocFromPoolAsync(&p, bytes ? bytes : 16, g->ctx->pool, s));
+  g->owned.push_back(p);
+  g->info.device_bytes += int64_t(bytes);
+  return p;
+}
+
 // gt_tune.cu: a parameter of this grammar (autotuned value, else the context's)
 int64_t gparam(const gt_grammar* g, const char* name, int64_t dflt);
 // gt_file.cu: term-vector result from (word, count) rows in (file, word) order

@@ -91,7 +91,7 @@ __global__ void edge_keys_kernel(const int32_t* __restrict__ sym, int64_t G, int
     }
     if (ref) {
       const uint32_t child = uint32_t(s - V);
-      const int64_t parent = upper_bound_i64(rule_off, int64_t(R) + 1, i) - 1;
+      const int64_t parent = i < root_len ? 0 : upper_bound_i64(rule_off, int64_t(R) + 1, i) - 1;
       gkeys[base + __popc(m & ((1u << lane) - 1u))] = (uint64_t(parent) << 32) | child;
       if (rootref) {
         const int64_t f = upper_bound_i64(file_off, int64_t(F) + 1, i) - 1;
@@ -170,13 +170,26 @@ __global__ void frontier_edges_kernel(const int32_t* __restrict__ order, int64_t
                                       const int64_t* __restrict__ cedge_off, const int32_t* __restrict__ cedge_child,
                                       int32_t* __restrict__ rem, int32_t* __restrict__ level, int32_t next_level,
                                       int32_t* __restrict__ out_order, unsigned long long* __restrict__ tail) {
-  for (int64_t j = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; j < total; j += int64_t(gridDim.x) * blockDim.x) {
-    const int64_t k = upper_bound_i64(foff, n, j) - 1;
-    const int32_t r = order[a + k];
-    const int32_t c = cedge_child[cedge_off[r] + (j - foff[k])];
-    if (atomicSub(&rem[c], 1) == 1) {
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  // warp-uniform trips (stride is a multiple of 32): one append per warp
+  for (int64_t j = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; j - lane < total; j += stride) {
+    bool done = false;
+    int32_t c = 0;
+    if (j < total) {
+      const int64_t k = upper_bound_i64(foff, n, j) - 1;
+      const int32_t r = order[a + k];
+      c = cedge_child[cedge_off[r] + (j - foff[k])];
+      done = atomicSub(&rem[c], 1) == 1;
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, done);
+    if (!m) continue;
+    unsigned long long base = 0;
+    if (lane == __ffs(m) - 1) base = atomicAdd(tail, (unsigned long long)__popc(m));
+    base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
+    if (done) {
       level[c] = next_level;
-      out_order[atomicAdd(tail, 1ull)] = c;
+      out_order[base + __popc(m & ((1u << lane) - 1u))] = c;
     }
   }
 }
@@ -230,33 +243,50 @@ __global__ void body_counts_kernel(const int32_t* __restrict__ sym, const int64_
 __device__ __forceinline__ uint64_t owned_part(uint64_t L) { return L >= 2 ? L - 2 : 0; }
 
 // Expansion lengths for one level of non-root rules (children are on deeper,
-// already finished levels).  Warp per rule.  Also adds each rule's owned
-// 3-word windows (the exact count behind Eq. 1's bound) to *owned.
+// already finished levels).  A group of 4 lanes per rule (most rules have a
+// few children).  Also adds each rule's owned 3-word windows (the exact count
+// behind Eq. 1's bound) to *owned, one atomic per block.
+constexpr int kExpGroup = 4;
+
 __global__ void exp_len_kernel(const int32_t* __restrict__ order, int64_t a, int64_t b,
                                const int64_t* __restrict__ cedge_off, const int32_t* __restrict__ cedge_child,
                                const uint32_t* __restrict__ cedge_mult, const int32_t* __restrict__ W,
                                uint64_t* __restrict__ L, unsigned long long* __restrict__ owned) {
+  __shared__ unsigned long long block_owned;
+  if (threadIdx.x == 0) block_owned = 0;
+  __syncthreads();
   const int lane = threadIdx.x & 31;
+  const int grp = lane / kExpGroup, sub = lane % kExpGroup;
+  constexpr int kGroups = 32 / kExpGroup;
   const int64_t warps = (int64_t(gridDim.x) * blockDim.x) >> 5;
-  for (int64_t k = a + ((blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5); k < b; k += warps) {
-    const int32_t r = order[k];
-    if (r == 0) continue;
+  const int64_t w0 = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
+  unsigned long long own = 0;
+  // a warp takes kGroups consecutive rules per trip: warp-uniform trips
+  for (int64_t kb = a + w0 * kGroups; kb < b; kb += warps * kGroups) {
+    const int64_t k = kb + grp;
+    const bool in = k < b;
+    const int32_t r = in ? order[k] : 0;
     uint64_t sum = 0, inner = 0;
-    for (int64_t e = cedge_off[r] + lane; e < cedge_off[r + 1]; e += 32) {
-      const uint64_t lc = L[cedge_child[e]];
-      sum += cedge_mult[e] * lc;
-      inner += cedge_mult[e] * owned_part(lc);
+    if (in && r != 0)
+      for (int64_t e = cedge_off[r] + sub; e < cedge_off[r + 1]; e += kExpGroup) {
+        const uint64_t lc = L[cedge_child[e]];
+        sum += cedge_mult[e] * lc;
+        inner += cedge_mult[e] * owned_part(lc);
+      }
+#pragma unroll
+    for (int o = kExpGroup / 2; o; o >>= 1) {
+      sum += __shfl_xor_sync(0xffffffffu, sum, o, kExpGroup);
+      inner += __shfl_xor_sync(0xffffffffu, inner, o, kExpGroup);
     }
-    for (int o = 16; o; o >>= 1) {
-      sum += __shfl_xor_sync(0xffffffffu, sum, o);
-      inner += __shfl_xor_sync(0xffffffffu, inner, o);
-    }
-    if (lane == 0) {
+    if (in && r != 0 && sub == 0) {
       const uint64_t lr = uint64_t(W[r]) + sum;
       L[r] = lr;
-      atomicAdd(owned, (unsigned long long)(owned_part(lr) - inner));
+      own += owned_part(lr) - inner;
     }
   }
+  if (own) atomicAdd(&block_owned, own);
+  __syncthreads();
+  if (threadIdx.x == 0 && block_owned) atomicAdd(owned, block_owned);
 }
 
 // Root, per file: references S_f, sum of mult * L_c and of mult * (L_c - 2)+
@@ -358,12 +388,7 @@ __global__ void tile_rule_kernel(const int64_t* __restrict__ rule_off, int32_t R
 
 template <class T>
 T* dalloc(gt_grammar* g, size_t n, cudaStream_t s) {
-  void* p = nullptr;
-  (void)s;
-  GT_CUDA(cudaMalloc(&p, n * sizeof(T) + 16));
-  g->owned.push_back(p);
-  g->info.device_bytes += int64_t(n * sizeof(T) + 16);
-  return static_cast<T*>(p);
+  return static_cast<T*>(grammar_alloc(g, n * sizeof(T) + 16, s));
 }
 
 int bits_for(int64_t x) {
@@ -632,7 +657,7 @@ void load_build_dag(gt_grammar* g, cudaStream_t s) {
     for (int32_t lv = d.depth - 1; lv >= 0; --lv) {
       const int64_t a = g->lvl_off[lv], b = g->lvl_off[lv + 1];
       if (b > a) {
-        exp_len_kernel<<<grid_for((b - a) * 32, threads, cap), threads, 0, s>>>(
+        exp_len_kernel<<<grid_for((b - a) * kExpGroup + 32, threads, cap), threads, 0, s>>>(
             d.lvl_order, a, b, d.cedge_off, d.cedge_child, d.cedge_mult, W, L, owned);
         GT_LAUNCH_CHECK();
       }
