@@ -207,10 +207,16 @@ struct TvSlots {
   uint32_t* bits;  // [F * nb * kTvThreads]: bit l of word t = word (bucket base + 32 t + l) occurs
 };
 
-constexpr int kChunk = kFileChunk;  // items per file-pure chunk
-constexpr int kCsThreads = 512;
-constexpr int kCsWarps = kCsThreads / 32;
-constexpr int kCsItems = kChunk / kCsThreads;
+constexpr int kChunk = 4096;  // rule words per chunk of the weighted sort
+constexpr int kCsItems = 8;   // items per thread in the chunk sort
+// root chunks (kFileChunk symbols) are sorted by 1024-thread CTAs, rule-word
+// chunks (kChunk words) by 512-thread CTAs: 8 items per thread either way
+template <bool kWeighted>
+struct ChunkShape {
+  static constexpr int kItemsPerChunk = kWeighted ? kChunk : kFileChunk;
+  static constexpr int kThreads = kItemsPerChunk / kCsItems;
+  static constexpr int kWarps = kThreads / 32;
+};
 constexpr int kMaxNb = 128;
 
 // A stream of (file-ordered) word items cut into chunks that never cross a
@@ -228,13 +234,15 @@ struct Chunks {
 // root words become their 14-bit index (uint16), rule words (index | weight
 // << 16) as uint64.  runs[c * nb + b] = (start, length) of bucket b's entries.
 template <bool kWeighted>
-__global__ void __launch_bounds__(kCsThreads) chunk_sort_kernel(Chunks ch, const int32_t* __restrict__ items,
-                                                                const uint32_t* __restrict__ wts, int nb, int32_t V,
-                                                                void* __restrict__ out, int64_t* __restrict__ run_start,
-                                                                int32_t* __restrict__ run_len) {
+__global__ void __launch_bounds__(ChunkShape<kWeighted>::kThreads) chunk_sort_kernel(
+    Chunks ch, const int32_t* __restrict__ items, const uint32_t* __restrict__ wts, int nb, int32_t V,
+    void* __restrict__ out, int64_t* __restrict__ run_start, int32_t* __restrict__ run_len) {
+  constexpr int kCsThreads = ChunkShape<kWeighted>::kThreads;
+  constexpr int kCsWarps = ChunkShape<kWeighted>::kWarps;
+  constexpr int kItems = ChunkShape<kWeighted>::kItemsPerChunk;
   __shared__ uint32_t wcnt[kCsWarps][kMaxNb + 1];
   __shared__ uint32_t bstart[kMaxNb + 1];
-  __shared__ __align__(16) unsigned char stage_raw[kChunk * (kWeighted ? 8 : 2)];
+  __shared__ __align__(16) unsigned char stage_raw[kItems * (kWeighted ? 8 : 2)];
   const int64_t nch = *ch.count;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nbits = nb > 1 ? 32 - __clz(nb - 1) : 0;  // bits of a bucket index
@@ -757,7 +765,7 @@ void file_hist(gt_grammar* g, cudaStream_t s, FileHist& fh) {
     Chunks rc{d.rch_start, d.rch_len, d.rch_foff, d.rch_count};
     Buf rent(ctx, size_t(d.root_len) * 2 + 16, s), rrs(ctx, size_t(nrc) * nb * 8, s), rrl(ctx, size_t(nrc) * nb * 4, s);
     if (nrc > 0) {
-      chunk_sort_kernel<false><<<unsigned(std::min<int64_t>(nrc, 65535)), kCsThreads, 0, s>>>(
+      chunk_sort_kernel<false><<<unsigned(std::min<int64_t>(nrc, 65535)), ChunkShape<false>::kThreads, 0, s>>>(
           rc, d.sym, nullptr, nb, V, rent.p, rrs.as<int64_t>(), rrl.as<int32_t>());
       GT_LAUNCH_CHECK();
     }
@@ -768,7 +776,7 @@ void file_hist(gt_grammar* g, cudaStream_t s, FileHist& fh) {
                                         xcn.as<int64_t>());
     GT_LAUNCH_CHECK();
     Chunks xc{xcs.as<int64_t>(), xcl.as<int32_t>(), xcf.as<int64_t>(), xcn.as<int64_t>()};
-    chunk_sort_kernel<true><<<unsigned(std::min<int64_t>(nxc, 65535)), kCsThreads, 0, s>>>(
+    chunk_sort_kernel<true><<<unsigned(std::min<int64_t>(nxc, 65535)), ChunkShape<true>::kThreads, 0, s>>>(
         xc, xw.as<int32_t>(), xwt.as<uint32_t>(), nb, V, xent.p, xrs.as<int64_t>(), xrl.as<int32_t>());
     GT_LAUNCH_CHECK();
     Phase ph3(ctx, "tv_hist_kernel", s);

@@ -50,7 +50,7 @@ enum : uint32_t {
 };
 
 constexpr int kTile = 2048;        // symbols per streaming tile (512 threads x int4)
-constexpr int kFileChunk = 4096;   // root symbols per file-pure chunk (per-file analytics)
+constexpr int kFileChunk = 8192;   // root symbols per file-pure chunk (per-file analytics)
 
 // Device-resident grammar and the DAG built from it at load time.  All
 // arrays are library-owned device memory.
