@@ -116,6 +116,30 @@ def algorithmic_bytes(info: dict, tv_entries: int) -> dict:
                                + 2056 * pieces)}
 
 
+def dist_env():
+    """(rank, world size, local rank) of this process under torchrun; one
+    process per GPU, 1 process when run directly."""
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def max_over_ranks(x: float, world: int, device="cuda") -> float:
+    """The largest value of x over all ranks (the job's time is its slowest
+    rank's); x itself when there is one rank."""
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, tokens_per_rank: int, steps: int, seconds: float) -> float:
+    """Whole-job tokens/s: every rank analyses its own copy (weak scaling)."""
+    return world * tokens_per_rank * steps / seconds
+
+
 def run_step(B, gh, bufs, analytics, stream, keep):
     """One pass of the workload's analytics as one batch (one traversal per
     grammar); result handles go to ``keep`` and are released after the timed
@@ -359,9 +383,7 @@ def main():
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    rank, world, local = dist_env()
     wl = WORKLOADS[args.workload]
 
     from paper_2106_06889_gb300.corpus import load_config
@@ -458,13 +480,8 @@ def main():
         for r in keep:
             B.gt_free_result(r)
         keep.clear()
-    ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * N * args.steps / (ms / 1e3)
+    ms = max_over_ranks(ev0.elapsed_time(ev1), world)
+    value = job_throughput(world, N, args.steps, ms / 1e3)
 
     # ---- dominant kernel: live CUDA-event time of its phase ----
     phases = {}
@@ -547,10 +564,10 @@ def main():
                 B.gt_free_result(r)
             keep.clear()
             B.gt_free_grammar(gh2)
-        e2e_s = (time.perf_counter() - t0) / max(e2e_steps, 1)
+        e2e_s = max_over_ranks((time.perf_counter() - t0) / max(e2e_steps, 1), world)
     if e2e_steps:
         d2h += d2h_res[0] // e2e_steps
-        e2e = {"value": world * N / e2e_s, "unit": "tokens/s", "h2d_bytes_per_step": h2d,
+        e2e = {"value": job_throughput(world, N, 1, e2e_s), "unit": "tokens/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h,
                "note": "gt_load_grammar from pinned host arrays + analytics + result copy back, per step"}
 
