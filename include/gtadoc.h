@@ -24,9 +24,10 @@
  *   - Counts are exact unsigned 64-bit integers.
  *   - Errors: a call returns a gt_status; GT_OK is 0.  A human-readable
  *     message for the last failure on a context is available from
- *     gt_last_error.  Failures that only the GPU can detect (a full hash
- *     table, a timed-out wait) are recorded in a device status word and
- *     reported by gt_sync / gt_result_view.
+ *     gt_last_error.  Failures that only the GPU can detect (a full overflow
+ *     list, a row count past its bound, an invalid symbol) are recorded in a
+ *     device status word and reported by gt_sync / gt_result_view.  No call
+ *     waits on the device inside a kernel.
  *   - There is no CPU fallback: if no usable sm_103a device is present,
  *     gt_create fails with GT_ECUDA.
  */
@@ -45,8 +46,8 @@ typedef int gt_status;
 #define GT_EINVAL 1       /* malformed argument or grammar                      */
 #define GT_ENOMEM 2       /* device or pool allocation failed                   */
 #define GT_ECUDA 3        /* a CUDA runtime call failed                         */
-#define GT_ETIMEOUT 4     /* a bounded device-side wait gave up                 */
-#define GT_ETABLE_FULL 5  /* a device hash table ran out of slots               */
+#define GT_ETIMEOUT 4     /* a bounded device-side wait gave up (none in this version) */
+#define GT_ETABLE_FULL 5  /* a device overflow list ran out of room             */
 #define GT_EOVERFLOW 6    /* a size exceeds what the encoding supports          */
 #define GT_EBUSY 7        /* admission refused: not enough free memory / slots  */
 #define GT_ENOTFOUND 8    /* unknown result field or ticket                     */
@@ -110,8 +111,12 @@ gt_status gt_sync(gt_ctx* ctx, void* stream);
  * lists with multiplicities (the subRules of Algorithm 1), the parent lists
  * (genRuleParentsKernel, Algorithm 2), per-file root edges, the DAG levels
  * that order top-down and bottom-up passes, per-rule word/rule counts and
- * expansion lengths.  Synchronises `stream` before returning (it validates
- * the grammar on the device).  GT_EINVAL for a malformed or cyclic grammar. */
+ * expansion lengths; for at most 64 files also the top-down per-file layout
+ * (each rule's set of files and its (rule, file) slots in file-major order),
+ * which depends only on the DAG.  Host arrays are read in place and uploaded
+ * directly (pinned memory gives asynchronous DMA).  Synchronises `stream`
+ * before returning (it validates the grammar on the device).  GT_EINVAL for a
+ * malformed or cyclic grammar. */
 gt_status gt_load_grammar(gt_ctx* ctx, const gt_grammar_desc* desc, void* stream, gt_grammar** out);
 gt_status gt_free_grammar(gt_grammar* g);
 gt_status gt_grammar_info_get(const gt_grammar* g, gt_grammar_info* info);
@@ -195,9 +200,12 @@ gt_status gt_head_tail(gt_grammar* g, int32_t* d_head, int32_t* d_tail, void* st
  * Several analytics over one or more grammars in one call.  Queries on the
  * same grammar share one traversal: word count and sort share the rule
  * weights and the counts; term vectors and the inverted index share the
- * per-file weights and (file, word) histograms.  out[i] receives query i's
- * result (NULL for a word count, which writes into its d_counts).  On failure
- * no result is returned.  (Not in the paper: it serves one query at a time.) */
+ * per-file weights and (file, word) histograms, and a word count of a grammar
+ * that also has such queries is summed from the per-file counts (top-down).
+ * The word counts of different grammars run as one fused launch sequence (as
+ * gt_word_count_batch).  out[i] receives query i's result (NULL for a word
+ * count, which writes into its d_counts).  On failure no result is returned.
+ * (Not in the paper: it serves one query at a time.) */
 typedef enum {
   GT_Q_WORD_COUNT = 0,     /* d_counts: device uint64[num_words]                */
   GT_Q_SORT = 1,           /* param: order (0 or 1)                             */
@@ -254,7 +262,9 @@ gt_status gt_free_result(gt_result* r);
 
 /* ---- profiling (not in the paper; the paper reports phase times only) ----
  * When enabled, the library records CUDA events on the caller's stream around
- * each phase it runs ("weights", "wc_partition", "wc_hist", "sort_canon", ...).
+ * each phase it runs ("weights", "wc_partition", "wc_hist", "file_weights",
+ * "tv_hist", "tv_hist_kernel", "tv_out", "ii_out", "wc_from_files",
+ * "seq_emit", "seq_sort", "seq_reduce", "bu_local", "bu_rows", "ranked", ...).
  * gt_profile_read waits for those events and returns, for one phase, the
  * summed device time in ms, the number of timed spans, and the number of
  * kernels launched inside them.  gt_kernel_launches returns how many kernels
