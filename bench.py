@@ -98,6 +98,7 @@ class ClockSampler:
 # DRAM bytes (read + write) per launch from one `ncu --set full` capture of the
 # kernel as it stands (see the named profile); None once the kernel changes.
 NCU_TRAFFIC = {
+    "tv_hist_kernel": (193.00e6, "profiles/tv_hist_kernel_multi64_50m.md"),
     "wc_partition_kernel": (221.78e6, "profiles/wc_partition_kernel_multi64_50m.md"),
 }
 
