@@ -444,5 +444,9 @@ size_t radix_scratch_bytes(int64_t n, bool with_values, int value_bytes);
 // keys_out / vals_out.  keys_in / vals_in are clobbered.
 void radix_sort_u64(uint64_t* keys_in, uint64_t* keys_out, void* vals_in, void* vals_out, int value_bytes,
                     int64_t n, int begin_bit, int end_bit, void* scratch, cudaStream_t s);
+// The same on bits [begin_a, end_a) then [begin_b, end_b) (keys whose other
+// bits are all equal, e.g. hi << 32 | lo with narrow hi and lo).
+void radix_sort_u64_split(uint64_t* keys_in, uint64_t* keys_out, void* vals_in, void* vals_out, int value_bytes,
+                          int64_t n, int begin_a, int end_a, int begin_b, int end_b, void* scratch, cudaStream_t s);
 
 }  // namespace gt

@@ -61,43 +61,77 @@ __global__ void validate_kernel(const int32_t* __restrict__ sym, int64_t G, int3
   }
 }
 
-// For every rule reference: key (parent << 32 | child); root references also
-// give (file << 32 | child).  Slots come from warp-aggregated counters.
-__global__ void edge_keys_kernel(const int32_t* __restrict__ sym, int64_t G, int32_t V,
-                                 const int64_t* __restrict__ rule_off, int32_t R,
-                                 const int64_t* __restrict__ file_off, int32_t F, int64_t root_len,
-                                 uint64_t* gkeys, unsigned long long* gcount, uint64_t* rkeys,
-                                 unsigned long long* rcount) {
-  const int lane = threadIdx.x & 31;
-  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-  const int64_t start = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-  // the loop runs while the warp's first index is in range, so every lane of a
-  // warp makes the same trips (stride is a multiple of 32)
-  for (int64_t i = start; (i - lane) < G; i += stride) {
-    const bool in = i < G;
-    const int32_t s = in ? sym[i] : 0;
-    const bool ref = in && s >= V;
-    const unsigned m = __ballot_sync(0xffffffffu, ref);
-    if (!m) continue;
-    unsigned long long base = 0;
-    if (lane == __ffs(m) - 1) base = atomicAdd(gcount, (unsigned long long)__popc(m));
-    base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
-    const bool rootref = ref && i < root_len;
-    const unsigned mr = __ballot_sync(0xffffffffu, rootref);
-    unsigned long long rbase = 0;
-    if (mr) {
-      if (lane == __ffs(mr) - 1) rbase = atomicAdd(rcount, (unsigned long long)__popc(mr));
-      rbase = __shfl_sync(0xffffffffu, rbase, __ffs(mr) - 1);
+// For every rule reference in a rule body: key (parent << 32 | child), the
+// parent read from sym_rule; for every reference in the root: (file << 32 |
+// child).  A block takes tiles of kEkTile symbols (kEkItems per thread,
+// coalesced) and claims the tile's output slots with one atomic per key array,
+// so the shared counters see G / kEkTile atomics in all.
+constexpr int kEkThreads = 256;
+constexpr int kEkItems = 16;
+constexpr int64_t kEkTile = int64_t(kEkThreads) * kEkItems;
+
+__global__ void __launch_bounds__(kEkThreads) edge_keys_kernel(
+    const int32_t* __restrict__ sym, int64_t G, int32_t V, const int32_t* __restrict__ sym_rule, int64_t sr_base,
+    const int64_t* __restrict__ file_off, int32_t F, int64_t root_len, uint64_t* __restrict__ gkeys,
+    unsigned long long* gcount, uint64_t* __restrict__ rkeys, unsigned long long* rcount) {
+  constexpr int kWarps = kEkThreads / 32;
+  __shared__ unsigned s_cnt[2][kWarps];
+  __shared__ unsigned long long s_base[2];
+  __shared__ int32_t s_file[2];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  for (int64_t t0 = blockIdx.x * kEkTile; t0 < G; t0 += int64_t(gridDim.x) * kEkTile) {
+    int32_t sv[kEkItems];
+    unsigned ref_bits = 0, root_bits = 0, wc = 0, wr = 0;
+#pragma unroll
+    for (int k = 0; k < kEkItems; ++k) {
+      const int64_t i = t0 + k * kEkThreads + threadIdx.x;
+      sv[k] = i < G ? sym[i] : 0;
+      const bool rr = i < G && sv[k] >= V && i < root_len;
+      const bool ref = i < G && sv[k] >= V && i >= root_len;
+      ref_bits |= unsigned(ref) << k;
+      root_bits |= unsigned(rr) << k;
+      wc += __popc(__ballot_sync(0xffffffffu, ref));
+      wr += __popc(__ballot_sync(0xffffffffu, rr));
     }
-    if (ref) {
-      const uint32_t child = uint32_t(s - V);
-      const int64_t parent = i < root_len ? 0 : upper_bound_i64(rule_off, int64_t(R) + 1, i) - 1;
-      gkeys[base + __popc(m & ((1u << lane) - 1u))] = (uint64_t(parent) << 32) | child;
-      if (rootref) {
-        const int64_t f = upper_bound_i64(file_off, int64_t(F) + 1, i) - 1;
-        rkeys[rbase + __popc(mr & ((1u << lane) - 1u))] = (uint64_t(f) << 32) | child;
+    if (lane == 0) {
+      s_cnt[0][warp] = wc;
+      s_cnt[1][warp] = wr;
+    }
+    __syncthreads();
+    if (threadIdx.x < 2) {
+      unsigned tot = 0;
+      for (int w = 0; w < kWarps; ++w) tot += s_cnt[threadIdx.x][w];
+      s_base[threadIdx.x] = tot ? atomicAdd(threadIdx.x ? rcount : gcount, (unsigned long long)tot) : 0ull;
+      // the files holding the tile's first and last root symbols
+      if (t0 < root_len) {
+        const int64_t last = t0 + kEkTile - 1 < root_len ? t0 + kEkTile - 1 : root_len - 1;
+        s_file[threadIdx.x] = int32_t(upper_bound_i64(file_off, int64_t(F) + 1, threadIdx.x ? last : t0) - 1);
       }
     }
+    __syncthreads();
+    unsigned long long gb = s_base[0], rb = s_base[1];
+    const int32_t f_lo = s_file[0], f_hi = s_file[1];
+    for (int w = 0; w < warp; ++w) {
+      gb += s_cnt[0][w];
+      rb += s_cnt[1][w];
+    }
+#pragma unroll
+    for (int k = 0; k < kEkItems; ++k) {
+      const int64_t i = t0 + k * kEkThreads + threadIdx.x;
+      const bool ref = (ref_bits >> k) & 1u, rr = (root_bits >> k) & 1u;
+      const unsigned m = __ballot_sync(0xffffffffu, ref), mr = __ballot_sync(0xffffffffu, rr);
+      const uint32_t child = uint32_t(sv[k] - V);
+      if (ref) gkeys[gb + __popc(m & lt)] = (uint64_t(uint32_t(sym_rule[i - sr_base])) << 32) | child;
+      if (rr) {
+        const int64_t f =
+            f_lo == f_hi ? f_lo : f_lo + upper_bound_i64(file_off + f_lo, int64_t(f_hi - f_lo) + 2, i) - 1;
+        rkeys[rb + __popc(mr & lt)] = (uint64_t(f) << 32) | child;
+      }
+      gb += __popc(m);
+      rb += __popc(mr);
+    }
+    __syncthreads();  // s_cnt and s_base are rewritten by the next tile
   }
 }
 
@@ -130,6 +164,50 @@ __global__ void run_split_kernel(const uint64_t* __restrict__ uk, const int64_t*
 __global__ void csr_offsets_kernel(const uint64_t* __restrict__ keys, int64_t n, int64_t nh, int64_t* __restrict__ off) {
   for (int64_t h = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; h <= nh; h += int64_t(gridDim.x) * blockDim.x)
     off[h] = h == nh ? n : lower_bound_u32key(keys, n, uint32_t(h));
+}
+
+// Root multiplicity of every child: the sum over files of its per-file
+// multiplicity.  The (child << 32 | file) keys are sorted by child, so a warp
+// adds up each run it holds (segmented shuffle scan) and issues one atomic per
+// run piece.
+__global__ void root_mult_kernel(const uint64_t* __restrict__ tks, const uint32_t* __restrict__ fm, int64_t n,
+                                 unsigned* __restrict__ rm) {
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i - lane < n; i += stride) {
+    const bool in = i < n;
+    const uint32_t c = in ? uint32_t(tks[i] >> 32) : 0xffffffffu;
+    unsigned v = in ? fm[i] : 0u;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned tv = __shfl_up_sync(0xffffffffu, v, o);
+      const uint32_t tc = __shfl_up_sync(0xffffffffu, c, o);
+      if (lane >= o && tc == c) v += tv;
+    }
+    const uint32_t nc = __shfl_down_sync(0xffffffffu, c, 1);
+    if (in && (lane == 31 || nc != c)) atomicAdd(&rm[c], v);
+  }
+}
+
+__global__ void nonzero_flags_kernel(const unsigned* __restrict__ rm, int32_t R, int64_t* __restrict__ flag) {
+  for (int64_t c = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; c < R; c += int64_t(gridDim.x) * blockDim.x)
+    flag[c] = rm[c] != 0u ? 1 : 0;
+}
+
+__global__ void root_compact_kernel(const unsigned* __restrict__ rm, int32_t R, const int64_t* __restrict__ flag,
+                                    const int64_t* __restrict__ pos, int32_t* __restrict__ lo,
+                                    uint32_t* __restrict__ mult) {
+  for (int64_t c = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; c < R; c += int64_t(gridDim.x) * blockDim.x)
+    if (flag[c]) {
+      lo[pos[c]] = int32_t(c);
+      mult[pos[c]] = rm[c];
+    }
+}
+
+// Keys (0 << 32 | child) of the root's distinct children.
+__global__ void prefix_keys_kernel(const int32_t* __restrict__ lo, int64_t n, uint64_t* __restrict__ uk) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    uk[i] = uint64_t(uint32_t(lo[i]));
 }
 
 __global__ void transpose_keys_kernel(const uint64_t* __restrict__ uk, int64_t n, uint64_t* __restrict__ tk) {
@@ -190,6 +268,38 @@ __global__ void frontier_edges_kernel(const int32_t* __restrict__ order, int64_t
     if (done) {
       level[c] = next_level;
       out_order[base + __popc(m & ((1u << lane) - 1u))] = c;
+    }
+  }
+}
+
+// One warp per frontier rule (levels after the first, whose frontiers hold
+// many rules with few children each): no per-level count and scan.
+__global__ void frontier_warp_kernel(const int32_t* __restrict__ order, int64_t a, int64_t n,
+                                     const int64_t* __restrict__ cedge_off, const int32_t* __restrict__ cedge_child,
+                                     int32_t* __restrict__ rem, int32_t* __restrict__ level, int32_t next_level,
+                                     int32_t* __restrict__ out_order, unsigned long long* __restrict__ tail) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t k = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5; k < n; k += nwarps) {
+    const int32_t r = order[a + k];
+    const int64_t e1 = cedge_off[r + 1];
+    for (int64_t e0 = cedge_off[r]; e0 < e1; e0 += 32) {
+      const int64_t e = e0 + lane;
+      bool done = false;
+      int32_t c = 0;
+      if (e < e1) {
+        c = cedge_child[e];
+        done = atomicSub(&rem[c], 1) == 1;
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, done);
+      if (!m) continue;
+      unsigned long long base = 0;
+      if (lane == __ffs(m) - 1) base = atomicAdd(tail, (unsigned long long)__popc(m));
+      base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
+      if (done) {
+        level[c] = next_level;
+        out_order[base + __popc(m & ((1u << lane) - 1u))] = c;
+      }
     }
   }
 }
@@ -350,11 +460,35 @@ __global__ void max_u64_kernel(const uint64_t* __restrict__ x, int64_t n, unsign
 }
 
 // Rule of every symbol from the tile holding the end of the root onwards.
-__global__ void sym_rule_kernel(const int64_t* __restrict__ rule_off, int32_t R, int64_t G, int64_t root_len,
-                                int64_t base, int64_t n, int32_t* __restrict__ out) {
-  for (int64_t j = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; j < n; j += int64_t(gridDim.x) * blockDim.x) {
-    const int64_t pos = base + j;
-    out[j] = (pos < root_len || pos >= G) ? 0 : int32_t(upper_bound_i64(rule_off, int64_t(R) + 1, pos) - 1);
+// Rule of every symbol from tile t_first on (root symbols read 0).  Block per
+// tile of kTile symbols: the tile's rules lie between tile_rule[t] and
+// tile_rule[t + 1] (at most kTile + 1 of them: non-root bodies are non-empty),
+// so their offsets fit in shared memory and each symbol searches there.
+__global__ void __launch_bounds__(256) sym_rule_kernel(const int64_t* __restrict__ rule_off,
+                                                       const int32_t* __restrict__ tile_rule, int64_t G,
+                                                       int64_t root_len, int64_t t_first, int64_t ntiles,
+                                                       int32_t* __restrict__ out) {
+  __shared__ int64_t so[kTile + 3];
+  for (int64_t t = t_first + blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int32_t r0 = tile_rule[t], r1 = tile_rule[t + 1];
+    const int nr = r1 - r0 + 2;  // rule_off[r0 .. r1 + 1]
+    __syncthreads();
+    for (int k = threadIdx.x; k < nr; k += blockDim.x) so[k] = rule_off[r0 + k];
+    __syncthreads();
+    for (int j = threadIdx.x; j < kTile; j += blockDim.x) {
+      const int64_t pos = t * kTile + j;
+      int32_t r = 0;
+      if (pos >= root_len && pos < G) {
+        int lo = 0, hi = nr - 1;  // so[lo] <= pos < so[hi]
+        while (hi - lo > 1) {
+          const int mid = (lo + hi) >> 1;
+          if (so[mid] <= pos) lo = mid;
+          else hi = mid;
+        }
+        r = r0 + lo;
+      }
+      out[(t - t_first) * kTile + j] = r;
+    }
   }
 }
 
@@ -399,14 +533,25 @@ int bits_for(int64_t x) {
 
 // Sort keys, deduplicate runs, split into (lo, multiplicity) and build CSR
 // offsets over the high half.  Returns the number of distinct keys.
-int64_t dedup_csr(gt_grammar* g, uint64_t* keys, int64_t n, int hi_bits, int64_t nh, int64_t** off_out,
-                  int32_t** lo_out, uint32_t** mult_out, uint64_t** ukeys_keep, cudaStream_t s) {
+// Sort keys (hi << 32 | lo) with lo < 2^lo_bits and hi < 2^hi_bits on the bits
+// that can be nonzero only.  The result lands in out (in is clobbered).
+void sort_hi_lo(uint64_t* in, uint64_t* out, void* vin, void* vout, int vb, int64_t n, int lo_bits, int hi_bits,
+                void* scratch, cudaStream_t s) {
+  radix_sort_u64_split(in, out, vin, vout, vb, n, 0, std::min(lo_bits, 32), 32, 32 + hi_bits, scratch, s);
+}
+
+// With prefix > 0 the outputs start with `prefix` given entries of high half 0
+// (lo pre_lo, multiplicity pre_mult, lo ascending) and keys must all have a
+// nonzero high half.
+int64_t dedup_csr(gt_grammar* g, uint64_t* keys, int64_t n, int hi_bits, int lo_bits, int64_t nh, int64_t** off_out,
+                  int32_t** lo_out, uint32_t** mult_out, uint64_t** ukeys_keep, cudaStream_t s, int64_t prefix = 0,
+                  const int32_t* pre_lo = nullptr, const uint32_t* pre_mult = nullptr) {
   gt_ctx* ctx = g->ctx;
   const int threads = 256;
   const int cap = ctx->num_sms * 16;
   Buf sorted(ctx, size_t(n) * 8, s);
   Buf rscratch(ctx, radix_scratch_bytes(n, false, 0), s);
-  radix_sort_u64(keys, sorted.as<uint64_t>(), nullptr, nullptr, 0, n, 0, 32 + hi_bits, rscratch.p, s);
+  sort_hi_lo(keys, sorted.as<uint64_t>(), nullptr, nullptr, 0, n, lo_bits, hi_bits, rscratch.p, s);
   Buf flag(ctx, size_t(n) * 8, s), pos(ctx, size_t(n) * 8, s);
   Buf sscratch(ctx, scan_scratch_bytes(n), s);
   int64_t nu = 0;
@@ -420,25 +565,32 @@ int64_t dedup_csr(gt_grammar* g, uint64_t* keys, int64_t n, int hi_bits, int64_t
     GT_CUDA(cudaStreamSynchronize(s));
     nu = last_pos + last_flag;
   }
-  uint64_t* uk = dalloc<uint64_t>(g, size_t(nu), s);
+  uint64_t* uk = dalloc<uint64_t>(g, size_t(prefix + nu), s);
   Buf ustart(ctx, size_t(nu) * 8, s);
-  int32_t* lo = dalloc<int32_t>(g, size_t(nu), s);
-  uint32_t* mult = dalloc<uint32_t>(g, size_t(nu), s);
+  int32_t* lo = dalloc<int32_t>(g, size_t(prefix + nu), s);
+  uint32_t* mult = dalloc<uint32_t>(g, size_t(prefix + nu), s);
   int64_t* off = dalloc<int64_t>(g, size_t(nh) + 1, s);
-  if (n > 0) {
-    run_compact_kernel<<<grid_for(n, threads, cap), threads, 0, s>>>(sorted.as<uint64_t>(), n, flag.as<int64_t>(),
-                                                                     pos.as<int64_t>(), uk, ustart.as<int64_t>());
+  if (prefix > 0) {
+    prefix_keys_kernel<<<grid_for(prefix, threads, cap), threads, 0, s>>>(pre_lo, prefix, uk);
     GT_LAUNCH_CHECK();
-    run_split_kernel<<<grid_for(nu, threads, cap), threads, 0, s>>>(uk, ustart.as<int64_t>(), nu, n, lo, mult);
+    GT_CUDA(cudaMemcpyAsync(lo, pre_lo, size_t(prefix) * 4, cudaMemcpyDeviceToDevice, s));
+    GT_CUDA(cudaMemcpyAsync(mult, pre_mult, size_t(prefix) * 4, cudaMemcpyDeviceToDevice, s));
+  }
+  if (n > 0) {
+    run_compact_kernel<<<grid_for(n, threads, cap), threads, 0, s>>>(
+        sorted.as<uint64_t>(), n, flag.as<int64_t>(), pos.as<int64_t>(), uk + prefix, ustart.as<int64_t>());
+    GT_LAUNCH_CHECK();
+    run_split_kernel<<<grid_for(nu, threads, cap), threads, 0, s>>>(uk + prefix, ustart.as<int64_t>(), nu, n,
+                                                                    lo + prefix, mult + prefix);
     GT_LAUNCH_CHECK();
   }
-  csr_offsets_kernel<<<grid_for(nh + 1, threads, cap), threads, 0, s>>>(uk, nu, nh, off);
+  csr_offsets_kernel<<<grid_for(nh + 1, threads, cap), threads, 0, s>>>(uk, prefix + nu, nh, off);
   GT_LAUNCH_CHECK();
   *off_out = off;
   *lo_out = lo;
   *mult_out = mult;
   if (ukeys_keep) *ukeys_keep = uk;
-  return nu;
+  return prefix + nu;
 }
 
 }  // namespace
@@ -474,13 +626,31 @@ void load_build_dag(gt_grammar* g, cudaStream_t s) {
   if (st & ST_INVALID) fail(GT_EINVAL, "grammar symbol out of range or referencing the root");
   const int64_t nref = int64_t(h[0]), nref_root = int64_t(h[1]);
 
+  // ---- tiles and the rule of every body symbol ----
+  {
+    d.ntiles = (G + kTile - 1) / kTile;
+    int32_t* tr = dalloc<int32_t>(g, size_t(d.ntiles) + 1, s);
+    tile_rule_kernel<<<grid_for(d.ntiles + 1, threads, cap), threads, 0, s>>>(d.rule_off, R, G, d.ntiles, tr);
+    GT_LAUNCH_CHECK();
+    d.tile_rule = tr;
+    d.first_rule_tile = d.root_len / kTile;
+    const int64_t nt = d.ntiles - d.first_rule_tile;
+    int32_t* sr = dalloc<int32_t>(g, size_t(nt > 0 ? nt * kTile : 1), s);
+    if (nt > 0) {
+      sym_rule_kernel<<<unsigned(std::min<int64_t>(nt, int64_t(ctx->num_sms) * 8)), 256, 0, s>>>(
+          d.rule_off, tr, G, d.root_len, d.first_rule_tile, d.ntiles, sr);
+      GT_LAUNCH_CHECK();
+    }
+    d.sym_rule = sr;
+  }
+
   // ---- edge keys ----
-  Buf gkeys(ctx, size_t(nref) * 8, s), rkeys(ctx, size_t(nref_root) * 8, s);
+  Buf gkeys(ctx, size_t(nref - nref_root) * 8, s), rkeys(ctx, size_t(nref_root) * 8, s);
   GT_CUDA(cudaMemsetAsync(ctr, 0, 16, s));
   if (G > 0) {
-    edge_keys_kernel<<<grid_for(G, threads, cap), threads, 0, s>>>(d.sym, G, V, d.rule_off, R, d.file_off, F,
-                                                                   d.root_len, gkeys.as<uint64_t>(), ctr + 0,
-                                                                   rkeys.as<uint64_t>(), ctr + 1);
+    edge_keys_kernel<<<grid_for((G + kEkItems - 1) / kEkItems, kEkThreads, cap), kEkThreads, 0, s>>>(
+        d.sym, G, V, d.sym_rule, d.first_rule_tile * kTile, d.file_off, F, d.root_len, gkeys.as<uint64_t>(), ctr + 0,
+        rkeys.as<uint64_t>(), ctr + 1);
     GT_LAUNCH_CHECK();
   }
   const int rbits = bits_for(R);
@@ -489,20 +659,19 @@ void load_build_dag(gt_grammar* g, cudaStream_t s) {
   int64_t* cedge_off;
   int32_t* cedge_child;
   uint32_t* cedge_mult;
-  d.E = dedup_csr(g, gkeys.as<uint64_t>(), nref, rbits, R, &cedge_off, &cedge_child, &cedge_mult, &ukeys, s);
-  d.cedge_off = cedge_off;
-  d.cedge_child = cedge_child;
-  d.cedge_mult = cedge_mult;
   int64_t* redge_off;
   int32_t* redge_child;
   uint32_t* redge_mult;
   uint64_t* rukeys = nullptr;
-  d.ER = dedup_csr(g, rkeys.as<uint64_t>(), nref_root, bits_for(F), F, &redge_off, &redge_child, &redge_mult,
-                   &rukeys, s);
+  d.ER = dedup_csr(g, rkeys.as<uint64_t>(), nref_root, bits_for(F), rbits, F, &redge_off, &redge_child,
+                   &redge_mult, &rukeys, s);
   d.redge_off = redge_off;
   d.redge_child = redge_child;
   d.redge_mult = redge_mult;
-  // the same root edges child-major: for each child, the files referencing it
+  // the same root edges child-major (for each child, the files referencing
+  // it), and from them the root's distinct children with their multiplicities
+  Buf root_lo(ctx, size_t(R) * 4, s), root_mult(ctx, size_t(R) * 4, s);
+  int64_t e_root = 0;
   {
     const int64_t ER = d.ER;
     Buf tk(ctx, size_t(ER) * 8, s), tks(ctx, size_t(ER) * 8, s), mv(ctx, size_t(ER) * 4, s);
@@ -514,9 +683,27 @@ void load_build_dag(gt_grammar* g, cudaStream_t s) {
       transpose_keys_kernel<<<grid_for(ER, threads, cap), threads, 0, s>>>(rukeys, ER, tk.as<uint64_t>());
       GT_LAUNCH_CHECK();
       GT_CUDA(cudaMemcpyAsync(mv.p, redge_mult, size_t(ER) * 4, cudaMemcpyDeviceToDevice, s));
-      radix_sort_u64(tk.as<uint64_t>(), tks.as<uint64_t>(), mv.p, fm, 4, ER, 0, 32 + rbits, rs.p, s);
+      // rukeys ascend by (file, child): a stable sort on the child alone keeps
+      // the files of each child ascending
+      radix_sort_u64(tk.as<uint64_t>(), tks.as<uint64_t>(), mv.p, fm, 4, ER, 32, 32 + rbits, rs.p, s);
       low32_kernel<<<grid_for(ER, threads, cap), threads, 0, s>>>(tks.as<uint64_t>(), ER, ff);
       GT_LAUNCH_CHECK();
+      Buf rm(ctx, size_t(R) * 4, s), flag(ctx, size_t(R) * 8, s), pos(ctx, size_t(R) * 8, s);
+      Buf sscratch(ctx, scan_scratch_bytes(R), s);
+      GT_CUDA(cudaMemsetAsync(rm.p, 0, size_t(R) * 4, s));
+      root_mult_kernel<<<grid_for(ER, threads, cap), threads, 0, s>>>(tks.as<uint64_t>(), fm, ER, rm.as<unsigned>());
+      GT_LAUNCH_CHECK();
+      nonzero_flags_kernel<<<grid_for(R, threads, cap), threads, 0, s>>>(rm.as<unsigned>(), R, flag.as<int64_t>());
+      GT_LAUNCH_CHECK();
+      exclusive_scan_i64(flag.as<int64_t>(), pos.as<int64_t>(), R, sscratch.p, s);
+      root_compact_kernel<<<grid_for(R, threads, cap), threads, 0, s>>>(
+          rm.as<unsigned>(), R, flag.as<int64_t>(), pos.as<int64_t>(), root_lo.as<int32_t>(), root_mult.as<uint32_t>());
+      GT_LAUNCH_CHECK();
+      int64_t last[2];
+      GT_CUDA(cudaMemcpyAsync(&last[0], pos.as<int64_t>() + R - 1, 8, cudaMemcpyDeviceToHost, s));
+      GT_CUDA(cudaMemcpyAsync(&last[1], flag.as<int64_t>() + R - 1, 8, cudaMemcpyDeviceToHost, s));
+      GT_CUDA(cudaStreamSynchronize(s));
+      e_root = last[0] + last[1];
     }
     csr_offsets_kernel<<<grid_for(int64_t(R) + 1, threads, cap), threads, 0, s>>>(tks.as<uint64_t>(), ER, R, fo);
     GT_LAUNCH_CHECK();
@@ -524,6 +711,13 @@ void load_build_dag(gt_grammar* g, cudaStream_t s) {
     d.rfile_f = ff;
     d.rfile_m = fm;
   }
+  // all distinct edges (parent << 32 | child): the root's first, then the
+  // deduplicated references of the rule bodies
+  d.E = dedup_csr(g, gkeys.as<uint64_t>(), nref - nref_root, rbits, rbits, R, &cedge_off, &cedge_child, &cedge_mult,
+                  &ukeys, s, e_root, root_lo.as<int32_t>(), root_mult.as<uint32_t>());
+  d.cedge_off = cedge_off;
+  d.cedge_child = cedge_child;
+  d.cedge_mult = cedge_mult;
 
   // ---- parent lists: transpose the distinct edges, keep multiplicities ----
   {
@@ -538,7 +732,8 @@ void load_build_dag(gt_grammar* g, cudaStream_t s) {
       transpose_keys_kernel<<<grid_for(E, threads, cap), threads, 0, s>>>(ukeys, E, tk.as<uint64_t>());
       GT_LAUNCH_CHECK();
       GT_CUDA(cudaMemcpyAsync(mv.p, cedge_mult, size_t(E) * 4, cudaMemcpyDeviceToDevice, s));
-      radix_sort_u64(tk.as<uint64_t>(), tks.as<uint64_t>(), mv.p, pm, 4, E, 0, 32 + rbits, rs.p, s);
+      // ukeys ascend by (parent, child): sort stably on the child alone
+      radix_sort_u64(tk.as<uint64_t>(), tks.as<uint64_t>(), mv.p, pm, 4, E, 32, 32 + rbits, rs.p, s);
       low32_kernel<<<grid_for(E, threads, cap), threads, 0, s>>>(tks.as<uint64_t>(), E, pp);
       GT_LAUNCH_CHECK();
       high32_kernel<<<grid_for(E, threads, cap), threads, 0, s>>>(tks.as<uint64_t>(), E, pc);
@@ -571,19 +766,27 @@ void load_build_dag(gt_grammar* g, cudaStream_t s) {
     Buf fcnt(ctx, size_t(R) * 8, s), foff(ctx, size_t(R) * 8, s), fsc(ctx, scan_scratch_bytes(R), s);
     while (b > a) {
       const int64_t n = b - a;
-      frontier_count_kernel<<<grid_for(n, threads, cap), threads, 0, s>>>(korder.as<int32_t>(), a, n, d.cedge_off,
-                                                                          fcnt.as<int64_t>());
-      GT_LAUNCH_CHECK();
-      exclusive_scan_i64(fcnt.as<int64_t>(), foff.as<int64_t>(), n, fsc.p, s);
-      int64_t lastc[2];
-      GT_CUDA(cudaMemcpyAsync(&lastc[0], foff.as<int64_t>() + n - 1, 8, cudaMemcpyDeviceToHost, s));
-      GT_CUDA(cudaMemcpyAsync(&lastc[1], fcnt.as<int64_t>() + n - 1, 8, cudaMemcpyDeviceToHost, s));
-      GT_CUDA(cudaStreamSynchronize(s));
-      const int64_t total = lastc[0] + lastc[1];
-      if (total > 0) {
-        frontier_edges_kernel<<<grid_for(total, threads, cap), threads, 0, s>>>(
-            korder.as<int32_t>(), a, n, foff.as<int64_t>(), total, d.cedge_off, d.cedge_child, rem.as<int32_t>(),
-            level, lv + 1, korder.as<int32_t>(), tail);
+      if (lv == 0) {
+        // the root's level: few rules with very many children, spread edge-wise
+        frontier_count_kernel<<<grid_for(n, threads, cap), threads, 0, s>>>(korder.as<int32_t>(), a, n, d.cedge_off,
+                                                                            fcnt.as<int64_t>());
+        GT_LAUNCH_CHECK();
+        exclusive_scan_i64(fcnt.as<int64_t>(), foff.as<int64_t>(), n, fsc.p, s);
+        int64_t lastc[2];
+        GT_CUDA(cudaMemcpyAsync(&lastc[0], foff.as<int64_t>() + n - 1, 8, cudaMemcpyDeviceToHost, s));
+        GT_CUDA(cudaMemcpyAsync(&lastc[1], fcnt.as<int64_t>() + n - 1, 8, cudaMemcpyDeviceToHost, s));
+        GT_CUDA(cudaStreamSynchronize(s));
+        const int64_t total = lastc[0] + lastc[1];
+        if (total > 0) {
+          frontier_edges_kernel<<<grid_for(total, threads, cap), threads, 0, s>>>(
+              korder.as<int32_t>(), a, n, foff.as<int64_t>(), total, d.cedge_off, d.cedge_child, rem.as<int32_t>(),
+              level, lv + 1, korder.as<int32_t>(), tail);
+          GT_LAUNCH_CHECK();
+        }
+      } else {
+        frontier_warp_kernel<<<grid_for(n * 32, threads, cap), threads, 0, s>>>(
+            korder.as<int32_t>(), a, n, d.cedge_off, d.cedge_child, rem.as<int32_t>(), level, lv + 1,
+            korder.as<int32_t>(), tail);
         GT_LAUNCH_CHECK();
       }
       GT_CUDA(cudaMemcpyAsync(&t, tail, 8, cudaMemcpyDeviceToHost, s));
@@ -599,7 +802,8 @@ void load_build_dag(gt_grammar* g, cudaStream_t s) {
     Buf rs(ctx, radix_scratch_bytes(R, false, 0), s);
     level_keys_kernel<<<grid_for(R, threads, cap), threads, 0, s>>>(level, R, lk.as<uint64_t>());
     GT_LAUNCH_CHECK();
-    radix_sort_u64(lk.as<uint64_t>(), lks.as<uint64_t>(), nullptr, nullptr, 0, R, 0, 32 + bits_for(lv), rs.p, s);
+    // keys are made in rule order: a stable sort on the level alone suffices
+    radix_sort_u64(lk.as<uint64_t>(), lks.as<uint64_t>(), nullptr, nullptr, 0, R, 32, 32 + bits_for(lv), rs.p, s);
     low32_kernel<<<grid_for(R, threads, cap), threads, 0, s>>>(lks.as<uint64_t>(), R, order);
     GT_LAUNCH_CHECK();
     Buf loff(ctx, size_t(lv + 1) * 8, s);
@@ -708,23 +912,6 @@ void load_build_dag(gt_grammar* g, cudaStream_t s) {
     g->max_file_len = int64_t(hb[2]);
   }
 
-  // ---- tiles ----
-  {
-    d.ntiles = (G + kTile - 1) / kTile;
-    int32_t* tr = dalloc<int32_t>(g, size_t(d.ntiles) + 1, s);
-    tile_rule_kernel<<<grid_for(d.ntiles + 1, threads, cap), threads, 0, s>>>(d.rule_off, R, G, d.ntiles, tr);
-    GT_LAUNCH_CHECK();
-    d.tile_rule = tr;
-    d.first_rule_tile = d.root_len / kTile;
-    const int64_t n = (d.ntiles - d.first_rule_tile) * kTile;
-    int32_t* sr = dalloc<int32_t>(g, size_t(n > 0 ? n : 1), s);
-    if (n > 0) {
-      sym_rule_kernel<<<grid_for(n, threads, cap), threads, 0, s>>>(d.rule_off, R, G, d.root_len,
-                                                                    d.first_rule_tile * kTile, n, sr);
-      GT_LAUNCH_CHECK();
-    }
-    d.sym_rule = sr;
-  }
   GT_CUDA(cudaStreamSynchronize(s));
   g->info.num_edges = d.E;
   g->info.num_root_edges = d.ER;

@@ -299,7 +299,22 @@ size_t radix_scratch_bytes(int64_t n, bool, int) {
 
 void radix_sort_u64(uint64_t* keys_in, uint64_t* keys_out, void* vals_in, void* vals_out, int value_bytes,
                     int64_t n, int begin_bit, int end_bit, void* scratch, cudaStream_t s) {
+  radix_sort_u64_split(keys_in, keys_out, vals_in, vals_out, value_bytes, n, begin_bit, end_bit, end_bit, end_bit,
+                       scratch, s);
+}
+
+void radix_sort_u64_split(uint64_t* keys_in, uint64_t* keys_out, void* vals_in, void* vals_out, int value_bytes,
+                          int64_t n, int begin_a, int end_a, int begin_b, int end_b, void* scratch, cudaStream_t s) {
   if (n <= 0) return;
+  // digit passes: [begin_a, end_a) then [begin_b, end_b), 8 bits at a time
+  int pass_shift[16], pass_bits[16], npass = 0;
+  for (int r = 0; r < 2; ++r) {
+    const int lo = r ? begin_b : begin_a, hi = r ? end_b : end_a;
+    for (int shift = lo; shift < hi && npass < 16; shift += 8) {
+      pass_shift[npass] = shift;
+      pass_bits[npass++] = hi - shift < 8 ? hi - shift : 8;
+    }
+  }
   const int64_t ntiles = (n + kRsTile - 1) / kRsTile;
   const int64_t nchunks = (ntiles + kRsChunk - 1) / kRsChunk;
   const int64_t m = 256 * ntiles, mc = 256 * nchunks;
@@ -312,9 +327,9 @@ void radix_sort_u64(uint64_t* keys_in, uint64_t* keys_out, void* vals_in, void* 
   uint64_t* kb = keys_out;
   void* va = vals_in;
   void* vb = vals_out;
-  for (int shift = begin_bit; shift < end_bit; shift += 8) {
-    const int bits = end_bit - shift < 8 ? end_bit - shift : 8;
-    const uint32_t mask = (1u << bits) - 1u;
+  for (int p = 0; p < npass; ++p) {
+    const int shift = pass_shift[p];
+    const uint32_t mask = (1u << pass_bits[p]) - 1u;
     radix_upsweep_kernel<<<unsigned(ntiles), kRsThreads, 0, s>>>(ka, n, shift, mask, hist);
     GT_LAUNCH_CHECK();
     radix_chunk_sum_kernel<<<unsigned(nchunks), 256, 0, s>>>(hist, ntiles, nchunks, csum);
