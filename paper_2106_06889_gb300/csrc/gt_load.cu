@@ -4,7 +4,9 @@
 //   * the deduplicated child list of every rule with multiplicities - the
 //     (subRuleId, subRuleFreq) pairs Algorithm 1 iterates;
 //   * the parent list of every rule (genRuleParentsKernel of Algorithm 2);
-//   * the root's child list per file, for per-file analytics;
+//   * the root's child list per file, for per-file analytics (the root's own
+//     child list is their sum over files, so the root's references are sorted
+//     once, by (file, child));
 //   * DAG levels by a frontier (Kahn) traversal: level(c) > level(p) for every
 //     edge p -> c, so processing levels in increasing order is a valid
 //     top-down schedule and in decreasing order a valid bottom-up one.  This
@@ -531,8 +533,6 @@ int bits_for(int64_t x) {
   return b;
 }
 
-// Sort keys, deduplicate runs, split into (lo, multiplicity) and build CSR
-// offsets over the high half.  Returns the number of distinct keys.
 // Sort keys (hi << 32 | lo) with lo < 2^lo_bits and hi < 2^hi_bits on the bits
 // that can be nonzero only.  The result lands in out (in is clobbered).
 void sort_hi_lo(uint64_t* in, uint64_t* out, void* vin, void* vout, int vb, int64_t n, int lo_bits, int hi_bits,
@@ -540,6 +540,8 @@ void sort_hi_lo(uint64_t* in, uint64_t* out, void* vin, void* vout, int vb, int6
   radix_sort_u64_split(in, out, vin, vout, vb, n, 0, std::min(lo_bits, 32), 32, 32 + hi_bits, scratch, s);
 }
 
+// Sort keys, deduplicate runs, split into (lo, multiplicity) and build CSR
+// offsets over the high half.  Returns the number of distinct keys.
 // With prefix > 0 the outputs start with `prefix` given entries of high half 0
 // (lo pre_lo, multiplicity pre_mult, lo ascending) and keys must all have a
 // nonzero high half.
