@@ -100,21 +100,40 @@ class ClockSampler:
 NCU_TRAFFIC = {
     "tv_hist_kernel": (193.00e6, "profiles/tv_hist_kernel_multi64_50m.md"),
     "wc_partition_kernel": (221.78e6, "profiles/wc_partition_kernel_multi64_50m.md"),
+    "chunk_sort_kernel<0>": (157.67e6, "profiles/chunk_sort_kernel_multi64_50m.md"),
 }
 
 
-def algorithmic_bytes(info: dict, tv_entries: int) -> dict:
+ROOT_CHUNK = 8192  # root symbols per file-pure chunk of the per-file analytics
+
+
+def root_layout(g) -> dict:
+    """Root length and number of file-pure root chunks of a host grammar."""
+    lens = np.diff(np.asarray(g.file_off, dtype=np.int64))
+    return {"root_len": int(g.rule_off[1]), "root_chunks": int(((lens + ROOT_CHUNK - 1) // ROOT_CHUNK).sum())}
+
+
+def algorithmic_bytes(info: dict, tv_entries: int, root: dict) -> dict:
     """Bytes each timed kernel must move per launch.
     wc_partition_kernel: the symbol stream, 4 B per body symbol (its bucketed
       output is overhead).
     tv_hist_kernel: its bucket-sorted input, 2 B per root word and 8 B per
       emitted (word, weight) of a (rule, file) pair, plus 8 B per term-vector
-      entry written, plus 2056 B of bits and size per (file, 2^14-word bucket)."""
+      entry written, plus 2056 B of bits and size per (file, 2^14-word bucket).
+    chunk_sort_kernel<0> (root chunks): 4 B per root symbol read, 2 B per root
+      word written, 12 B per (root chunk, bucket) run descriptor.
+    expand_words_kernel: per (rule, file) pair its key, weight, output offset
+      and the rule's two body offsets (36 B), per emitted word 4 B read and
+      8 B (word, weight) written."""
     G, V, F = info["num_syms"], info["num_words"], info["num_files"]
-    pieces = F * ((V + 16383) // 16384)
+    nb = (V + 16383) // 16384
+    pieces = F * nb
     return {"wc_partition": ("wc_partition_kernel", 4 * G),
             "tv_hist_kernel": ("tv_hist_kernel", 2 * info["root_words"] + 8 * info["file_words"] + 8 * tv_entries
-                               + 2056 * pieces)}
+                               + 2056 * pieces),
+            "chunk_sort_root": ("chunk_sort_kernel<0>", 4 * root["root_len"] + 2 * info["root_words"]
+                                + 12 * root["root_chunks"] * nb),
+            "expand_words": ("expand_words_kernel", 36 * info["file_pairs"] + 12 * info["file_words"])}
 
 
 def dist_env():
@@ -486,13 +505,13 @@ def main():
 
     # ---- dominant kernel: live CUDA-event time of its phase ----
     phases = {}
-    for ph in ("weights", "wc_partition", "wc_hist", "sort_canon", "file_weights", "tv_hist", "tv_hist_kernel",
-               "tv_out", "ii_out", "wc_from_files"):
+    for ph in ("weights", "wc_partition", "wc_hist", "sort_canon", "file_weights", "expand_words", "tv_hist",
+               "chunk_sort_root", "chunk_sort_rules", "tv_hist_kernel", "tv_out", "ii_out", "wc_from_files"):
         tot, spans, la = B.gt_profile_read(ctx, ph)
         if spans:
             phases[ph] = {"ms_per_launch": tot / spans, "spans": spans, "launches": la}
     hbm, src = peaks()
-    ab = algorithmic_bytes(info, tv_entries)
+    ab = algorithmic_bytes(info, tv_entries, root_layout(g))
     # the dominant kernel: the measured one with the largest time per step
     cands = [(phases[p]["ms_per_launch"] * phases[p]["launches"] / phases[p]["spans"], p)
              for p in ab if p in phases and phases[p]["launches"] == phases[p]["spans"]]

@@ -263,7 +263,8 @@ gt_status gt_free_result(gt_result* r);
 /* ---- profiling (not in the paper; the paper reports phase times only) ----
  * When enabled, the library records CUDA events on the caller's stream around
  * each phase it runs ("weights", "wc_partition", "wc_hist", "file_weights",
- * "tv_hist", "tv_hist_kernel", "tv_out", "ii_out", "wc_from_files",
+ * "expand_words", "tv_hist", "chunk_sort_root", "chunk_sort_rules",
+ * "tv_hist_kernel", "tv_out", "ii_out", "wc_from_files",
  * "seq_emit", "seq_sort", "seq_reduce", "bu_local", "bu_rows", "ranked", ...).
  * gt_profile_read waits for those events and returns, for one phase, the
  * summed device time in ms, the number of timed spans, and the number of

@@ -743,6 +743,7 @@ void file_hist(gt_grammar* g, cudaStream_t s, FileHist& fh) {
     gather_w_kernel<<<grid_for(EB, threads, cap), threads, 0, s>>>(w.as<uint32_t>(), g->fe_slot, EB,
                                                                     swt.as<uint32_t>());
     GT_LAUNCH_CHECK();
+    Phase ph1(ctx, "expand_words", s);
     expand_words_kernel<<<grid_for(EB, threads, cap), threads, 0, s>>>(g->fe_keys, swt.as<uint32_t>(), EB, pos, d,
                                                                         xw.as<int32_t>(), xwt.as<uint32_t>());
     GT_LAUNCH_CHECK();
@@ -765,6 +766,7 @@ void file_hist(gt_grammar* g, cudaStream_t s, FileHist& fh) {
     Chunks rc{d.rch_start, d.rch_len, d.rch_foff, d.rch_count};
     Buf rent(ctx, size_t(d.root_len) * 2 + 16, s), rrs(ctx, size_t(nrc) * nb * 8, s), rrl(ctx, size_t(nrc) * nb * 4, s);
     if (nrc > 0) {
+      Phase ph4(ctx, "chunk_sort_root", s);
       chunk_sort_kernel<false><<<unsigned(std::min<int64_t>(nrc, 65535)), ChunkShape<false>::kThreads, 0, s>>>(
           rc, d.sym, nullptr, nb, V, rent.p, rrs.as<int64_t>(), rrl.as<int32_t>());
       GT_LAUNCH_CHECK();
@@ -776,9 +778,12 @@ void file_hist(gt_grammar* g, cudaStream_t s, FileHist& fh) {
                                         xcn.as<int64_t>());
     GT_LAUNCH_CHECK();
     Chunks xc{xcs.as<int64_t>(), xcl.as<int32_t>(), xcf.as<int64_t>(), xcn.as<int64_t>()};
-    chunk_sort_kernel<true><<<unsigned(std::min<int64_t>(nxc, 65535)), ChunkShape<true>::kThreads, 0, s>>>(
-        xc, xw.as<int32_t>(), xwt.as<uint32_t>(), nb, V, xent.p, xrs.as<int64_t>(), xrl.as<int32_t>());
-    GT_LAUNCH_CHECK();
+    {
+      Phase ph5(ctx, "chunk_sort_rules", s);
+      chunk_sort_kernel<true><<<unsigned(std::min<int64_t>(nxc, 65535)), ChunkShape<true>::kThreads, 0, s>>>(
+          xc, xw.as<int32_t>(), xwt.as<uint32_t>(), nb, V, xent.p, xrs.as<int64_t>(), xrl.as<int32_t>());
+      GT_LAUNCH_CHECK();
+    }
     Phase ph3(ctx, "tv_hist_kernel", s);
     tv_hist_kernel<<<unsigned(pieces), kTvThreads, 0, s>>>(F, nb, rc, rrs.as<int64_t>(), rrl.as<int32_t>(),
                                                            rent.as<uint16_t>(), xc, xrs.as<int64_t>(),
