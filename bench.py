@@ -100,7 +100,7 @@ class ClockSampler:
 NCU_TRAFFIC = {
     "tv_hist_kernel": (193.00e6, "profiles/tv_hist_kernel_multi64_50m.md"),
     "wc_partition_kernel": (221.78e6, "profiles/wc_partition_kernel_multi64_50m.md"),
-    "chunk_sort_kernel<0>": (157.67e6, "profiles/chunk_sort_kernel_multi64_50m.md"),
+    "chunk_sort_kernel<0, 5>": (156.89e6, "profiles/chunk_sort_kernel_multi64_50m.md"),
 }
 
 
@@ -120,8 +120,9 @@ def algorithmic_bytes(info: dict, tv_entries: int, root: dict) -> dict:
     tv_hist_kernel: its bucket-sorted input, 2 B per root word and 8 B per
       emitted (word, weight) of a (rule, file) pair, plus 8 B per term-vector
       entry written, plus 2056 B of bits and size per (file, 2^14-word bucket).
-    chunk_sort_kernel<0> (root chunks): 4 B per root symbol read, 2 B per root
-      word written, 12 B per (root chunk, bucket) run descriptor.
+    chunk_sort_kernel<0, bits> (root chunks; bits = width of a bucket index):
+      4 B per root symbol read, 2 B per root word written, 12 B per (root
+      chunk, bucket) run descriptor.
     expand_words_kernel: per (rule, file) pair its key, weight, output offset
       and the rule's two body offsets (36 B), per emitted word 4 B read and
       8 B (word, weight) written."""
@@ -131,8 +132,8 @@ def algorithmic_bytes(info: dict, tv_entries: int, root: dict) -> dict:
     return {"wc_partition": ("wc_partition_kernel", 4 * G),
             "tv_hist_kernel": ("tv_hist_kernel", 2 * info["root_words"] + 8 * info["file_words"] + 8 * tv_entries
                                + 2056 * pieces),
-            "chunk_sort_root": ("chunk_sort_kernel<0>", 4 * root["root_len"] + 2 * info["root_words"]
-                                + 12 * root["root_chunks"] * nb),
+            "chunk_sort_root": (f"chunk_sort_kernel<0, {max(nb - 1, 0).bit_length()}>",
+                                4 * root["root_len"] + 2 * info["root_words"] + 12 * root["root_chunks"] * nb),
             "expand_words": ("expand_words_kernel", 36 * info["file_pairs"] + 12 * info["file_words"])}
 
 

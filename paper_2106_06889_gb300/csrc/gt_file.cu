@@ -233,7 +233,7 @@ struct Chunks {
 // to the chunk's own item range (one entry per word, so it always fits):
 // root words become their 14-bit index (uint16), rule words (index | weight
 // << 16) as uint64.  runs[c * nb + b] = (start, length) of bucket b's entries.
-template <bool kWeighted>
+template <bool kWeighted, int kBits>
 __global__ void __launch_bounds__(ChunkShape<kWeighted>::kThreads) chunk_sort_kernel(
     Chunks ch, const int32_t* __restrict__ items, const uint32_t* __restrict__ wts, int nb, int32_t V,
     void* __restrict__ out, int64_t* __restrict__ run_start, int32_t* __restrict__ run_len) {
@@ -245,7 +245,6 @@ __global__ void __launch_bounds__(ChunkShape<kWeighted>::kThreads) chunk_sort_ke
   __shared__ __align__(16) unsigned char stage_raw[kItems * (kWeighted ? 8 : 2)];
   const int64_t nch = *ch.count;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int nbits = nb > 1 ? 32 - __clz(nb - 1) : 0;  // bits of a bucket index
   for (int64_t c = blockIdx.x; c < nch; c += gridDim.x) {
     for (int i = tid; i < kCsWarps * (kMaxNb + 1); i += kCsThreads) (&wcnt[0][0])[i] = 0;
     __syncthreads();
@@ -266,7 +265,8 @@ __global__ void __launch_bounds__(ChunkShape<kWeighted>::kThreads) chunk_sort_ke
       const bool valid = uint32_t(w[j]) < uint32_t(V);
       const uint32_t bk = valid ? uint32_t(w[j]) >> kFBLog2 : 0u;
       unsigned peers = __ballot_sync(0xffffffffu, valid);
-      for (int bit = 0; bit < nbits; ++bit) {
+#pragma unroll
+      for (int bit = 0; bit < kBits; ++bit) {
         const bool on = (bk >> bit) & 1u;
         const unsigned bal = __ballot_sync(0xffffffffu, on);
         peers &= on ? bal : ~bal;
@@ -336,6 +336,34 @@ __global__ void __launch_bounds__(ChunkShape<kWeighted>::kThreads) chunk_sort_ke
     }
     __syncthreads();
   }
+}
+
+// Launch the chunk sort with the bucket index width as a compile-time
+// constant (nb <= kMaxNb = 128 buckets: at most 7 bits), so the ranking's
+// per-bit ballots unroll.
+template <bool kWeighted>
+void launch_chunk_sort(unsigned grid, cudaStream_t s, const Chunks& ch, const int32_t* items, const uint32_t* wts,
+                       int nb, int32_t V, void* out, int64_t* run_start, int32_t* run_len) {
+  const int nbits = nb > 1 ? 32 - __builtin_clz(unsigned(nb - 1)) : 0;
+  constexpr int kT = ChunkShape<kWeighted>::kThreads;
+#define GT_CHUNK_SORT_CASE(B)                                                                       \
+  case B:                                                                                           \
+    chunk_sort_kernel<kWeighted, B><<<grid, kT, 0, s>>>(ch, items, wts, nb, V, out, run_start, run_len); \
+    break;
+  switch (nbits) {
+    GT_CHUNK_SORT_CASE(0)
+    GT_CHUNK_SORT_CASE(1)
+    GT_CHUNK_SORT_CASE(2)
+    GT_CHUNK_SORT_CASE(3)
+    GT_CHUNK_SORT_CASE(4)
+    GT_CHUNK_SORT_CASE(5)
+    GT_CHUNK_SORT_CASE(6)
+    GT_CHUNK_SORT_CASE(7)
+    default:
+      fail(GT_EOVERFLOW, "more than 128 word buckets");
+  }
+#undef GT_CHUNK_SORT_CASE
+  GT_LAUNCH_CHECK();
 }
 
 // Chunk table of the emitted rule words: file f's words [xoff[f], xoff[f+1]).
@@ -767,9 +795,8 @@ void file_hist(gt_grammar* g, cudaStream_t s, FileHist& fh) {
     Buf rent(ctx, size_t(d.root_len) * 2 + 16, s), rrs(ctx, size_t(nrc) * nb * 8, s), rrl(ctx, size_t(nrc) * nb * 4, s);
     if (nrc > 0) {
       Phase ph4(ctx, "chunk_sort_root", s);
-      chunk_sort_kernel<false><<<unsigned(std::min<int64_t>(nrc, 65535)), ChunkShape<false>::kThreads, 0, s>>>(
-          rc, d.sym, nullptr, nb, V, rent.p, rrs.as<int64_t>(), rrl.as<int32_t>());
-      GT_LAUNCH_CHECK();
+      launch_chunk_sort<false>(unsigned(std::min<int64_t>(nrc, 65535)), s, rc, d.sym, nullptr, nb, V, rent.p,
+                               rrs.as<int64_t>(), rrl.as<int32_t>());
     }
     const int64_t nxc = XB / kChunk + F + 1;  // bound on the rule-word chunks
     Buf xcs(ctx, size_t(nxc) * 8, s), xcl(ctx, size_t(nxc) * 4, s), xcf(ctx, size_t(F + 1) * 8, s), xcn(ctx, 8, s);
@@ -780,9 +807,8 @@ void file_hist(gt_grammar* g, cudaStream_t s, FileHist& fh) {
     Chunks xc{xcs.as<int64_t>(), xcl.as<int32_t>(), xcf.as<int64_t>(), xcn.as<int64_t>()};
     {
       Phase ph5(ctx, "chunk_sort_rules", s);
-      chunk_sort_kernel<true><<<unsigned(std::min<int64_t>(nxc, 65535)), ChunkShape<true>::kThreads, 0, s>>>(
-          xc, xw.as<int32_t>(), xwt.as<uint32_t>(), nb, V, xent.p, xrs.as<int64_t>(), xrl.as<int32_t>());
-      GT_LAUNCH_CHECK();
+      launch_chunk_sort<true>(unsigned(std::min<int64_t>(nxc, 65535)), s, xc, xw.as<int32_t>(), xwt.as<uint32_t>(),
+                              nb, V, xent.p, xrs.as<int64_t>(), xrl.as<int32_t>());
     }
     Phase ph3(ctx, "tv_hist_kernel", s);
     tv_hist_kernel<<<unsigned(pieces), kTvThreads, 0, s>>>(F, nb, rc, rrs.as<int64_t>(), rrl.as<int32_t>(),
