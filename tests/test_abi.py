@@ -50,3 +50,60 @@ def test_create_without_gpu_fails_loudly(so):
     h = ctypes.c_void_p()
     rc = lib.gt_create(ctypes.byref(h), 0, ctypes.c_size_t(0))
     assert rc != 0 and not h.value
+
+
+def test_null_arguments_are_rejected_before_any_device_call(so):
+    """Every entry point checks its pointers first and answers GT_EINVAL (1)
+    to a missing context, grammar, server, result or output pointer."""
+    lib = ctypes.CDLL(str(so))
+    P = ctypes.c_void_p
+    null = P()
+    calls = {
+        "gt_create": (null, 0, ctypes.c_size_t(0)),
+        "gt_destroy": (null,),
+        "gt_sync": (null, null),
+        "gt_load_grammar": (null, null, null, null),
+        "gt_free_grammar": (null,),
+        "gt_grammar_info_get": (null, null),
+        "gt_rule_weights": (null, null, null),
+        "gt_word_count": (null, null, null),
+        "gt_word_count_noalloc": (null, null, null),
+        "gt_word_count_batch": (null, null, 1, null),
+        "gt_head_tail": (null, null, null, null),
+        "gt_sort": (null, 0, null, null),
+        "gt_term_vector": (null, 0, null, null),
+        "gt_inverted_index": (null, null, null),
+        "gt_sequence_count": (null, 0, null, null),
+        "gt_ranked_index": (null, 1, null, null),
+        "gt_run_batch": (null, null, 0, null, null),
+        "gt_result_view": (null, null, null, null),
+        "gt_free_result": (null,),
+        "gt_profile_enable": (null, 1),
+        "gt_profile_reset": (null,),
+        "gt_profile_read": (null, null, null, null, null),
+        "gt_set_param": (null, null, ctypes.c_int64(0)),
+        "gt_autotune": (null, ctypes.c_uint32(1), 3, null, null),
+        "gt_server_create": (null, 4, ctypes.c_size_t(0), null),
+        "gt_submit": (null, null, 1, null),
+        "gt_poll": (null, ctypes.c_uint64(0), 0, null, null),
+        "gt_server_stats": (null, null, null, null, null),
+        "gt_server_destroy": (null,),
+    }
+    for name, args in calls.items():
+        f = getattr(lib, name)
+        f.restype = ctypes.c_int
+        assert f(*args) == 1, name
+    lib.gt_last_error.restype = ctypes.c_char_p
+    lib.gt_last_error.argtypes = [P]
+    assert lib.gt_last_error(null) == b"null context"
+    lib.gt_kernel_launches.restype = ctypes.c_int64
+    assert lib.gt_kernel_launches() == 0
+
+
+def test_every_entry_point_is_covered_by_the_null_argument_test():
+    # entry points that take no pointer to check, or return a value, not a status
+    exempt = {"gt_last_error", "gt_kernel_launches"}
+    src = Path(__file__).read_text()
+    block = src[src.index("calls = {"):src.index("for name, args in calls.items()")]
+    covered = set(re.findall(r'"(gt_[a-z_0-9]+)"', block))
+    assert set(declared()) - exempt - covered == set()
