@@ -116,7 +116,9 @@ gt_status gt_sync(gt_ctx* ctx, void* stream);
  * which depends only on the DAG.  Host arrays are read in place and uploaded
  * directly (pinned memory gives asynchronous DMA).  Synchronises `stream`
  * before returning (it validates the grammar on the device).  GT_EINVAL for a
- * malformed or cyclic grammar. */
+ * malformed or cyclic grammar; GT_EOVERFLOW when num_words + num_rules >= 2^31,
+ * the grammar holds 2^40 symbols or more, or one body (the root included)
+ * holds 2^32 or more. */
 gt_status gt_load_grammar(gt_ctx* ctx, const gt_grammar_desc* desc, void* stream, gt_grammar** out);
 gt_status gt_free_grammar(gt_grammar* g);
 gt_status gt_grammar_info_get(const gt_grammar* g, gt_grammar_info* info);

@@ -205,6 +205,8 @@ GT_API gt_status gt_load_grammar(gt_ctx* ctx, const gt_grammar_desc* desc, void*
     for (int32_t r = 0; r < R; ++r) {
       if (roff[r + 1] < roff[r]) fail(GT_EINVAL, "rule_off must be non-decreasing");
       if (r > 0 && roff[r + 1] == roff[r]) fail(GT_EINVAL, "every non-root rule body must be non-empty");
+      // edge multiplicities are 32-bit: a body (the root included) holds fewer than 2^32 symbols
+      if (roff[r + 1] - roff[r] >= (int64_t(1) << 32)) fail(GT_EOVERFLOW, "a rule body of 2^32 symbols or more");
     }
     const int64_t G = roff[R], root_len = roff[1];
     if (G >= (int64_t(1) << 40)) fail(GT_EOVERFLOW, "grammar too large");
