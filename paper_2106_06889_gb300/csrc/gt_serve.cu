@@ -80,7 +80,7 @@ size_t query_footprint(const gt_grammar* g, int kind) {
   switch (kind) {
     case GT_Q_WORD_COUNT:
     case GT_Q_SORT:
-      b = 20 * Gp + 16 * R + 64 * V + 4 * 152 * nb * 16384 * 3;
+      b = 20 * Gp + 16 * R + 64 * V + 4.0 * g->ctx->num_sms * nb * 16384 * 3;
       break;
     case GT_Q_INVERTED_INDEX:
     case GT_Q_TERM_VECTOR:
