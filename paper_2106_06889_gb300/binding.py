@@ -99,7 +99,7 @@ def lib() -> ctypes.CDLL:
         for name, args in sig.items():
             f = getattr(L, name, None)
             if f is None:
-                continue
+                raise RuntimeError(f"{GTADOC_SO} does not export {name}; rebuild it with __graft_entry__.build()")
             f.argtypes = args
             f.restype = ctypes.c_int
         L.gt_kernel_launches.argtypes = []

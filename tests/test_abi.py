@@ -107,3 +107,12 @@ def test_every_entry_point_is_covered_by_the_null_argument_test():
     block = src[src.index("calls = {"):src.index("for name, args in calls.items()")]
     covered = set(re.findall(r'"(gt_[a-z_0-9]+)"', block))
     assert set(declared()) - exempt - covered == set()
+
+
+def test_binding_loads_the_library_and_types_every_entry_point(so):
+    from paper_2106_06889_gb300 import binding
+    L = binding.lib()
+    for name in declared():
+        f = getattr(L, name)
+        if name not in ("gt_last_error", "gt_kernel_launches"):
+            assert f.argtypes is not None and f.restype is ctypes.c_int, name
