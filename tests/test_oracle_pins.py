@@ -196,6 +196,22 @@ def test_oracle_matches_brute_force(name, g, toks, lens):
         pin_source(oracle, g, toks, lens)
 
 
+def test_oracle_matches_brute_force_at_the_largest_vocabulary():
+    """num_words = 2^21, the most a 21-bit field of a 3-word key holds: word
+    IDs at both ends of the range, so a key packing that loses the top bit or
+    mixes fields shows in the sequence count and the ranked index."""
+    V = 1 << 21
+    rng = np.random.default_rng(2021)
+    pool = np.array([0, 1, 2, 1 << 20, V - 3, V - 2, V - 1], np.int32)
+    toks = pool[rng.integers(0, pool.size, size=300)]
+    toks[100:108] = toks[10:18]  # a repeated phrase gives nested rules
+    lens = np.array([120, 0, 180], np.int64)
+    g = sequitur(toks, lens, V)
+    assert g.num_words == V and toks.max() == V - 1
+    pin_brute(oracle, g)
+    pin_source(oracle, g, toks, lens)
+
+
 @pytest.mark.parametrize("name,g,toks,lens", [c for c in CASES if c[0].startswith("seq")][:25],
                          ids=[c[0] for c in CASES if c[0].startswith("seq")][:25])
 def test_eq1_owned_windows(name, g, toks, lens):
