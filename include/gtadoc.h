@@ -76,7 +76,7 @@ typedef struct {
   int32_t on_device;
 } gt_grammar_desc;
 
-/* Facts about a loaded grammar, filled by gt_grammar_info. */
+/* Facts about a loaded grammar, filled by gt_grammar_info_get. */
 typedef struct {
   int64_t num_words, num_rules, num_files;
   int64_t num_syms;        /* G: total body symbols                              */
@@ -99,7 +99,8 @@ typedef struct {
  * absent or is not compute capability 10.3. */
 gt_status gt_create(gt_ctx** ctx, int device, size_t pool_bytes);
 gt_status gt_destroy(gt_ctx* ctx);
-/* Message for the last failure on ctx (never NULL; "" when none). */
+/* Message for the last failure on ctx (never NULL; "" when none, "null
+ * context" when ctx is NULL). */
 const char* gt_last_error(const gt_ctx* ctx);
 /* Wait for `stream`, then return and clear the device status word. */
 gt_status gt_sync(gt_ctx* ctx, void* stream);
