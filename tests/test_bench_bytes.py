@@ -38,3 +38,17 @@ def test_bucket_index_width_matches_the_launch_dispatch():
         info = {"num_syms": 0, "num_words": V, "num_files": 1, "root_words": 0, "file_words": 0, "file_pairs": 0}
         name = bench.algorithmic_bytes(info, 0, {"root_len": 0, "root_chunks": 0})["chunk_sort_root"][0]
         assert name == f"chunk_sort_kernel<0, {bits}>", (V, name)
+
+
+def test_cpu_baseline_runs_the_step_analytics_on_a_file_prefix():
+    from paper_2106_06889_gb300.corpus import sequitur
+    rng = np.random.default_rng(5)
+    lens = np.array([400, 300, 500, 200], np.int64)
+    toks = rng.integers(0, 50, size=int(lens.sum())).astype(np.int32)
+    g = sequitur(toks, lens, 50)
+    rate, nfiles, ntok, dt = bench.oracle_sample(g, ["word_count", "inverted_index", "term_vector"], budget_s=0.0)
+    # a zero budget stops after the first prefix: one file, its tokens counted
+    assert nfiles == 1 and ntok == 400 and dt > 0 and rate == ntok / dt
+    rate, nfiles, ntok, dt = bench.oracle_sample(g, ["sequence_count"], budget_s=1e9)
+    # an unbounded budget grows the prefix to every file
+    assert nfiles == 4 and ntok == int(lens.sum())
