@@ -89,10 +89,6 @@ __global__ void mask_totals_kernel(const unsigned long long* __restrict__ mask, 
   }
 }
 
-__device__ __forceinline__ int64_t slot_of(const int64_t* off, const unsigned long long* mask, int32_t r, int f) {
-  return off[r] + __popcll(mask[r] & ((1ull << f) - 1ull));
-}
-
 // The root's per-file references give the first part of every weight.
 __global__ void fweight_root_kernel(const int64_t* __restrict__ rfile_off, const int32_t* __restrict__ rfile_f,
                                     const uint32_t* __restrict__ rfile_m, int32_t R, const int64_t* __restrict__ off,
@@ -756,7 +752,7 @@ void file_hist(gt_grammar* g, cudaStream_t s, FileHist& fh) {
   gt_ctx* ctx = g->ctx;
   const DevGrammar& d = g->d;
   const int threads = 256, cap = ctx->num_sms * 16;
-  const int32_t R = d.R, F = d.F, V = d.V;
+  const int32_t F = d.F, V = d.V;
   const int64_t EB = g->fentry_bound, XB = g->fword_bound;
   Phase ph(ctx, "file_weights", s);
   FileWeights fwt;
