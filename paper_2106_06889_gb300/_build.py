@@ -76,7 +76,7 @@ def build_gtadoc(force: bool = False, verbose_ptxas: bool = False) -> Path:
     def compile_one(src: Path):
         obj = BUILD / (src.stem + ".o")
         out = _run([nvcc, *ARCH, *NVCC_FLAGS, *extra, "-I", str(INCLUDE), "-I", str(CSRC),
-                    "-dc" if False else "-c", str(src), "-o", str(obj)])
+                    "-c", str(src), "-o", str(obj)])
         return obj, out
 
     with ThreadPoolExecutor(max_workers=min(8, len(srcs) or 1)) as ex:
