@@ -1,10 +1,13 @@
 #!/usr/bin/env python3
 """Benchmark: uncompressed tokens/s analysed on a grammar-compressed corpus.
 
-One step = one pass of the analytics of the workload over the resident
-compressed corpus (weights, traversal, reduction, canonical output), through
-the gt_* C ABI.  Default workload: 64 files, ~50M tokens, Zipf(s=1.0) over
-500k words, 5% repeated passages, one shared Sequitur grammar.
+One step = one pass of the workload's analytics over the resident compressed
+corpus (weights, traversal, reduction, canonical output), through the gt_* C
+ABI.  Default workload (the headline): 64 files, ~50M tokens, Zipf(s=1.0)
+over 500k words, 5% repeated passages, one shared Sequitur grammar; word
+count + inverted index + term vector in one batch.  The 500M-token one-file
+corpus with nested repeats (3-word sequence count + sort) is measured the
+same way and reported under ``extras``.
 
 Prints ONE JSON line (rank 0).  ``--impl reference`` times the CPU oracle on
 the host cores instead (the reference arm).
@@ -29,6 +32,9 @@ WORKLOADS = {
     "multi64_50m": {"analytics": ["word_count", "inverted_index", "term_vector"],
                     "desc": "64 files, log-uniform 10k-2M tokens (~50M), Zipf s=1.0, V=500k, 5% repeated "
                             "passages, one Sequitur grammar"},
+    "nested_500m": {"analytics": ["sequence_count", "sort"],
+                    "desc": "one file of 500M tokens, Zipf s=1.05, V=1M, nested repeats (passages of passages, "
+                            "depth 6) on 50% of the tokens, one Sequitur grammar (16 shards)"},
 }
 METRIC = "uncompressed tokens/s analysed (word count, 3-gram count); p50/p99 query ms"
 
@@ -100,46 +106,55 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-# DRAM bytes (read + write) per launch from one `ncu --set full` capture of the
-# kernel as it stands (see the named profile); None once the kernel changes.
-NCU_TRAFFIC = {
-    "tv_hist_kernel": (193.00e6, "profiles/tv_hist_kernel_multi64_50m.md"),
-    "wc_partition_kernel": (221.78e6, "profiles/wc_partition_kernel_multi64_50m.md"),
-    "chunk_sort_kernel<0, 5>": (156.89e6, "profiles/chunk_sort_kernel_multi64_50m.md"),
-}
+# ---------------------------------------------------------------------------
+# Algorithmic bytes (the bytes the method must move; intermediates excluded)
+# ---------------------------------------------------------------------------
+
+def step_bytes(workload: str, info: dict, out: dict) -> int:
+    """Bytes one step of the workload must move, by the per-unit figures of
+    the hot-path measurement plan:
+      word count:  4 B per body symbol + 8 B per DAG edge + 8 B per rule
+                   weight + 8 B per word count;
+      per file:    + 8 B per (file, rule) weight + 12 B per term-vector pair
+                   + 4 B per inverted-index posting (one traversal serves
+                   the term vector, the inverted index and the word count);
+      3-gram:      4 B per body symbol + 8 B per rule weight + 16 B per rule
+                   of head/tail words + 32 B per owned window (one table
+                   update) + 16 B per distinct 3-gram;
+      sort:        the word count's bytes + 12 B per distinct word."""
+    G, E, R, V = info["num_syms"], info["num_edges"], info["num_rules"], info["num_words"]
+    wc = 4 * G + 8 * E + 8 * R + 8 * V
+    if workload == "multi64_50m":
+        return wc + 8 * info["file_pairs"] + 12 * out["tv_pairs"] + 4 * out["ii_postings"]
+    seq = 4 * G + 8 * R + 16 * R + 32 * info["owned_windows"] + 16 * out["distinct_3grams"]
+    return seq + wc + 12 * out["distinct_words"]
 
 
-ROOT_CHUNK = 8192  # root symbols per file-pure chunk of the per-file analytics
-
-
-def root_layout(g) -> dict:
-    """Root length and number of file-pure root chunks of a host grammar."""
-    lens = np.diff(np.asarray(g.file_off, dtype=np.int64))
-    return {"root_len": int(g.rule_off[1]), "root_chunks": int(((lens + ROOT_CHUNK - 1) // ROOT_CHUNK).sum())}
-
-
-def algorithmic_bytes(info: dict, tv_entries: int, root: dict) -> dict:
-    """Bytes each timed kernel must move per launch.
-    wc_partition_kernel: the symbol stream, 4 B per body symbol (its bucketed
-      output is overhead).
-    tv_hist_kernel: its bucket-sorted input, 2 B per root word and 8 B per
-      emitted (word, weight) of a (rule, file) pair, plus 8 B per term-vector
-      entry written, plus 2056 B of bits and size per (file, 2^14-word bucket).
-    chunk_sort_kernel<0, bits> (root chunks; bits = width of a bucket index):
-      4 B per root symbol read, 2 B per root word written, 12 B per (root
-      chunk, bucket) run descriptor.
-    expand_words_kernel: per (rule, file) pair its key, weight, output offset
-      and the rule's two body offsets (36 B), per emitted word 4 B read and
-      8 B (word, weight) written."""
-    G, V, F = info["num_syms"], info["num_words"], info["num_files"]
+def kernel_bytes(workload: str, info: dict, out: dict) -> dict:
+    """Per timed single-kernel phase: (kernel, bytes of the method's own input
+    or output that kernel moves).  chunk_sort_kernel<0, bits>: the root
+    symbols it reads (4 B each); tv_hist_kernel: the term-vector pairs it
+    writes (12 B each); expand_words_kernel: the rule bodies it reads (4 B per
+    rule symbol); wc_partition_kernel and sg_scatter_kernel: the symbol stream
+    (4 B per body symbol); sg_reduce_kernel: the owned windows it counts (32 B
+    each, one table update) and the distinct 3-grams it writes (16 B each)."""
+    G, V = info["num_syms"], info["num_words"]
+    root_len = out["root_len"]
     nb = (V + 16383) // 16384
-    pieces = F * nb
-    return {"wc_partition": ("wc_partition_kernel", 4 * G),
-            "tv_hist_kernel": ("tv_hist_kernel", 2 * info["root_words"] + 8 * info["file_words"] + 8 * tv_entries
-                               + 2056 * pieces),
-            "chunk_sort_root": (f"chunk_sort_kernel<0, {max(nb - 1, 0).bit_length()}>",
-                                4 * root["root_len"] + 2 * info["root_words"] + 12 * root["root_chunks"] * nb),
-            "expand_words": ("expand_words_kernel", 36 * info["file_pairs"] + 12 * info["file_words"])}
+    if workload == "multi64_50m":
+        return {"chunk_sort_root": (f"chunk_sort_kernel<0, {max(nb - 1, 0).bit_length()}>", 4 * root_len),
+                "tv_hist_kernel": ("tv_hist_kernel", 12 * out["tv_pairs"]),
+                "expand_words": ("expand_words_kernel", 4 * (G - root_len)),
+                "wc_partition": ("wc_partition_kernel", 4 * G)}
+    return {"seq_scatter": ("sg_scatter_kernel", 4 * G),
+            "seq_reduce": ("sg_reduce_kernel", 32 * info["owned_windows"] + 16 * out["distinct_3grams"]),
+            "wc_partition": ("wc_partition_kernel", 4 * G)}
+
+
+PHASES = ("weights", "wc_partition", "wc_hist", "sort_canon", "file_weights", "expand_words", "tv_hist",
+          "chunk_sort_root", "chunk_sort_rules", "tv_hist_kernel", "tv_out", "ii_out", "wc_from_files",
+          "seq_headtail", "seq_part", "seq_scatter", "seq_fine", "seq_reduce")
+LOAD_PHASES = ("load_upload", "load_dag", "load_file_layout")
 
 
 def dist_env():
@@ -166,60 +181,260 @@ def job_throughput(world: int, tokens_per_rank: int, steps: int, seconds: float)
     return world * tokens_per_rank * steps / seconds
 
 
-def run_step(B, gh, bufs, analytics, stream, keep):
-    """One pass of the workload's analytics as one batch (one traversal per
-    grammar); result handles go to ``keep`` and are released after the timed
-    region (freeing waits for the GPU)."""
-    kinds = {"word_count": B.GT_Q_WORD_COUNT, "inverted_index": B.GT_Q_INVERTED_INDEX,
-             "term_vector": B.GT_Q_TERM_VECTOR, "sort": B.GT_Q_SORT}
-    qs = [(gh, kinds[a], 0, bufs["counts"] if a == "word_count" else None) for a in analytics]
-    keep.extend(r for r in B.gt_run_batch(gh.ctx, qs, stream) if r is not None)
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def step_queries(B, gh, analytics, counts):
+    """The workload's analytics as one batch (one traversal per grammar).
+    Sort is by word ID (order 0); the sequence count is global."""
+    kind = {"word_count": B.GT_Q_WORD_COUNT, "sort": B.GT_Q_SORT, "inverted_index": B.GT_Q_INVERTED_INDEX,
+            "term_vector": B.GT_Q_TERM_VECTOR, "sequence_count": B.GT_Q_SEQUENCE_COUNT}
+    return [(gh, kind[a], 0, counts if a == "word_count" else None) for a in analytics]
 
 
-SERVING_TOKENS = (1_000_000, 32_000_000)
+def run_step(B, ctx, qs, stream, keep):
+    """Enqueue one step; result handles go to ``keep`` and are released
+    after the timed region (freeing waits for the GPU)."""
+    keep.extend(r for r in B.gt_run_batch(ctx, qs, stream) if r is not None)
 
 
-def serving_bench(B, ctx, n_corpora=32, n_queries=1000, seed=7):
-    """Continuous-batching server vs the plain one-query-at-a-time path on a set
-    of resident corpora; mix 40% word count / 30% inverted index / 30% 3-gram
-    count, corpus chosen uniformly; Poisson arrivals at 50/80/95% of the
-    measured saturated capacity."""
+def step_outputs(B, analytics, results) -> dict:
+    """Sizes of one step's results (for the algorithmic bytes)."""
+    out = {"tv_pairs": 0, "ii_postings": 0, "distinct_3grams": 0, "distinct_words": 0}
+    it = iter(results)
+    for a in analytics:
+        if a == "word_count":
+            continue
+        r = next(it)
+        if a == "term_vector":
+            out["tv_pairs"] = B.gt_result_view(r, "word")[1]
+        elif a == "inverted_index":
+            out["ii_postings"] = B.gt_result_view(r, "file")[1]
+        elif a == "sequence_count":
+            out["distinct_3grams"] = B.gt_result_view(r, "key")[1]
+        elif a == "sort":
+            out["distinct_words"] = B.gt_result_view(r, "word")[1]
+    return out
+
+
+def load_timed(B, ctx, g, stream, reps=2):
+    """Load the grammar ``reps`` times (the first includes one-time costs),
+    keep the last; its wall time from pinned host arrays and its phases
+    (upload, DAG build, per-file layout)."""
+    import torch
+    pinned = {k: torch.from_numpy(np.ascontiguousarray(getattr(g, k))).pin_memory()
+              for k in ("rule_off", "sym", "file_off")}
+
+    class HostG:
+        num_words = g.num_words
+        rule_off = pinned["rule_off"].numpy()
+        sym = pinned["sym"].numpy()
+        file_off = pinned["file_off"].numpy()
+
+    gh = None
+    for _ in range(reps):
+        if gh is not None:
+            B.gt_free_grammar(gh)
+        B.gt_profile_reset(ctx)
+        B.gt_profile_enable(ctx, True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        gh = B.gt_load_grammar(ctx, HostG, stream)
+        stream.synchronize()
+        ms = 1e3 * (time.perf_counter() - t0)
+        B.gt_profile_enable(ctx, False)
+    ph = {p: B.gt_profile_read(ctx, p)[0] for p in LOAD_PHASES}
+    B.gt_profile_reset(ctx)
+    load = {"ms": ms, "upload_ms": ph["load_upload"], "dag_ms": ph["load_dag"],
+            "file_layout_ms": ph["load_file_layout"],
+            "note": "gt_load_grammar from pinned host arrays (timed separately from the step, as the paper "
+                    "splits initialisation from traversal); file_layout_ms is the top-down per-file layout "
+                    "(<= 64 files) that per-file queries reuse: DAG facts, no counts"}
+    return gh, load, pinned, HostG
+
+
+def measure(B, ctx, workload, g, steps, warmup, world, stream, autotune=True, e2e_steps=3, clocks=True):
+    """Device-timed steps of one workload on a resident grammar, with its
+    step-level and dominant-kernel rooflines, phases, load time and the
+    end-to-end figure through the public API from host buffers."""
+    import torch
+    analytics = WORKLOADS[workload]["analytics"]
+    gh, load, pinned, HostG = load_timed(B, ctx, g, stream)
+    info = B.gt_grammar_info_get(gh)
+    N = info["num_tokens"]
+    counts = torch.empty(g.num_words, dtype=torch.int64, device="cuda")
+    tune = None
+    if autotune:
+        kinds = [k for a, k in (("word_count", B.GT_Q_WORD_COUNT), ("sort", B.GT_Q_SORT),
+                                ("inverted_index", B.GT_Q_INVERTED_INDEX), ("term_vector", B.GT_Q_TERM_VECTOR))
+                 if a in analytics]
+        tune = B.gt_autotune(gh, kinds, reps=3, stream=stream) if kinds else None
+    qs = step_queries(B, gh, analytics, counts)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    keep = []
+    with torch.cuda.stream(stream):
+        for _ in range(max(warmup, 3)):
+            run_step(B, ctx, qs, stream, keep)
+        torch.cuda.synchronize()
+        outs = step_outputs(B, analytics, keep[-(len(keep) // max(warmup, 3)):])
+        for r in keep:
+            B.gt_free_result(r)
+        keep.clear()
+        launches0 = B.gt_kernel_launches()
+        barrier()
+        torch.cuda.synchronize()
+        sampler = ClockSampler(torch.cuda.current_device()) if clocks else None
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(steps):
+            run_step(B, ctx, qs, stream, keep)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        clk = sampler.stop() if sampler else None
+        launches = B.gt_kernel_launches() - launches0
+        for r in keep:
+            B.gt_free_result(r)
+        keep.clear()
+        # phase timers: a separate pass with CUDA events around every phase
+        # (kept out of the timed region; graphs are not replayed while profiling)
+        B.gt_profile_reset(ctx)
+        B.gt_profile_enable(ctx, True)
+        for _ in range(max(3, min(steps, 5))):
+            run_step(B, ctx, qs, stream, keep)
+        torch.cuda.synchronize()
+        B.gt_profile_enable(ctx, False)
+        for r in keep:
+            B.gt_free_result(r)
+        keep.clear()
+    ms = max_over_ranks(ev0.elapsed_time(ev1), world)
+    ms_step = ms / steps
+    phases = {}
+    for ph in PHASES:
+        tot, spans, la = B.gt_profile_read(ctx, ph)
+        if spans:
+            phases[ph] = {"ms_per_launch": tot / spans, "spans": spans, "launches": la}
+    B.gt_profile_reset(ctx)
+    hbm, src = peaks()
+    outs["root_len"] = int(g.rule_off[1])
+    sb = step_bytes(workload, info, outs)
+    kb = kernel_bytes(workload, info, outs)
+    # dominant kernel: the single-kernel phase with the largest time per step
+    cands = [(phases[p]["ms_per_launch"] * phases[p]["launches"] / phases[p]["spans"], p)
+             for p in kb if p in phases and phases[p]["launches"] == phases[p]["spans"]]
+    dom = max(cands)[1] if cands else None
+    kernel = None
+    if dom:
+        kname, kbytes = kb[dom]
+        kms = phases[dom]["ms_per_launch"]
+        kernel = {"kernel": kname, "ms_per_launch": kms, "algorithmic_bytes_per_launch": kbytes,
+                  "achieved": kbytes / (kms / 1e3) / 1e9, "frac": kbytes / (kms / 1e3) / 1e9 / hbm,
+                  "bytes": "the method's own input or output this kernel moves (intermediates excluded)"}
+    achieved = sb / (ms_step / 1e3) / 1e9
+    roofline = {"bound": "hbm", "scope": "whole step (every kernel of the step)", "achieved": achieved,
+                "peak": hbm, "peak_source": src, "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+                "algorithmic_bytes_per_step": sb, "dominant_kernel": kernel}
+
+    # ---- end to end through the public API with host buffers ----
+    e2e = None
+    if e2e_steps:
+        out_host = torch.empty(g.num_words, dtype=torch.int64).pin_memory()
+        h2d = sum(int(v.numel() * v.element_size()) for v in pinned.values())
+        d2h_res = 0
+        with torch.cuda.stream(stream):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(e2e_steps):
+                gh2 = B.gt_load_grammar(ctx, HostG, stream)
+                q2 = step_queries(B, gh2, analytics, counts)
+                res = [r for r in B.gt_run_batch(ctx, q2, stream) if r is not None]
+                if "word_count" in analytics:
+                    out_host.copy_(counts, non_blocking=True)
+                    d2h_res += out_host.numel() * out_host.element_size()
+                for r in res:  # every result field back to host memory
+                    for fld in ("offsets", "word", "key", "count", "file"):
+                        try:
+                            t = B.result_tensor(r, fld)
+                        except B.GtError:
+                            continue
+                        d2h_res += t.numel() * t.element_size()
+                        t.to("cpu", non_blocking=True)
+                stream.synchronize()
+                for r in res:
+                    B.gt_free_result(r)
+                B.gt_free_grammar(gh2)
+            e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, world)
+        e2e = {"value": job_throughput(world, N, 1, e2e_s), "unit": "tokens/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h_res // e2e_steps, "ms_per_step": 1e3 * e2e_s,
+               "note": "gt_load_grammar from pinned host arrays + the step's analytics + every result copied back"}
+    B.gt_free_grammar(gh)
+    return {"value": job_throughput(world, N, steps, ms / 1e3), "ms_per_step": ms_step, "tokens": N,
+            "info": info, "outputs": outs, "roofline": roofline, "phases": phases, "load": load, "e2e": e2e,
+            "gpu_launches": launches, "clocks": clk, "autotune": tune}
+
+
+# ---------------------------------------------------------------------------
+# Serving: continuous batching against the plain path, same arrivals
+# ---------------------------------------------------------------------------
+
+SERVING = {"corpora": 48, "tokens": (1_000_000, 64_000_000), "queries": 10_000, "slots": 8,
+           "mem_budget": 12 << 30}
+
+
+def serving_bench(B, ctx, cfg=SERVING, seed=7):
+    """Resident corpora; mix 40% word count / 30% inverted index / 30% 3-gram
+    count, corpus chosen uniformly.  Plain = one query at a time on one
+    stream, each waited for; served = the continuous-batching server (slots,
+    admission by estimated memory footprint under a budget).  Both see the
+    same Poisson arrivals at 50/80/95% of the server's saturated rate, and
+    each latency is from arrival to completion."""
     import torch
     from paper_2106_06889_gb300.corpus import load_serving_set
-    gs = load_serving_set(n_corpora, SERVING_TOKENS)
+    gs = load_serving_set(cfg["corpora"], cfg["tokens"])
     hs = [B.gt_load_grammar(ctx, g) for g in gs]
-    ntok = [int(g.meta["N"]) for g in gs]
+    ntok = [int(B.gt_grammar_info_get(h)["num_tokens"]) for h in hs]
+    nq = cfg["queries"]
     rng = np.random.default_rng(seed)
-    kinds = rng.choice([B.GT_Q_WORD_COUNT, B.GT_Q_INVERTED_INDEX, B.GT_Q_SEQUENCE_COUNT], size=n_queries,
+    kinds = rng.choice([B.GT_Q_WORD_COUNT, B.GT_Q_INVERTED_INDEX, B.GT_Q_SEQUENCE_COUNT], size=nq,
                        p=[0.4, 0.3, 0.3])
-    which = rng.integers(0, n_corpora, size=n_queries)
+    which = rng.integers(0, len(gs), size=nq)
     bufs = [torch.empty(g.num_words, dtype=torch.int64, device="cuda") for g in gs]
 
     def q(i):
         k = int(kinds[i])
         return [(hs[which[i]], k, 0, bufs[which[i]] if k == B.GT_Q_WORD_COUNT else None)]
 
-    tokens = sum(ntok[which[i]] for i in range(n_queries))
-    # plain: one query at a time, each waited for
+    tokens = sum(ntok[which[i]] for i in range(nq))
     st = torch.cuda.Stream()
-    for i in range(min(20, n_queries)):  # warm-up
-        for r in B.gt_run_batch(ctx, q(i), st):
-            if r is not None:
-                B.gt_free_result(r)
-    st.synchronize()
-    t0 = time.perf_counter()
-    for i in range(n_queries):
-        out = B.gt_run_batch(ctx, q(i), st)
-        st.synchronize()
-        for r in out:
-            if r is not None:
-                B.gt_free_result(r)
-    t_plain = time.perf_counter() - t0
-    sv = B.gt_server_create(ctx, slots=8)
 
-    def run(arrivals):
+    def plain(arrivals):
+        """One query at a time; a query arriving while another runs waits."""
+        lats, t_start = np.zeros(nq), time.perf_counter()
+        for i in range(nq):
+            if arrivals is not None:
+                delay = t_start + arrivals[i] - time.perf_counter()
+                if delay > 0:
+                    time.sleep(delay)
+            out = B.gt_run_batch(ctx, q(i), st)
+            st.synchronize()
+            done = time.perf_counter()
+            lats[i] = 1e3 * (done - (t_start + arrivals[i] if arrivals is not None else done))
+            for r in out:
+                if r is not None:
+                    B.gt_free_result(r)
+        return time.perf_counter() - t_start, lats
+
+    sv = B.gt_server_create(ctx, slots=cfg["slots"], mem_budget=cfg["mem_budget"])
+
+    def served(arrivals):
         tickets, t_start = [], time.perf_counter()
-        for i in range(n_queries):
+        for i in range(nq):
             if arrivals is not None:
                 delay = t_start + arrivals[i] - time.perf_counter()
                 if delay > 0:
@@ -234,16 +449,25 @@ def serving_bench(B, ctx, n_corpora=32, n_queries=1000, seed=7):
                     B.gt_free_result(r)
         return time.perf_counter() - t_start, np.array(lats)
 
-    run(None)  # warm-up
-    t_sat, _ = run(None)
-    cap_qps = n_queries / t_sat
+    for i in range(min(50, nq)):  # warm-up (graphs, pools)
+        for r in B.gt_run_batch(ctx, q(i), st):
+            if r is not None:
+                B.gt_free_result(r)
+    st.synchronize()
+    t_plain, _ = plain(None)
+    served(None)  # warm-up
+    t_sat, _ = served(None)
+    cap_qps = nq / t_sat
     rates = []
     for frac in (0.5, 0.8, 0.95):
         lam = frac * cap_qps
-        arr = np.cumsum(rng.exponential(1.0 / lam, size=n_queries))
-        t, lats = run(arr)
-        rates.append({"load": frac, "offered_qps": lam, "achieved_qps": n_queries / t,
-                      "p50_ms": float(np.percentile(lats, 50)), "p99_ms": float(np.percentile(lats, 99))})
+        arr = np.cumsum(rng.exponential(1.0 / lam, size=nq))
+        row = {"load": frac, "offered_qps": lam}
+        for name, fn in (("served", served), ("plain", plain)):
+            t, lats = fn(arr)
+            row[name] = {"achieved_qps": nq / t, "p50_ms": float(np.percentile(lats, 50)),
+                         "p99_ms": float(np.percentile(lats, 99))}
+        rates.append(row)
     stats = B.gt_server_stats(sv)
     B.gt_server_destroy(sv)
     # word counts of every resident corpus: fused launch sequences (64 grammars
@@ -253,7 +477,7 @@ def serving_bench(B, ctx, n_corpora=32, n_queries=1000, seed=7):
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         for mode in ("per_corpus", "fused", "per_corpus", "fused"):  # second round is timed
             ev0.record(st)
-            for _ in range(20):
+            for _ in range(10):
                 if mode == "fused":
                     B.gt_word_count_batch(hs, bufs, st)
                 else:
@@ -261,86 +485,16 @@ def serving_bench(B, ctx, n_corpora=32, n_queries=1000, seed=7):
                         B.gt_word_count(h, b, st)
             ev1.record(st)
             st.synchronize()
-            fused[mode] = ev0.elapsed_time(ev1) / 20
+            fused[mode] = ev0.elapsed_time(ev1) / 10
     for h in hs:
         B.gt_free_grammar(h)
-    return {"corpora": n_corpora, "corpus_tokens": ntok, "queries": n_queries,
-            "word_count_all_corpora_ms": fused,
+    return {"corpora": len(gs), "corpus_tokens_total": int(sum(ntok)), "tokens_range": list(cfg["tokens"]),
+            "queries_per_rate": nq, "slots": cfg["slots"], "mem_budget_bytes": cfg["mem_budget"],
             "mix": "40% word count / 30% inverted index / 30% 3-gram count, corpus uniform",
-            "plain": {"qps": n_queries / t_plain, "tokens_per_s": tokens / t_plain},
-            "served_saturated": {"qps": cap_qps, "tokens_per_s": tokens / t_sat, "slots": 8,
-                                 "max_inflight": stats["max_inflight"]},
-            "poisson": rates}
-
-
-def word_count_alone(B, ctx, gh, out, stream, info, hbm, reps=20):
-    """The word count of the benchmark corpus on its own (one grammar, one
-    traversal: weights, partition, histogram, reduce), replayed from its CUDA
-    graph; then a profiled pass for the partition kernel's roofline (4 B per
-    body symbol, the symbol stream it must read)."""
-    import torch
-    with torch.cuda.stream(stream):
-        for _ in range(3):
-            B.gt_word_count(gh, out, stream)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        for _ in range(reps):
-            B.gt_word_count(gh, out, stream)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / reps
-        B.gt_profile_reset(ctx)
-        B.gt_profile_enable(ctx, True)
-        for _ in range(5):
-            B.gt_word_count(gh, out, stream)
-        torch.cuda.synchronize()
-        B.gt_profile_enable(ctx, False)
-    tot, spans, _ = B.gt_profile_read(ctx, "wc_partition")
-    part_ms = tot / max(spans, 1)
-    ach = 4 * info["num_syms"] / (part_ms / 1e3) / 1e9
-    return {"ms_per_query": ms, "tokens_per_s": info["num_tokens"] / (ms / 1e3),
-            "partition_kernel": {"ms_per_launch": part_ms, "achieved_gbs": ach, "frac_of_measured_hbm": ach / hbm,
-                                 "algorithmic_bytes_per_launch": 4 * info["num_syms"],
-                                 "traffic": NCU_TRAFFIC.get("wc_partition_kernel", (None, None))[0],
-                                 "traffic_source": NCU_TRAFFIC.get("wc_partition_kernel", (None, None))[1]}}
-
-
-def many_files(B, ctx, reps=3):
-    """100k small files in one grammar (files100k): ranked inverted index over
-    words and over 3-word keys, and term vector + inverted index, all by the
-    bottom-up per-file strategy (the top-down file masks hold 64 files).
-    Device time per query, results freed outside the timed region."""
-    import torch
-    from paper_2106_06889_gb300.corpus import load_config
-    g, _ = load_config("files100k")
-    gh = B.gt_load_grammar(ctx, g)
-    info = B.gt_grammar_info_get(gh)
-    N = info["num_tokens"]
-    st = torch.cuda.Stream()
-    out = {"tokens": N, "files": info["num_files"], "grammar_symbols": info["num_syms"]}
-    cases = {"ranked_index_words": lambda: [B.gt_ranked_index(gh, 1, st)],
-             "ranked_index_3grams": lambda: [B.gt_ranked_index(gh, 3, st)],
-             "term_vector_inverted_index": lambda: B.gt_run_batch(
-                 ctx, [(gh, B.GT_Q_TERM_VECTOR, 0, None), (gh, B.GT_Q_INVERTED_INDEX, 0, None)], st)}
-    with torch.cuda.stream(st):
-        for name, fn in cases.items():
-            for r in fn():  # warm-up
-                B.gt_free_result(r)
-            ts = []
-            for _ in range(reps):
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(st)
-                res = fn()
-                e1.record(st)
-                st.synchronize()
-                ts.append(e0.elapsed_time(e1))
-                for r in res:
-                    B.gt_free_result(r)
-            ms = float(np.median(ts))
-            out[name] = {"ms_per_query": ms, "tokens_per_s": N / (ms / 1e3)}
-    B.gt_free_grammar(gh)
-    return out
+            "saturated": {"plain_qps": nq / t_plain, "plain_tokens_per_s": tokens / t_plain,
+                          "served_qps": cap_qps, "served_tokens_per_s": tokens / t_sat,
+                          "max_inflight": stats["max_inflight"]},
+            "poisson": rates, "word_count_all_corpora_ms": fused}
 
 
 def small_word_count(B, ctx, reps=200):
@@ -373,35 +527,247 @@ def small_word_count(B, ctx, reps=200):
     return res
 
 
+def many_files(B, ctx, reps=3):
+    """100k small files in one grammar: ranked inverted index over words and
+    over 3-word keys, and term vector + inverted index, all by the bottom-up
+    per-file strategy.  Device time per query, results freed outside the
+    timed region."""
+    import torch
+    from paper_2106_06889_gb300.corpus import load_config
+    g, _ = load_config("files100k")
+    gh = B.gt_load_grammar(ctx, g)
+    info = B.gt_grammar_info_get(gh)
+    N = info["num_tokens"]
+    st = torch.cuda.Stream()
+    out = {"tokens": N, "files": info["num_files"], "grammar_symbols": info["num_syms"]}
+    cases = {"ranked_index_words": lambda: [B.gt_ranked_index(gh, 1, st)],
+             "ranked_index_3grams": lambda: [B.gt_ranked_index(gh, 3, st)],
+             "term_vector_inverted_index": lambda: B.gt_run_batch(
+                 ctx, [(gh, B.GT_Q_TERM_VECTOR, 0, None), (gh, B.GT_Q_INVERTED_INDEX, 0, None)], st)}
+    with torch.cuda.stream(st):
+        for name, fn in cases.items():
+            for r in fn():  # warm-up
+                B.gt_free_result(r)
+            ts = []
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                res = fn()
+                e1.record(st)
+                st.synchronize()
+                ts.append(e0.elapsed_time(e1))
+                for r in res:
+                    B.gt_free_result(r)
+            ms = float(np.median(ts))
+            out[name] = {"ms_per_query": ms, "tokens_per_s": N / (ms / 1e3)}
+    B.gt_free_grammar(gh)
+    return out
+
+
+def sequence_paths(B, ctx, g, stream, reps=3):
+    """The global 3-word count by the sample-sort buckets (default) and by the
+    one-row-per-window LSD radix sort it replaced, on the same grammar."""
+    import torch
+    gh = B.gt_load_grammar(ctx, g, stream)
+    out = {}
+    with torch.cuda.stream(stream):
+        for name, path in (("bucketed", 0), ("radix_sort", 1)):
+            B.gt_set_param(ctx, "seq_path", path)
+            B.gt_free_result(B.gt_sequence_count(gh, 0, stream))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            keep = []
+            e0.record(stream)
+            for _ in range(reps):
+                keep.append(B.gt_sequence_count(gh, 0, stream))
+            e1.record(stream)
+            torch.cuda.synchronize()
+            for r in keep:
+                B.gt_free_result(r)
+            out[name + "_ms"] = e0.elapsed_time(e1) / reps
+    B.gt_set_param(ctx, "seq_path", 0)
+    B.gt_free_grammar(gh)
+    return out
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the oracle (test infrastructure) on the host cores
+# ---------------------------------------------------------------------------
+
 ORACLE_CALLS = {  # the oracle's form of each analytic of a step
     "word_count": lambda orc, g: orc.word_count(g),
     "inverted_index": lambda orc, g: orc.inverted_index(g),
     "term_vector": lambda orc, g: orc.term_vector(g, 0),
     "sequence_count": lambda orc, g: orc.sequence_count(g, 0),
+    "sort": lambda orc, g: orc.sort_words(g, 0),
 }
 
 
+def sample_grammar(g, k):
+    """The first k files, or for a one-file corpus its first k root symbols."""
+    from paper_2106_06889_gb300.corpus import prefix_files, root_prefix
+    return prefix_files(g, k) if g.num_files > 1 else root_prefix(g, k)
+
+
 def oracle_sample(g, analytics, budget_s: float = 20.0):
-    """Time the CPU oracle running a step's analytics on a bounded prefix of
-    the files; returns (tokens/s, files, tokens, seconds)."""
+    """Time the CPU oracle, one core, running a step's analytics on a bounded
+    sample of the workload (a prefix of its files, or of its one file's root
+    symbols), grown geometrically until one run takes >= budget/4 seconds.
+    Returns (tokens/s, sample description, tokens, seconds)."""
     import oracle
-    from paper_2106_06889_gb300.corpus import prefix_files
-    nfiles = 1
-    # grow the sample geometrically until one run takes >= ~budget/4
+    many = g.num_files > 1
+    k, limit = (1, g.num_files) if many else (1 << 16, int(g.file_off[1]))
     while True:
-        sub = prefix_files(g, nfiles)
-        out = {}
+        sub = sample_grammar(g, k)
         t0 = time.perf_counter()
         for a in analytics:
-            out[a] = ORACLE_CALLS[a](oracle, sub)
+            ORACLE_CALLS[a](oracle, sub)
         dt = time.perf_counter() - t0
-        wc = out["word_count"] if "word_count" in out else oracle.word_count(sub)  # the sample's size
-        ntok = int(np.asarray(wc).astype(np.int64).sum())
-        best = (ntok / dt if dt > 0 else 0.0, nfiles, ntok, dt)
-        if dt > budget_s / 4 or nfiles >= g.num_files:
+        if dt > budget_s / 4 or k >= limit:
             break
-        nfiles = min(g.num_files, nfiles * 2)
-    return best
+        k = min(limit, k * 2)
+    ntok = int(oracle.word_count(sub).astype(np.int64).sum())
+    what = (f"the first {k} of {g.num_files} files" if many
+            else f"the first {k} of {int(g.file_off[1])} root symbols of its one file")
+    return ntok / dt, what, ntok, dt
+
+
+_POOL_G = None
+
+
+def _pool_init(g):
+    global _POOL_G
+    _POOL_G = g
+
+
+def _pool_ping(_):
+    return os.getpid()
+
+
+def _pool_part(args):
+    """One worker's share of the file-split oracle: its files' analytics."""
+    a, b, analytics = args
+    import oracle
+    from paper_2106_06889_gb300.corpus import file_range
+    sub = file_range(_POOL_G, a, b)
+    files = oracle.expand_files(sub)
+    out = {}
+    if "word_count" in analytics:
+        out["word_count"] = oracle.word_count_text(files, sub.num_words)
+    if "term_vector" in analytics:
+        out["term_vector"] = oracle.term_vector_text(files)
+    if "inverted_index" in analytics:
+        out["inverted_index"] = oracle.inverted_index_text(files, sub.num_words)
+    return a, out
+
+
+def oracle_file_split(g, analytics, workers: int):
+    """The oracle split by file over `workers` processes (the coarse-grained,
+    file-level parallelism of the CPU baseline the paper compares against),
+    partial results merged in the parent.  Every file of the workload; the
+    pool is started (spawn) before the timed region.  Returns (tokens/s,
+    workers used, seconds) or None if the workload has one file."""
+    import multiprocessing as mp
+    F = g.num_files
+    if F < 2 or not set(analytics) <= {"word_count", "term_vector", "inverted_index"}:
+        return None
+    workers = max(1, min(workers, F))
+    size = np.diff(np.asarray(g.file_off, np.int64))
+    ends = np.cumsum(size)
+    cuts = [0] + sorted(set(int(np.searchsorted(ends, ends[-1] * k / workers)) + 1
+                            for k in range(1, workers))) + [F]
+    ranges = [(a, b) for a, b in zip(cuts, cuts[1:]) if b > a]
+    with mp.get_context("spawn").Pool(len(ranges), initializer=_pool_init, initargs=(g,)) as pool:
+        pool.map(_pool_ping, range(len(ranges)))
+        t0 = time.perf_counter()
+        parts = pool.map(_pool_part, [(a, b, analytics) for a, b in ranges])
+        merged = merge_file_split(parts, analytics, g.num_words)
+        dt = time.perf_counter() - t0
+    ntok = int(merged["word_count"].sum()) if "word_count" in merged else int(merged["term_vector"][2].sum())
+    return ntok / dt, len(ranges), dt, ntok
+
+
+def merge_file_split(parts, analytics, V):
+    """Whole-corpus results from per-file-range parts ((first file, results)):
+    word counts summed, term vectors concatenated in file order, inverted
+    index postings regrouped by word with files ascending."""
+    parts = sorted(parts, key=lambda p: p[0])
+    merged = {}
+    if "word_count" in analytics:
+        merged["word_count"] = np.sum([p["word_count"] for _, p in parts], axis=0)
+    if "term_vector" in analytics:
+        offs, ws, cs, base = [np.zeros(1, np.int64)], [], [], 0
+        for _, p in parts:
+            o, w, c = p["term_vector"]
+            offs.append(o[1:] + base)
+            base += int(o[-1])
+            ws.append(w)
+            cs.append(c)
+        merged["term_vector"] = (np.concatenate(offs), np.concatenate(ws), np.concatenate(cs))
+    if "inverted_index" in analytics:
+        wl, fl = [], []
+        for a, p in parts:
+            o, f = p["inverted_index"]
+            wl.append(np.repeat(np.arange(V, dtype=np.int64), np.diff(o)))
+            fl.append(f.astype(np.int64) + a)
+        w, f = np.concatenate(wl), np.concatenate(fl)
+        order = np.argsort(w, kind="stable")  # files of each word stay ascending
+        merged["inverted_index"] = (np.concatenate([[0], np.cumsum(np.bincount(w, minlength=V))]),
+                                    f[order].astype(np.int32))
+    return merged
+
+
+def cpu_baselines(g, analytics, budget_s=20.0):
+    rate, what, ntok, dt = oracle_sample(g, analytics, budget_s)
+    nproc = os.cpu_count() or 1
+    cpu = {"value": rate, "unit": "tokens/s", "cores": 1, "kind": "oracle", "nproc": nproc,
+           "sample": f"{' + '.join(analytics)} on {what} ({ntok} tokens), {dt:.1f} s"}
+    par = oracle_file_split(g, analytics, nproc)
+    if par:
+        cpu["file_split"] = {"value": par[0], "unit": "tokens/s", "cores": par[1], "kind": "oracle split by file",
+                             "sample": f"every file ({par[3]} tokens), {par[2]:.1f} s, partial results merged"}
+    else:
+        cpu["file_split"] = {"value": None, "note": "one file: nothing to split by file"}
+    return cpu
+
+
+# ---------------------------------------------------------------------------
+# main
+# ---------------------------------------------------------------------------
+
+def reference_arm(args, rank):
+    """The oracle as it stands, one core, a bounded sample of the workload per
+    step (rank 0 only)."""
+    from paper_2106_06889_gb300.corpus import load_config
+    if rank != 0:
+        return
+    wl = WORKLOADS[args.workload]
+    g, _ = load_config(args.workload)
+    runs = []
+    for i in range(args.warmup + args.steps):
+        r = oracle_sample(g, wl["analytics"], budget_s=4.0)
+        if i >= args.warmup:
+            runs.append(r)
+    v = statistics.median(r[0] for r in runs)
+    s = runs[0]
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "tokens/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * s[3],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic", "config": {"workload": args.workload, "analytics": wl["analytics"],
+                                            "desc": wl["desc"]},
+            "cpu_baseline": {"value": v, "unit": "tokens/s", "cores": 1, "kind": "oracle", "nproc": os.cpu_count(),
+                             "sample": f"{' + '.join(wl['analytics'])} on {s[1]} ({s[2]} tokens) per step"},
+            "e2e": {"value": v, "unit": "tokens/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def workload_summary(m: dict) -> dict:
+    """The figures of one measured workload for the JSON line."""
+    info = m["info"]
+    return {"value": m["value"], "unit": "tokens/s", "ms_per_step": m["ms_per_step"],
+            "roofline": m["roofline"], "phases": m["phases"], "load_ms": m["load"], "e2e": m["e2e"],
+            "gpu_launches": m["gpu_launches"], "outputs": m["outputs"],
+            "grammar": {k: info[k] for k in ("num_tokens", "num_syms", "num_rules", "num_files", "num_edges",
+                                             "depth", "owned_windows", "file_pairs")}}
 
 
 def main():
@@ -412,229 +778,68 @@ def main():
     ap.add_argument("--impl", default="gtadoc", choices=["gtadoc", "reference"])
     ap.add_argument("--workload", default="multi64_50m", choices=list(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (used for profiling runs)")
-    ap.add_argument("--no-extras", action="store_true", help="skip the secondary sequence-count timing")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end legs (used for profiling runs)")
+    ap.add_argument("--no-extras", action="store_true", help="skip every secondary measurement")
+    ap.add_argument("--no-c3", action="store_true", help="skip the 500M-token 3-gram workload in the extras")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving (p50/p99) measurement")
     ap.add_argument("--no-autotune", action="store_true", help="time the default launch configuration")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
-
     rank, world, local = dist_env()
-    wl = WORKLOADS[args.workload]
-
-    from paper_2106_06889_gb300.corpus import load_config
-
     if args.impl == "reference":
-        if rank != 0:
-            return
-        g, _ = load_config(args.workload)
-        t_all = []
-        rate = None
-        for i in range(args.warmup + args.steps):
-            r = oracle_sample(g, wl["analytics"], budget_s=4.0)
-            if i >= args.warmup:
-                t_all.append(r)
-        rates = [r[0] for r in t_all]
-        v = statistics.median(rates)
-        s = t_all[0]
-        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "tokens/s", "n_gpus": args.gpus,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * s[3],
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
-                "data": "synthetic", "config": {"workload": args.workload, "analytics": wl["analytics"],
-                                                "desc": wl["desc"]},
-                "cpu_baseline": {"value": v, "unit": "tokens/s", "cores": 1, "kind": "oracle",
-                                 "sample": f"{' + '.join(wl['analytics'])} on the first {s[1]} of "
-                                           f"{g.num_files} files ({s[2]} tokens) per step"},
-                "e2e": {"value": v, "unit": "tokens/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-        print(json.dumps(line))
+        reference_arm(args, rank)
         return
 
     import torch
     from paper_2106_06889_gb300 import binding as B
+    from paper_2106_06889_gb300.corpus import load_config
 
     torch.cuda.set_device(local)
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    wl = WORKLOADS[args.workload]
     g, _ = load_config(args.workload)  # every rank analyses its own resident copy (weak scaling)
     ctx = B.gt_create(local)
     stream = torch.cuda.Stream()
-    gh = B.gt_load_grammar(ctx, g, stream)
-    info = B.gt_grammar_info_get(gh)
-    N = info["num_tokens"]
-    bufs = {"counts": torch.empty(g.num_words, dtype=torch.int64, device="cuda")}
-    # per-grammar launch configuration, chosen by measurement before timing
-    tune = None
-    if not args.no_autotune:
-        kinds = {"word_count": B.GT_Q_WORD_COUNT, "inverted_index": B.GT_Q_INVERTED_INDEX,
-                 "term_vector": B.GT_Q_TERM_VECTOR}
-        tune = B.gt_autotune(gh, [kinds[a] for a in wl["analytics"]], reps=3, stream=stream)
-
-    def barrier():
-        if world > 1:
-            import torch.distributed as dist
-            dist.barrier()
-
-    # ---- device-timed steps (inputs resident; the 148 MB symbol array exceeds L2) ----
-    keep = []
-    with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
-            run_step(B, gh, bufs, wl["analytics"], stream, keep)
-        torch.cuda.synchronize()
-        for r in keep:
-            B.gt_free_result(r)
-        keep.clear()
-        launches0 = B.gt_kernel_launches()
-        barrier()
-        torch.cuda.synchronize()
-        clocks = ClockSampler(local)
-        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        ev0.record(stream)
-        for _ in range(args.steps):
-            run_step(B, gh, bufs, wl["analytics"], stream, keep)
-        ev1.record(stream)
-        torch.cuda.synchronize()
-        barrier()
-        clk = clocks.stop()
-        launches = B.gt_kernel_launches() - launches0
-        tv_entries = 0
-        for r in keep:
-            try:
-                tv_entries = max(tv_entries, B.gt_result_view(r, "count")[1])
-            except B.GtError:
-                pass
-        for r in keep:
-            B.gt_free_result(r)
-        keep.clear()
-        # phase timers: a separate pass with CUDA events around every phase
-        # (kept out of the timed region; graphs are not replayed while profiling)
-        B.gt_profile_reset(ctx)
-        B.gt_profile_enable(ctx, True)
-        for _ in range(max(3, min(args.steps, 10))):
-            run_step(B, gh, bufs, wl["analytics"], stream, keep)
-        torch.cuda.synchronize()
-        B.gt_profile_enable(ctx, False)
-        for r in keep:
-            B.gt_free_result(r)
-        keep.clear()
-    ms = max_over_ranks(ev0.elapsed_time(ev1), world)
-    value = job_throughput(world, N, args.steps, ms / 1e3)
-
-    # ---- dominant kernel: live CUDA-event time of its phase ----
-    phases = {}
-    for ph in ("weights", "wc_partition", "wc_hist", "sort_canon", "file_weights", "expand_words", "tv_hist",
-               "chunk_sort_root", "chunk_sort_rules", "tv_hist_kernel", "tv_out", "ii_out", "wc_from_files"):
-        tot, spans, la = B.gt_profile_read(ctx, ph)
-        if spans:
-            phases[ph] = {"ms_per_launch": tot / spans, "spans": spans, "launches": la}
-    hbm, src = peaks()
-    ab = algorithmic_bytes(info, tv_entries, root_layout(g))
-    # the dominant kernel: the measured one with the largest time per step
-    cands = [(phases[p]["ms_per_launch"] * phases[p]["launches"] / phases[p]["spans"], p)
-             for p in ab if p in phases and phases[p]["launches"] == phases[p]["spans"]]
-    dom = max(cands)[1]
-    kname, abytes = ab[dom]
-    dom_ms = phases[dom]["ms_per_launch"]
-    achieved = abytes / (dom_ms / 1e3) / 1e9
-    traffic = NCU_TRAFFIC.get(kname)
-    roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm, "peak_source": src,
-                "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic[0] if traffic else None,
-                "traffic_source": traffic[1] if traffic else None, "algorithmic_bytes_per_launch": abytes,
-                "ms_per_launch": dom_ms}
-
-    # ---- secondary: 3-word sequence count on the same corpus ----
+    m = measure(B, ctx, args.workload, g, args.steps, args.warmup, world, stream,
+                autotune=not args.no_autotune, e2e_steps=0 if args.no_e2e else max(2, min(args.steps, 5)))
     extras = {}
-    if not args.no_extras:
-        with torch.cuda.stream(stream):
-            r = B.gt_sequence_count(gh, 0, stream)
-            torch.cuda.synchronize()
-            B.gt_free_result(r)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            n3 = max(2, min(args.steps, 5))
-            e0.record(stream)
-            for _ in range(n3):
-                keep.append(B.gt_sequence_count(gh, 0, stream))
-            e1.record(stream)
-            torch.cuda.synchronize()
-            for r in keep:
-                B.gt_free_result(r)
-            keep.clear()
-        ms3 = e0.elapsed_time(e1) / n3
-        extras["sequence_count"] = {"tokens_per_s": N / (ms3 / 1e3), "ms_per_query": ms3}
-        extras["word_count"] = word_count_alone(B, ctx, gh, bufs["counts"], stream, info, hbm)
+    if not args.no_extras and world == 1:
+        extras["sequence_count_paths"] = {"corpus": args.workload, **sequence_paths(B, ctx, g, stream)}
         extras["small_word_count"] = small_word_count(B, ctx)
         extras["many_files"] = many_files(B, ctx)
-
-    # ---- end to end through the public API with host buffers ----
-    e2e = None
-    pinned = {k: torch.from_numpy(np.ascontiguousarray(getattr(g, k))).pin_memory()
-              for k in ("rule_off", "sym", "file_off")}
-
-    class HostG:
-        num_words = g.num_words
-        rule_off = pinned["rule_off"].numpy()
-        sym = pinned["sym"].numpy()
-        file_off = pinned["file_off"].numpy()
-
-    out_host = torch.empty(g.num_words, dtype=torch.int64).pin_memory()
-    e2e_steps = 0 if args.no_e2e else max(2, min(args.steps, 5))
-    d2h_res = [0]
-    h2d = sum(int(v.numel() * v.element_size()) for v in pinned.values())
-    d2h = int(out_host.numel() * out_host.element_size())
-    with torch.cuda.stream(stream):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(e2e_steps):
-            gh2 = B.gt_load_grammar(ctx, HostG, stream)
-            run_step(B, gh2, bufs, wl["analytics"], stream, keep)
-            out_host.copy_(bufs["counts"], non_blocking=True)
-            for r in keep:  # copy every result field back to host memory
-                for fld in ("offsets", "word", "count", "file"):
-                    try:
-                        t = B.result_tensor(r, fld)
-                    except B.GtError:
-                        continue
-                    d2h_res[0] += t.numel() * t.element_size()
-                    t.to("cpu", non_blocking=True)
-            stream.synchronize()
-            for r in keep:
-                B.gt_free_result(r)
-            keep.clear()
-            B.gt_free_grammar(gh2)
-        e2e_s = max_over_ranks((time.perf_counter() - t0) / max(e2e_steps, 1), world)
-    if e2e_steps:
-        d2h += d2h_res[0] // e2e_steps
-        e2e = {"value": job_throughput(world, N, 1, e2e_s), "unit": "tokens/s", "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h,
-               "note": "gt_load_grammar from pinned host arrays + analytics + result copy back, per step"}
-
-    # ---- serving: continuous batching vs one query at a time, p50/p99 ----
+        other = "nested_500m" if args.workload != "nested_500m" else None
+        if other and not args.no_c3:
+            g3, _ = load_config(other)
+            m3 = measure(B, ctx, other, g3, max(3, min(args.steps, 10)), 3, world, stream, autotune=False,
+                         e2e_steps=0 if args.no_e2e else 2, clocks=False)
+            x = {"workload": other, "desc": WORKLOADS[other]["desc"], "analytics": WORKLOADS[other]["analytics"],
+                 **workload_summary(m3), "sequence_count_paths": sequence_paths(B, ctx, g3, stream)}
+            if not args.no_cpu_baseline:
+                x["cpu_baseline"] = cpu_baselines(g3, WORKLOADS[other]["analytics"])
+            extras[other] = x
+            del g3
     serving = None
-    if rank == 0 and not args.no_serving:
+    if rank == 0 and world == 1 and not args.no_serving and not args.no_extras:
         serving = serving_bench(B, ctx)
-
-    # ---- CPU baseline: the oracle on a bounded sample, rank 0 ----
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, nf, ntok, dt = oracle_sample(g, wl["analytics"])
-        cpu = {"value": rate, "unit": "tokens/s", "cores": 1, "kind": "oracle",
-               "sample": f"{' + '.join(wl['analytics'])} on the first {nf} of {g.num_files} files "
-                         f"({ntok} tokens), {dt:.1f} s"}
-
+        cpu = cpu_baselines(g, wl["analytics"])
     if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": "tokens/s", "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        info = m["info"]
+        line = {"metric": METRIC, "value": m["value"], "unit": "tokens/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": m["ms_per_step"], "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
                 "config": {"workload": args.workload, "analytics": wl["analytics"], "desc": wl["desc"],
-                           "tokens": N, "grammar_symbols": info["num_syms"], "rules": info["num_rules"],
-                           "files": info["num_files"], "l2": "inputs larger than L2 (symbol array "
-                           f"{4 * info['num_syms'] / 1e6:.0f} MB > 129 MB)",
-                           "autotune": tune},
-                "roofline": roofline, "phases": phases, "extras": extras, "serving": serving,
-                "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": launches, "clocks": clk}
+                           "tokens": m["tokens"], "grammar_symbols": info["num_syms"], "rules": info["num_rules"],
+                           "files": info["num_files"],
+                           "l2": f"inputs larger than L2 (symbol array {4 * info['num_syms'] / 1e6:.0f} MB > 129 MB)",
+                           "autotune": m["autotune"]},
+                "roofline": m["roofline"], "load_ms": m["load"], "phases": m["phases"], "outputs": m["outputs"],
+                "extras": extras, "serving": serving, "cpu_baseline": cpu, "e2e": m["e2e"],
+                "gpu_launches": m["gpu_launches"], "clocks": m["clocks"]}
         print(json.dumps(line))
-    B.gt_free_grammar(gh)
     B.gt_destroy(ctx)
     if world > 1:
         import torch.distributed as dist

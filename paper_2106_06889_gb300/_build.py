@@ -13,6 +13,7 @@ from __future__ import annotations
 import os
 import shutil
 import subprocess
+import threading
 from concurrent.futures import ThreadPoolExecutor
 from pathlib import Path
 
@@ -51,12 +52,18 @@ def _run(cmd):
     return r.stdout
 
 
+_corpus_lock = threading.Lock()
+
+
 def build_corpus(force: bool = False) -> Path:
+    """Build the Sequitur library; threads of one process build it once (the
+    lock), processes each write their own temporary file."""
     src = PKG / "corpus" / "sequitur.cpp"
-    if force or _stale(CORPUS_SO, [src]):
-        tmp = CORPUS_SO.with_suffix(f".so.tmp{os.getpid()}")
-        _run(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", str(src), "-o", str(tmp)])
-        os.replace(tmp, CORPUS_SO)
+    with _corpus_lock:
+        if force or _stale(CORPUS_SO, [src]):
+            tmp = CORPUS_SO.with_suffix(f".so.tmp{os.getpid()}_{threading.get_ident()}")
+            _run(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", str(src), "-o", str(tmp)])
+            os.replace(tmp, CORPUS_SO)
     return CORPUS_SO
 
 

@@ -16,6 +16,7 @@ import ctypes
 import hashlib
 import json
 import os
+import threading
 from dataclasses import dataclass, field
 from pathlib import Path
 
@@ -24,7 +25,8 @@ import numpy as np
 from .._build import build_corpus, CORPUS_SO, ROOT
 
 __all__ = ["Grammar", "sequitur", "zipf_tokens", "Corpus", "make_corpus", "CONFIGS", "load_config",
-           "root_only_grammar", "refactor_grammar", "prefix_files", "serving_corpus", "load_serving",
+           "root_only_grammar", "refactor_grammar", "prefix_files", "file_range", "root_prefix",
+           "serving_corpus", "load_serving",
            "load_serving_set"]
 
 
@@ -71,11 +73,14 @@ class Grammar:
 
 
 _lib = None
+_lib_lock = threading.Lock()  # sequitur_sharded's threads may load it at once
 
 
 def _corpus_lib():
     global _lib
-    if _lib is None:
+    with _lib_lock:
+        if _lib is not None:
+            return _lib
         so = build_corpus()
         lib = ctypes.CDLL(str(so))
         lib.gtc_sequitur_build.restype = ctypes.c_void_p
@@ -220,6 +225,26 @@ def zipf_tokens(rng: np.random.Generator, n: int, cdf: np.ndarray, perm: np.ndar
     return perm[rank].astype(np.int32)
 
 
+def zipf_tokens_chunked(seed: int, n: int, cdf: np.ndarray, perm: np.ndarray, chunk: int = 1 << 24,
+                        workers: int | None = None) -> np.ndarray:
+    """n word IDs like ``zipf_tokens``, drawn in chunks of ``chunk`` tokens
+    from independent streams spawned from ``seed`` and filled by threads (the
+    draws release the GIL).  The result depends on seed and n only, not on
+    the number of threads."""
+    from concurrent.futures import ThreadPoolExecutor
+    out = np.empty(n, np.int32)
+    nch = (n + chunk - 1) // chunk
+    seqs = np.random.SeedSequence([int(seed), 0x5A]).spawn(max(nch, 1))
+
+    def fill(c):
+        a, b = c * chunk, min(n, (c + 1) * chunk)
+        out[a:b] = zipf_tokens(np.random.default_rng(seqs[c]), b - a, cdf, perm)
+
+    with ThreadPoolExecutor(max_workers=workers or min(16, os.cpu_count() or 1)) as ex:
+        list(ex.map(fill, range(nch)))
+    return out
+
+
 def inject(rng: np.random.Generator, base: np.ndarray, pieces) -> np.ndarray:
     """Insert each piece into ``base`` at independent uniform positions."""
     if not pieces:
@@ -285,7 +310,7 @@ def make_corpus(name: str, seed: int | None = None, scale: float = 1.0) -> Corpu
         F = max(2, int(round(spec["F"] * scale)))
         lo, hi = spec["len_range"]
         lens = np.round(np.exp(rng.uniform(np.log(lo), np.log(hi), size=F))).astype(np.int64)
-        toks = zipf_tokens(rng, int(lens.sum()), cdf, perm)
+        toks = zipf_tokens_chunked(seed, int(lens.sum()), cdf, perm)
     elif kind == "nested":
         # passages of passages: level 0 phrases of Zipf words, level d items
         # are concatenations of `fanout` level d-1 items; pieces from every
@@ -322,10 +347,12 @@ CONFIGS = {
                            passages=50, passage_len=200, copies=4),
     "multi64_50m": dict(kind="files_passages", seed=20210614, N=50_000_000, F=64, len_range=(10_000, 2_000_000),
                         V=500_000, s=1.0, passages=500, passage_len=200, passage_frac=0.05),
-    # many small files: 100k files, Zipf 1.1 over 200k words; file lengths
-    # log-uniform in [100, 5000] tokens (a tenth of [1k, 50k], ~125M tokens,
-    # so that the CPU Sequitur build stays within minutes)
-    "files100k": dict(kind="many_files", seed=20210616, F=100_000, len_range=(100, 5_000), V=200_000, s=1.1),
+    # many files: 100k files of 1k-50k tokens (log-uniform, ~1.25B tokens),
+    # Zipf 1.1 over 200k words
+    "files100k": dict(kind="many_files", seed=20210616, F=100_000, len_range=(1_000, 50_000), V=200_000, s=1.1),
+    # the same shape with files of 100-5000 tokens: every file fits one CTA's
+    # shared memory (the per-file bottom-up path for short files)
+    "files_short": dict(kind="many_files", seed=20210618, F=100_000, len_range=(100, 5_000), V=200_000, s=1.1),
     # one large file with nested repeats (like dataset E): a deep rule DAG
     "nested_500m": dict(kind="nested", seed=20210615, N=500_000_000, V=1_000_000, s=1.05, phrases=4096,
                         phrase_len=16, depth=6, fanout=4, pool=256, inject_frac=0.5),
@@ -397,10 +424,12 @@ def load_config(name: str, scale: float = 1.0, keep_tokens: bool = False):
     corpus = make_corpus(name, scale=scale)
     if path.exists():
         g = Grammar.load(path)
-    elif corpus.tokens.shape[0] > SHARD_ABOVE:
-        g = sequitur_sharded(corpus.tokens, corpus.file_lens, corpus.num_words, shards=min(16, os.cpu_count() or 1))
     else:
-        g = sequitur(corpus.tokens, corpus.file_lens, corpus.num_words)
+        if corpus.tokens.shape[0] > SHARD_ABOVE:
+            g = sequitur_sharded(corpus.tokens, corpus.file_lens, corpus.num_words,
+                                 shards=min(16, os.cpu_count() or 1))
+        else:
+            g = sequitur(corpus.tokens, corpus.file_lens, corpus.num_words)
         g.meta = dict(corpus.meta)
         tmp = path.with_suffix(f".tmp{os.getpid()}.npz")
         g.save(tmp)
@@ -410,10 +439,26 @@ def load_config(name: str, scale: float = 1.0, keep_tokens: bool = False):
 
 def prefix_files(g: Grammar, k: int) -> Grammar:
     """The same grammar restricted to its first ``k`` files (rules unchanged)."""
-    k = max(1, min(k, g.num_files))
-    root_end = int(g.file_off[k])
+    return file_range(g, 0, max(1, min(k, g.num_files)))
+
+
+def file_range(g: Grammar, a: int, b: int) -> Grammar:
+    """The same grammar restricted to files ``a .. b-1`` (rules unchanged)."""
+    a, b = max(0, a), min(b, g.num_files)
+    r0, r1 = int(g.file_off[a]), int(g.file_off[b])
     root_len = int(g.rule_off[1])
-    sym = np.concatenate([g.sym[:root_end], g.sym[root_len:]]).astype(np.int32)
+    sym = np.concatenate([g.sym[r0:r1], g.sym[root_len:]]).astype(np.int32)
     rule_off = g.rule_off.copy()
-    rule_off[1:] -= root_len - root_end
-    return Grammar(g.num_words, rule_off, sym, g.file_off[:k + 1].copy(), dict(g.meta))
+    rule_off[1:] -= root_len - (r1 - r0)
+    return Grammar(g.num_words, rule_off, sym, (g.file_off[a:b + 1] - r0).astype(np.int64), dict(g.meta))
+
+
+def root_prefix(g: Grammar, n: int) -> Grammar:
+    """A one-file grammar whose file is the first ``n`` root symbols of ``g``'s
+    first file (rules unchanged): a bounded sample of a one-file corpus."""
+    n = max(1, min(n, int(g.file_off[1])))
+    root_len = int(g.rule_off[1])
+    sym = np.concatenate([g.sym[:n], g.sym[root_len:]]).astype(np.int32)
+    rule_off = g.rule_off.copy()
+    rule_off[1:] -= root_len - n
+    return Grammar(g.num_words, rule_off, sym, np.array([0, n], np.int64), dict(g.meta))

@@ -3,6 +3,7 @@
 // library's CUDA kernels; there is no CPU path.
 #include <algorithm>
 #include <cstring>
+#include <memory>
 #include <new>
 
 #include <unordered_map>
@@ -224,6 +225,7 @@ GT_API gt_status gt_load_grammar(gt_ctx* ctx, const gt_grammar_desc* desc, void*
     // symbols padded to whole tiles with -1 (never a word, never a rule);
     // uploads go straight from the caller's arrays (DMA when they are pinned)
     const cudaMemcpyKind up = desc->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    auto upload_phase = std::make_unique<gt::Phase>(ctx, "load_upload", s);
     const int64_t Gp = std::max<int64_t>((G + gt::kTile - 1) / gt::kTile, 1) * gt::kTile;
     void* p = gt::grammar_alloc(g, size_t(Gp) * 4, s);
     if (Gp > G) GT_CUDA(cudaMemsetAsync(static_cast<int32_t*>(p) + G, 0xff, size_t(Gp - G) * 4, s));
@@ -257,14 +259,22 @@ GT_API gt_status gt_load_grammar(gt_ctx* ctx, const gt_grammar_desc* desc, void*
       std::memcpy(bp + size_t(nc + 1) * 8 + size_t(F + 2) * 8, cl.data(), size_t(nc) * 4);
       char* q = static_cast<char*>(gt::grammar_alloc(g, blob.size(), s));
       GT_CUDA(cudaMemcpyAsync(q, blob.data(), blob.size(), cudaMemcpyHostToDevice, s));
+      upload_phase.reset();
       GT_CUDA(cudaStreamSynchronize(s));  // blob is a host temporary
       d.rch_start = reinterpret_cast<int64_t*>(q);
       d.rch_foff = reinterpret_cast<int64_t*>(q + size_t(nc + 1) * 8);
       d.rch_count = d.rch_foff + F + 1;
       d.rch_len = reinterpret_cast<int32_t*>(q + size_t(nc + 1) * 8 + size_t(F + 2) * 8);
     }
-    gt::load_build_dag(g, s);
-    gt::file_sizes(g, s);
+    {
+      gt::Phase ph(ctx, "load_dag", s);
+      gt::load_build_dag(g, s);
+    }
+    {
+      // the top-down per-file layout (<= 64 files): DAG facts every per-file query reuses
+      gt::Phase ph(ctx, "load_file_layout", s);
+      gt::file_sizes(g, s);
+    }
     g->info.file_pairs = g->fentry_bound;
     g->info.file_words = g->fword_bound;
     g->info.num_words = V;
@@ -286,6 +296,7 @@ GT_API gt_status gt_free_grammar(gt_grammar* g) {
   cudaDeviceSynchronize();
   for (auto& e : g->wc_graphs)
     if (e.exec) cudaGraphExecDestroy(e.exec);
+  if (g->seq_tile_ev) cudaEventDestroy(g->seq_tile_ev);
   for (void* p : g->owned) cudaFreeAsync(p, nullptr);  // grammar memory comes from the context pool
   delete g;
   return GT_OK;
@@ -311,29 +322,51 @@ GT_API gt_status gt_rule_weights(gt_grammar* g, uint64_t* d_weights, void* strea
 
 namespace {
 
-void word_count_direct(gt_grammar* g, uint64_t* d_counts, cudaStream_t s) {
+void word_count_direct(gt_grammar* g, uint64_t* d_counts, cudaStream_t s, uint32_t* status = nullptr) {
   Buf wt(g->ctx, size_t(g->d.R) * 8, s);
   gt::run_rule_weights(g, wt.as<uint64_t>(), s);
-  gt::run_word_count(g, wt.as<uint64_t>(), d_counts, s);
+  gt::run_word_count(g, wt.as<uint64_t>(), d_counts, s, status);
+}
+
+__global__ void or_status_kernel(uint32_t* __restrict__ dst, const uint32_t* __restrict__ src) {
+  if (*src) atomicOr(dst, *src);
 }
 
 // The whole word-count launch sequence of one grammar into one output buffer,
 // captured once as a CUDA graph (scratch allocations and frees included as
 // graph memory nodes) and replayed: one launch instead of about a dozen.
-// Returns null if the sequence cannot be captured.
-cudaGraphExec_t word_count_graph(gt_grammar* g, uint64_t* d_counts) {
+// Launches the replay on s and returns true, or returns false (first call
+// with this buffer, or the sequence cannot be captured).  The lock is held
+// through the launch, so an eviction by another thread cannot free the exec
+// in between.
+bool word_count_graph(gt_grammar* g, uint64_t* d_counts, cudaStream_t s) {
   std::lock_guard<std::mutex> lk(g->graph_mu);
   gt_grammar::WcGraph* ent = nullptr;
   for (auto& e : g->wc_graphs)
     if (e.out == d_counts) ent = &e;
-  if (ent && ent->exec) return ent->exec;
+  const uint64_t now = ++g->graph_tick;
+  if (ent) ent->last_use = now;
+  auto replay = [&](const gt_grammar::WcGraph& e) {
+    GT_CUDA(cudaGraphLaunch(e.exec, s));
+    gt::g_launches.fetch_add(e.kernels);
+    return true;
+  };
+  if (ent && ent->exec) return replay(*ent);
   if (!ent) {  // first call with this buffer: run directly, capture on the next one
-    g->wc_graphs.push_back({d_counts, nullptr, 1, 0});
-    return nullptr;
+    if (g->wc_graphs.size() >= gt_grammar::kMaxWcGraphs) {
+      // evict the least recently used entry (an exec still running is freed
+      // by CUDA once it completes)
+      auto lru = std::min_element(g->wc_graphs.begin(), g->wc_graphs.end(),
+                                  [](const auto& a, const auto& b) { return a.last_use < b.last_use; });
+      if (lru->exec) cudaGraphExecDestroy(lru->exec);
+      g->wc_graphs.erase(lru);
+    }
+    g->wc_graphs.push_back({d_counts, nullptr, now, 0});
+    return false;
   }
   const long long l0 = gt::g_launches.load();
   cudaStream_t cs;
-  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return false;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
@@ -353,29 +386,17 @@ cudaGraphExec_t word_count_graph(gt_grammar* g, uint64_t* d_counts) {
   // kernels recorded during capture did not run; replays account for them
   const long long recorded = gt::g_launches.load() - l0;
   gt::g_launches.fetch_sub(recorded);
-  if (!ok) return nullptr;
+  if (!ok) return false;
   ent->exec = exec;
   ent->kernels = int(recorded);
-  return exec;
+  return replay(*ent);
 }
 
 // Word count into d_counts: replayed from a graph when allowed (not while
 // profiling, so that phase timers keep seeing each launch).
 void word_count_any(gt_grammar* g, uint64_t* d_counts, cudaStream_t s) {
-  cudaGraphExec_t exec =
-      (g->ctx->param("use_graphs", 1) && !g->ctx->prof_on) ? word_count_graph(g, d_counts) : nullptr;
-  if (exec) {
-    GT_CUDA(cudaGraphLaunch(exec, s));
-    int k = 0;
-    {
-      std::lock_guard<std::mutex> lk(g->graph_mu);
-      for (auto& e : g->wc_graphs)
-        if (e.exec == exec) k = e.kernels;
-    }
-    gt::g_launches.fetch_add(k);
-  } else {
-    word_count_direct(g, d_counts, s);
-  }
+  const bool replayed = g->ctx->param("use_graphs", 1) && !g->ctx->prof_on && word_count_graph(g, d_counts, s);
+  if (!replayed) word_count_direct(g, d_counts, s);
 }
 
 }  // namespace
@@ -410,7 +431,9 @@ GT_API gt_status gt_head_tail(gt_grammar* g, int32_t* d_head, int32_t* d_tail, v
 namespace {
 
 // Sort result from already computed word counts.
-gt_result* sort_from_counts(gt_grammar* g, const uint64_t* wc, int order, cudaStream_t s) {
+// wc_status: device status word of the word count that produced wc.
+gt_result* sort_from_counts(gt_grammar* g, const uint64_t* wc, int order, cudaStream_t s,
+                            const uint32_t* wc_status) {
   gt_ctx* ctx = g->ctx;
   const int64_t V = g->d.V;
   const int threads = 256, cap = ctx->num_sms * 8;
@@ -441,7 +464,7 @@ gt_result* sort_from_counts(gt_grammar* g, const uint64_t* wc, int order, cudaSt
   }
   rb.field_dyn("word", words, nlen);
   rb.field_dyn("count", counts, nlen);
-  GT_CUDA(cudaMemcpyAsync(rb.status(), ctx->d_status, 4, cudaMemcpyDeviceToDevice, s));
+  GT_CUDA(cudaMemcpyAsync(rb.status(), wc_status, 4, cudaMemcpyDeviceToDevice, s));
   return rb.finish();
 }
 
@@ -453,13 +476,14 @@ GT_API gt_status gt_sort(gt_grammar* g, int order, void* stream, gt_result** out
   return guard(g->ctx, [&] {
     use_device(g->ctx);
     cudaStream_t s = as_stream(stream);
-    Buf wc(g->ctx, size_t(g->d.V) * 8, s);
+    Buf wc(g->ctx, size_t(g->d.V) * 8, s), wst(g->ctx, 4, s);
+    GT_CUDA(cudaMemsetAsync(wst.p, 0, 4, s));
     {
       Buf wt(g->ctx, size_t(g->d.R) * 8, s);
       gt::run_rule_weights(g, wt.as<uint64_t>(), s);
-      gt::run_word_count(g, wt.as<uint64_t>(), wc.as<uint64_t>(), s);
+      gt::run_word_count(g, wt.as<uint64_t>(), wc.as<uint64_t>(), s, wst.as<uint32_t>());
     }
-    *out = sort_from_counts(g, wc.as<uint64_t>(), order, s);
+    *out = sort_from_counts(g, wc.as<uint64_t>(), order, s, wst.as<uint32_t>());
   });
 }
 
@@ -557,17 +581,25 @@ GT_API gt_status gt_run_batch(gt_ctx* ctx, const gt_query* q, int nq, void* stre
         fg.push_back(wg[k]);
         fc.push_back(wc[k]);
       }
+    // this batch's own status word: sorts report the flags of the word counts
+    // they are built on, word-count queries also through the context's word
+    Buf bst(ctx, 4, s);
+    GT_CUDA(cudaMemsetAsync(bst.p, 0, 4, s));
+    bool any_sort = false, used_bst = !fg.empty();
+    for (int i = 0; i < nq; ++i) any_sort = any_sort || q[i].kind == GT_Q_SORT;
     if (fg.size() == 1) {
       bool caller = false;
       for (int i = 0; i < nq; ++i)
         if (q[i].grammar == fg[0] && q[i].kind == GT_Q_WORD_COUNT && q[i].d_counts == fc[0]) caller = true;
-      if (caller)
-        word_count_any(fg[0], fc[0], s);  // caller buffer: graph-replayable
-      else
-        word_count_direct(fg[0], fc[0], s);
+      if (caller && !any_sort) {
+        word_count_any(fg[0], fc[0], s);  // caller buffer: graph-replayable (flags go to the context word)
+        used_bst = false;
+      } else
+        word_count_direct(fg[0], fc[0], s, bst.as<uint32_t>());
     } else {
       for (size_t a = 0; a < fg.size(); a += 64)
-        gt::run_word_count_multi(fg.data() + a, fc.data() + a, int(std::min<size_t>(64, fg.size() - a)), s);
+        gt::run_word_count_multi(fg.data() + a, fc.data() + a, int(std::min<size_t>(64, fg.size() - a)), s,
+                                 bst.as<uint32_t>());
     }
     for (int i = 0; i < nq; ++i) {
       if (done[i]) continue;
@@ -607,7 +639,12 @@ GT_API gt_status gt_run_batch(gt_ctx* ctx, const gt_query* q, int nq, void* stre
       if (q[j].kind == GT_Q_WORD_COUNT && q[j].d_counts != counts_of[q[j].grammar])
         GT_CUDA(cudaMemcpyAsync(q[j].d_counts, counts_of[q[j].grammar], size_t(q[j].grammar->d.V) * 8,
                                 cudaMemcpyDeviceToDevice, s));
-      if (q[j].kind == GT_Q_SORT) out[j] = sort_from_counts(q[j].grammar, counts_of[q[j].grammar], q[j].param, s);
+      if (q[j].kind == GT_Q_SORT)
+        out[j] = sort_from_counts(q[j].grammar, counts_of[q[j].grammar], q[j].param, s, bst.as<uint32_t>());
+    }
+    if (used_bst) {
+      or_status_kernel<<<1, 1, 0, s>>>(ctx->d_status, bst.as<uint32_t>());
+      GT_LAUNCH_CHECK();
     }
   });
   if (st != GT_OK)
@@ -708,7 +745,8 @@ GT_API int64_t gt_kernel_launches(void) { return gt::g_launches.load(); }
 
 GT_API gt_status gt_set_param(gt_ctx* ctx, const char* name, int64_t value) {
   if (!ctx || !name) return GT_EINVAL;
-  static const char* known[] = {"wc_aggregate", "use_graphs", "file_strategy", "wc_slices", "bu_local"};
+  static const char* known[] = {"wc_aggregate", "use_graphs", "file_strategy", "wc_slices", "bu_local", "seq_path",
+                                "seq_table_cap"};
   for (const char* k : known)
     if (std::strcmp(k, name) == 0) {
       ctx->params[name] = value;

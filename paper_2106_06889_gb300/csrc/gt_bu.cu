@@ -610,7 +610,6 @@ gt_result* bu_inverted_index(gt_grammar* g, WordRows& wr, cudaStream_t s) {
   GT_LAUNCH_CHECK();
   rb.field("offsets", off, int64_t(d.V) + 1);
   rb.field_dyn("file", files, len);
-  GT_CUDA(cudaMemcpyAsync(rb.status(), ctx->d_status, 4, cudaMemcpyDeviceToDevice, s));
   return rb.finish();
 }
 

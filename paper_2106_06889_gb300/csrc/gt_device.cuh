@@ -8,6 +8,19 @@
 
 namespace gt {
 
+// Lanes of the warp holding the same 8-bit digit as this lane (among `active`),
+// from one ballot per digit bit.  Every lane of the warp must call it.
+__device__ __forceinline__ unsigned warp_digit_peers(uint32_t d, unsigned active) {
+  unsigned peers = active;
+#pragma unroll
+  for (int b = 0; b < 8; ++b) {
+    const bool bit = (d >> b) & 1u;
+    const unsigned bal = __ballot_sync(0xffffffffu, bit);
+    peers &= bit ? bal : ~bal;
+  }
+  return peers;
+}
+
 __device__ __forceinline__ int64_t upper_bound_dev(const int64_t* a, int64_t n, int64_t x) {
   int64_t lo = 0, hi = n;
   while (lo < hi) {
@@ -76,6 +89,43 @@ __device__ __forceinline__ int windows_at(const DevGrammar& d, const int32_t* __
   k[0] = w0 ? x0 : x1;
   k[1] = x1;
   return int(w0) + int(n2 >= 0);
+}
+
+// Windows of the 4 symbols j0 .. j0+3: symbol i has n[i] of them, keys
+// k[i][0..n[i]), owner rule r[i].
+struct TileWin {
+  uint64_t k[4][2];
+  int32_t r[4];
+  int n[4];
+};
+
+__device__ __forceinline__ int tile_windows(const DevGrammar& d, const int32_t* __restrict__ head,
+                                            const int32_t* __restrict__ tail, int kb, int64_t j0, TileWin& t) {
+  int c = 0;
+  int64_t end = -1;  // end of the body sequence holding the previous symbol (rule or root file)
+  int32_t rule = 0, f;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int64_t j = j0 + i;
+    t.n[i] = 0;
+    t.r[i] = 0;
+    if (j < d.G) {
+      // the four symbols usually share one sequence: look it up again only
+      // when the previous one ended (or at a root / rule boundary)
+      if (j >= end || j == d.root_len) end = seq_end(d, j, &rule, &f);
+      t.r[i] = rule;
+      t.n[i] = windows_at(d, head, tail, j, end, kb, t.k[i]);
+    }
+    c += t.n[i];
+  }
+  return c;
+}
+
+// compact key (kb bits per word) -> w1 << 42 | w2 << 21 | w3; kb == 0 keeps it
+__device__ __forceinline__ uint64_t to_output_key(uint64_t k, int kb) {
+  if (kb == 0) return k;
+  const uint64_t m = (uint64_t(1) << kb) - 1;
+  return ((k >> (2 * kb)) << 42) | (((k >> kb) & m) << 21) | (k & m);
 }
 
 }  // namespace gt

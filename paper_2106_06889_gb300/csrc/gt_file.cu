@@ -853,7 +853,6 @@ gt_result* term_vector_from(gt_grammar* g, FileHist& fh, int top_k, cudaStream_t
   rb.field("offsets", tv_off, int64_t(d.F) + 1);
   rb.field_dyn("word", word, len);
   rb.field_dyn("count", cnt, len);
-  GT_CUDA(cudaMemcpyAsync(rb.status(), ctx->d_status, 4, cudaMemcpyDeviceToDevice, s));
   return rb.finish();
 }
 
@@ -879,7 +878,6 @@ gt_result* inverted_index_from(gt_grammar* g, FileHist& fh, cudaStream_t s) {
   GT_CUDA(cudaMemcpyAsync(len, fh.total.p, 8, cudaMemcpyDeviceToDevice, s));
   rb.field("offsets", ii_off, V + 1);
   rb.field_dyn("file", files, len);
-  GT_CUDA(cudaMemcpyAsync(rb.status(), ctx->d_status, 4, cudaMemcpyDeviceToDevice, s));
   return rb.finish();
 }
 
@@ -982,7 +980,6 @@ gt_result* tv_from_arrays(gt_ctx* ctx, const int32_t* word, const uint64_t* cnt,
     rb.field_dyn("word", kw, len);
     rb.field_dyn("count", kcnt, len);
   }
-  GT_CUDA(cudaMemcpyAsync(rb.status(), ctx->d_status, 4, cudaMemcpyDeviceToDevice, s));
   return rb.finish();
 }
 

@@ -192,15 +192,24 @@ struct gt_grammar {
   int64_t bu_words = 0;           // sum over distinct (file, root child) pairs of the child's length
   int64_t bu_windows = 0;         // ... and of the child's 3-word windows
   int64_t max_file_len = 0;       // tokens of the longest file
+  // owned 3-word windows of every tile of symbols, exclusive scan [ntiles + 1]:
+  // structure only (no weights), built by the first global sequence count
+  // and kept; seq_tile_ev marks its completion for other streams
+  const int64_t* seq_tile_off = nullptr;
+  cudaEvent_t seq_tile_ev = nullptr;
+  std::mutex seq_mu;
   std::vector<void*> owned;      // device allocations to free with the grammar
-  // word-count launch sequences captured as CUDA graphs, keyed by output buffer
+  // word-count launch sequences captured as CUDA graphs, keyed by output
+  // buffer; at most kMaxWcGraphs per grammar, the least recently used evicted
   struct WcGraph {
     uint64_t* out;
     cudaGraphExec_t exec;  // null until the second call with this buffer
-    int uses;
+    uint64_t last_use;     // value of graph_tick at the last call
     int kernels;           // kernels one replay launches
   };
+  static constexpr size_t kMaxWcGraphs = 8;
   std::vector<WcGraph> wc_graphs;
+  uint64_t graph_tick = 0;
   std::mutex graph_mu;
   // per-grammar parameter choices of gt_autotune; they take precedence over
   // the context's gt_set_param values
@@ -355,9 +364,13 @@ void csr_offsets_hi(const uint64_t* keys, int64_t n, int64_t nh, int64_t* off, c
 
 // gt_wc.cu
 void run_rule_weights(gt_grammar* g, uint64_t* d_wt, cudaStream_t s);
-void run_word_count(gt_grammar* g, const uint64_t* d_wt, uint64_t* d_counts, cudaStream_t s);
+// Device-detected failures of a word count (ST_* bits) go to *status, or to
+// the context's status word (read by gt_sync) when status is null.
+void run_word_count(gt_grammar* g, const uint64_t* d_wt, uint64_t* d_counts, cudaStream_t s,
+                    uint32_t* status = nullptr);
 // word counts of up to 64 grammars (one context) in one fused launch sequence
-void run_word_count_multi(gt_grammar* const* gs, uint64_t* const* counts, int n, cudaStream_t s);
+void run_word_count_multi(gt_grammar* const* gs, uint64_t* const* counts, int n, cudaStream_t s,
+                          uint32_t* status = nullptr);
 void run_head_tail(gt_grammar* g, int32_t* d_head, int32_t* d_tail, cudaStream_t s);
 
 // Sorted 3-word window rows: compact keys (kb bits per word, key_pad above
@@ -405,6 +418,8 @@ gt_result* tv_from_arrays(gt_ctx* ctx, const int32_t* word, const uint64_t* cnt,
 
 // gt_seq.cu: sequence count (l = 3) and ranked inverted index
 gt_result* run_sequence_count(gt_grammar* g, int per_file, cudaStream_t s);
+// gt_seqg.cu: the global count (per_file == 0) by sample-sort buckets
+gt_result* run_sequence_count_global(gt_grammar* g, cudaStream_t s);
 gt_result* run_ranked_windows(gt_grammar* g, cudaStream_t s);
 // rows (key, file, count) -> ranked index; keys are compact 3-word keys
 // (windows = true, kb bits per word) or word ids (windows = false)

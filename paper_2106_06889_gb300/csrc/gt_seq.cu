@@ -31,32 +31,6 @@ namespace {
 // tile its first row, and pass 2 ranks the windows inside the tile.
 constexpr int kWinThreads = kTile / 4;
 
-// Windows of the 4 symbols j0 .. j0+3: symbol i has n[i] of them, keys
-// k[i][0..n[i]), owner rule r[i].
-struct TileWin {
-  uint64_t k[4][2];
-  int32_t r[4];
-  int n[4];
-};
-
-__device__ __forceinline__ int tile_windows(const DevGrammar& d, const int32_t* __restrict__ head,
-                                            const int32_t* __restrict__ tail, int kb, int64_t j0, TileWin& t) {
-  int c = 0;
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int64_t j = j0 + i;
-    t.n[i] = 0;
-    t.r[i] = 0;
-    if (j < d.G) {
-      int32_t f;
-      const int64_t end = seq_end(d, j, &t.r[i], &f);
-      t.n[i] = windows_at(d, head, tail, j, end, kb, t.k[i]);
-    }
-    c += t.n[i];
-  }
-  return c;
-}
-
 // Exclusive prefix of v over the CTA (kWinThreads threads); *total gets the sum.
 __device__ __forceinline__ int cta_excl_scan(int v, int* total) {
   __shared__ int warp_tot[kWinThreads / 32];
@@ -181,13 +155,6 @@ __global__ void pad_tail_kernel(uint64_t* __restrict__ keys, uint64_t* __restric
     if (fkeys) fkeys[i] = file_pad;
     if (vals) vals[i] = 0;
   }
-}
-
-// compact key (kb bits per word) -> w1 << 42 | w2 << 21 | w3; kb == 0 keeps it
-__device__ __forceinline__ uint64_t to_output_key(uint64_t k, int kb) {
-  if (kb == 0) return k;
-  const uint64_t m = (uint64_t(1) << kb) - 1;
-  return ((k >> (2 * kb)) << 42) | (((k >> kb) & m) << 21) | (k & m);
 }
 
 // Rows that are already one per (file, key): keys to 21-bit fields, copied.
@@ -417,7 +384,8 @@ void sort_by_file_key(gt_ctx* ctx, Buf& k0, Buf& f0, Buf& v0, int64_t bound, int
 
 namespace {
 
-void sorted_windows(gt_grammar* g, bool per_file, cudaStream_t s, Windows& out) {
+// Device-detected failures go to *status (the result's own status word).
+void sorted_windows(gt_grammar* g, bool per_file, cudaStream_t s, Windows& out, uint32_t* status) {
   gt_ctx* ctx = g->ctx;
   const DevGrammar& d = g->d;
   const int threads = 256, cap = ctx->num_sms * 16;
@@ -454,7 +422,7 @@ void sorted_windows(gt_grammar* g, bool per_file, cudaStream_t s, Windows& out) 
       exclusive_scan_i64(tcnt.as<int64_t>(), toff.as<int64_t>(), nt + 1, tsc.p, s);
       win_emit_kernel<<<unsigned(nt), kWinThreads, 0, s>>>(d, head.as<int32_t>(), tail.as<int32_t>(),
                                                             wt.as<uint64_t>(), kb, out.key_pad, toff.as<int64_t>(), n,
-                                                            k0.as<uint64_t>(), v0.as<uint32_t>(), ctx->d_status);
+                                                            k0.as<uint64_t>(), v0.as<uint32_t>(), status);
       GT_LAUNCH_CHECK();
       pad_tail_kernel<<<grid_for(n, threads, cap), threads, 0, s>>>(k0.as<uint64_t>(), nullptr, v0.as<uint32_t>(),
                                                                      toff.as<int64_t>() + nt, n, out.key_pad, 0);
@@ -602,14 +570,15 @@ gt_result* ranked_from_rows(gt_ctx* ctx, Buf& rkey, Buf& rfile, Buf& rcnt, const
   rb.field_dyn("key", okey, len_key);
   rb.field_dyn("file", ofile, len_row);
   rb.field_dyn("count", ocnt, len_row);
-  GT_CUDA(cudaMemcpyAsync(rb.status(), ctx->d_status, 4, cudaMemcpyDeviceToDevice, s));
   return rb.finish();
 }
 
 gt_result* run_ranked_windows(gt_grammar* g, cudaStream_t s) {
   gt_ctx* ctx = g->ctx;
   Windows w;
-  sorted_windows(g, true, s, w);
+  Buf st(ctx, 4, s);  // no kernel of the per-file window paths raises a flag
+  GT_CUDA(cudaMemsetAsync(st.p, 0, 4, s));
+  sorted_windows(g, true, s, w, st.as<uint32_t>());
   if (w.reduced)
     return ranked_from_rows(ctx, w.keys, w.rfile, w.rcnt, w.total.as<int64_t>(), w.n, w.kb, true, w.key_pad,
                             uint64_t(g->max_file_len), s);
@@ -622,10 +591,11 @@ gt_result* run_ranked_windows(gt_grammar* g, cudaStream_t s) {
 }
 
 gt_result* run_sequence_count(gt_grammar* g, int per_file, cudaStream_t s) {
+  if (!per_file && gparam(g, "seq_path", 0) == 0) return run_sequence_count_global(g, s);
   gt_ctx* ctx = g->ctx;
   ResultBuilder rb(ctx, s);
   Windows w;
-  sorted_windows(g, per_file != 0, s, w);
+  sorted_windows(g, per_file != 0, s, w, rb.status());
   Phase ph(ctx, "seq_reduce", s);
   auto* key = static_cast<uint64_t*>(rb.alloc(size_t(w.n) * 8));
   auto* count = static_cast<uint64_t*>(rb.alloc(size_t(w.n) * 8));
@@ -646,7 +616,6 @@ gt_result* run_sequence_count(gt_grammar* g, int per_file, cudaStream_t s) {
   if (per_file) rb.field_dyn("file", file, len);
   rb.field_dyn("key", key, len);
   rb.field_dyn("count", count, len);
-  GT_CUDA(cudaMemcpyAsync(rb.status(), ctx->d_status, 4, cudaMemcpyDeviceToDevice, s));
   return rb.finish();
 }
 

@@ -104,11 +104,15 @@ void worker_loop(gt_server* sv) {
     // ---- retire finished groups ----
     for (size_t i = 0; i < sv->inflight.size();) {
       Group& gr = sv->inflight[i];
-      if (cudaEventQuery(gr.ev) == cudaSuccess) {
+      // anything but "not ready" ends the group: a failed query (a sticky
+      // context error included) must not stay in flight forever
+      const cudaError_t q = cudaEventQuery(gr.ev);
+      if (q != cudaErrorNotReady) {
         const auto now = Clock::now();
         for (Request* r : gr.reqs) {
           r->finished = now;
           r->done = true;
+          if (q != cudaSuccess && r->status == GT_OK) r->status = GT_ECUDA;
         }
         sv->busy[gr.slot] = false;
         sv->in_use -= gr.footprint;

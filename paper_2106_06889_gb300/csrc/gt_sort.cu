@@ -5,7 +5,7 @@
 // canonical ordering of every result.
 #include <type_traits>
 
-#include "gt_internal.cuh"
+#include "gt_device.cuh"
 
 namespace gt {
 namespace {
@@ -93,19 +93,6 @@ constexpr int kRsThreads = 256;  // one thread per digit value in the per-tile b
 constexpr int kRsWarps = kRsThreads / 32;
 constexpr int kRsItems = 8;      // keys per thread; 8 x 256 threads with 4 CTAs per SM measured fastest
 constexpr int kRsTile = kRsThreads * kRsItems;  // keys per tile
-
-// Lanes of the warp holding the same 8-bit digit as this lane (among `active`),
-// from one ballot per digit bit.
-__device__ __forceinline__ unsigned warp_digit_peers(uint32_t d, unsigned active) {
-  unsigned peers = active;
-#pragma unroll
-  for (int b = 0; b < 8; ++b) {
-    const bool bit = (d >> b) & 1u;
-    const unsigned bal = __ballot_sync(0xffffffffu, bit);
-    peers &= bit ? bal : ~bal;
-  }
-  return peers;
-}
 
 // Per-tile digit counts, stored tile-major (hist[tile * 256 + d]) so that
 // each CTA writes one contiguous row.

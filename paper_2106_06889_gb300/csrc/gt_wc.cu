@@ -473,8 +473,9 @@ struct WcScratch {
 
 template <int NJ>
 void word_count_batch(gt_grammar* const* gs, const uint64_t* const* wts, uint64_t* const* counts, int n,
-                      cudaStream_t s) {
+                      cudaStream_t s, uint32_t* status) {
   gt_ctx* ctx = gs[0]->ctx;
+  if (!status) status = ctx->d_status;
   WcBatch<NJ> bt{};
   std::unique_ptr<WcScratch[]> scr(new WcScratch[size_t(n)]);
   int part = 0, hist = 0, red = 0;
@@ -546,7 +547,7 @@ void word_count_batch(gt_grammar* const* gs, const uint64_t* const* wts, uint64_
     Phase ph(ctx, "wc_partition", s);
     const size_t smem = sizeof(PartShared);
     GT_CUDA(cudaFuncSetAttribute(wc_partition_kernel<NJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
-    wc_partition_kernel<NJ><<<part, kPartThreads, smem, s>>>(bt, ctx->d_status);
+    wc_partition_kernel<NJ><<<part, kPartThreads, smem, s>>>(bt, status);
     GT_LAUNCH_CHECK();
   }
   {
@@ -565,11 +566,12 @@ void word_count_batch(gt_grammar* const* gs, const uint64_t* const* wts, uint64_
 
 void run_rule_weights(gt_grammar* g, uint64_t* d_wt, cudaStream_t s) { weights_batch<1>(&g, &d_wt, 1, s); }
 
-void run_word_count(gt_grammar* g, const uint64_t* d_wt, uint64_t* d_counts, cudaStream_t s) {
-  word_count_batch<1>(&g, &d_wt, &d_counts, 1, s);
+void run_word_count(gt_grammar* g, const uint64_t* d_wt, uint64_t* d_counts, cudaStream_t s, uint32_t* status) {
+  word_count_batch<1>(&g, &d_wt, &d_counts, 1, s, status);
 }
 
-void run_word_count_multi(gt_grammar* const* gs, uint64_t* const* counts, int n, cudaStream_t s) {
+void run_word_count_multi(gt_grammar* const* gs, uint64_t* const* counts, int n, cudaStream_t s,
+                          uint32_t* status) {
   if (n <= 0) return;
   if (n > kMaxWcJobs) fail(GT_EINVAL, "at most 64 grammars per fused word count");
   std::vector<Buf> wt;
@@ -580,10 +582,10 @@ void run_word_count_multi(gt_grammar* const* gs, uint64_t* const* counts, int n,
   }
   if (n == 1) {
     weights_batch<1>(gs, wp.data(), 1, s);
-    word_count_batch<1>(gs, wp.data(), counts, 1, s);
+    word_count_batch<1>(gs, wp.data(), counts, 1, s, status);
   } else {
     weights_batch<kMaxWcJobs>(gs, wp.data(), n, s);
-    word_count_batch<kMaxWcJobs>(gs, wp.data(), counts, n, s);
+    word_count_batch<kMaxWcJobs>(gs, wp.data(), counts, n, s, status);
   }
 }
 

@@ -73,7 +73,8 @@ def test_sequitur_rejects_bad_input():
         sequitur(np.array([0, 1], np.int32), [3], 3)  # lengths do not add up
 
 
-@pytest.mark.parametrize("name,scale", [("nested_500m", 0.001), ("files100k", 0.01), ("multi64_50m", 0.004)])
+@pytest.mark.parametrize("name,scale", [("nested_500m", 0.001), ("files100k", 0.001), ("files_short", 0.01),
+                                        ("multi64_50m", 0.004)])
 @pytest.mark.parametrize("shards", [1, 3, 7])
 def test_sharded_sequitur_expands_to_source(name, scale, shards):
     """The shard-parallel build used for the largest corpora encodes the same

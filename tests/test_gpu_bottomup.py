@@ -143,10 +143,13 @@ def test_batch_shares_bottom_up_rows(ctx):
         B.gt_free_grammar(gh)
 
 
-def test_many_small_files(ctx):
-    """The many-small-files workload (Zipf 1.1 over 200k words), 2000 files:
-    ranked index (words and 3-word keys), term vector and inverted index."""
-    c = make_corpus("files100k", scale=0.02)
+@pytest.mark.parametrize("name,scale,files", [("files_short", 0.02, 2000), ("files100k", 0.002, 200)])
+def test_many_files(ctx, name, scale, files):
+    """The many-files workloads (Zipf 1.1 over 200k words): 2000 files of
+    100-5000 tokens (per-file shared-memory path) and 200 files of 1k-50k
+    tokens (global sort path): ranked index (words and 3-word keys), term
+    vector and inverted index."""
+    c = make_corpus(name, scale=scale)
     g = sequitur(c.tokens, c.file_lens, c.num_words)
-    assert g.num_files == 2000
+    assert g.num_files == files
     check_all(ctx, g)

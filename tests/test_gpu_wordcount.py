@@ -181,3 +181,21 @@ def test_graph_replay_matches(ctx):
     assert np.array_equal(out.cpu().numpy().astype(np.uint64), want)
     B.gt_set_param(ctx, "use_graphs", 1)
     B.gt_free_grammar(gh)
+
+
+def test_graph_cache_bounded_by_lru(ctx):
+    """More output buffers than the per-grammar graph cache holds (8): every
+    call, captured, replayed or after an eviction, gives the oracle's counts."""
+    c = make_corpus("wc_single_200k", scale=0.25)
+    g = sequitur(c.tokens, c.file_lens, c.num_words)
+    gh = B.gt_load_grammar(ctx, g)
+    want = oracle.word_count(g)
+    outs = [torch.empty(g.num_words, dtype=torch.int64, device="cuda") for _ in range(12)]
+    for rnd in range(3):  # buffer k: direct, captured, replayed or re-captured after eviction
+        for k, out in enumerate(outs):
+            out.fill_(-3)
+            B.gt_word_count(gh, out)
+        B.gt_sync(ctx)
+        for k, out in enumerate(outs):
+            assert np.array_equal(out.cpu().numpy().astype(np.uint64), want), (rnd, k)
+    B.gt_free_grammar(gh)
