@@ -136,8 +136,11 @@ def kernel_bytes(workload: str, info: dict, out: dict) -> dict:
     symbols it reads (4 B each); tv_hist_kernel: the term-vector pairs it
     writes (12 B each); expand_words_kernel: the rule bodies it reads (4 B per
     rule symbol); wc_partition_kernel and sg_scatter_kernel: the symbol stream
-    (4 B per body symbol); sg_reduce_kernel: the owned windows it counts (32 B
-    each, one table update) and the distinct 3-grams it writes (16 B each)."""
+    (4 B per body symbol).  On the 3-gram workload the rows of owned windows
+    (8 B key + 4 B weight) stand in for the per-window table updates of the
+    paper's sequence support (Section IV-D): radix_downsweep_kernel<4> and sg_scatter_kernel read and write
+    every row once per launch (24 B), sg_reduce_kernel reads them (12 B) and
+    writes the distinct 3-grams (16 B each)."""
     G, V = info["num_syms"], info["num_words"]
     root_len = out["root_len"]
     nb = (V + 16383) // 16384
@@ -146,14 +149,17 @@ def kernel_bytes(workload: str, info: dict, out: dict) -> dict:
                 "tv_hist_kernel": ("tv_hist_kernel", 12 * out["tv_pairs"]),
                 "expand_words": ("expand_words_kernel", 4 * (G - root_len)),
                 "wc_partition": ("wc_partition_kernel", 4 * G)}
-    return {"seq_scatter": ("sg_scatter_kernel", 4 * G),
-            "seq_reduce": ("sg_reduce_kernel", 32 * info["owned_windows"] + 16 * out["distinct_3grams"]),
+    U = info["owned_windows"]
+    return {"radix_pass": ("radix_downsweep_kernel<4>", 24 * U),
+            "seq_scatter": ("sg_scatter_kernel", 24 * U),
+            "seq_reduce": ("sg_reduce_kernel", 12 * U + 16 * out["distinct_3grams"]),
             "wc_partition": ("wc_partition_kernel", 4 * G)}
 
 
 PHASES = ("weights", "wc_partition", "wc_hist", "sort_canon", "file_weights", "expand_words", "tv_hist",
           "chunk_sort_root", "chunk_sort_rules", "tv_hist_kernel", "tv_out", "ii_out", "wc_from_files",
-          "seq_headtail", "seq_part", "seq_scatter", "seq_fine", "seq_reduce")
+          "seq_headtail", "seq_emit", "seq_sort", "radix_pass", "seq_part", "seq_scatter", "seq_fine", "seq_reduce",
+          "tv_out", "cooc_rows", "rows_sort")
 LOAD_PHASES = ("load_upload", "load_dag", "load_file_layout")
 
 
@@ -315,6 +321,27 @@ def measure(B, ctx, workload, g, steps, warmup, world, stream, autotune=True, e2
         keep.clear()
     ms = max_over_ranks(ev0.elapsed_time(ev1), world)
     ms_step = ms / steps
+    # ---- the same step as one graph launch (gt_plan: the batch captured once) ----
+    graph_step = None
+    try:
+        plan = B.gt_plan_create(ctx, qs, stream)
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                B.gt_plan_launch(plan, stream)
+            torch.cuda.synchronize()
+            g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            l0 = B.gt_kernel_launches()
+            g0.record(stream)
+            for _ in range(steps):
+                B.gt_plan_launch(plan, stream)
+            g1.record(stream)
+            torch.cuda.synchronize()
+        gms = max_over_ranks(g0.elapsed_time(g1), world) / steps
+        graph_step = {"ms_per_step": gms, "value": job_throughput(world, N, 1, gms / 1e3), "unit": "tokens/s",
+                      "kernels_per_launch": (B.gt_kernel_launches() - l0) // steps, "graph_launches_per_step": 1}
+        B.gt_plan_destroy(plan)
+    except B.GtError as e:
+        graph_step = {"error": str(e)}
     phases = {}
     for ph in PHASES:
         tot, spans, la = B.gt_profile_read(ctx, ph)
@@ -376,7 +403,7 @@ def measure(B, ctx, workload, g, steps, warmup, world, stream, autotune=True, e2
     B.gt_free_grammar(gh)
     return {"value": job_throughput(world, N, steps, ms / 1e3), "ms_per_step": ms_step, "tokens": N,
             "info": info, "outputs": outs, "roofline": roofline, "phases": phases, "load": load, "e2e": e2e,
-            "gpu_launches": launches, "clocks": clk, "autotune": tune}
+            "gpu_launches": launches, "clocks": clk, "autotune": tune, "graph_step": graph_step}
 
 
 # ---------------------------------------------------------------------------
@@ -565,13 +592,13 @@ def many_files(B, ctx, reps=3):
 
 
 def sequence_paths(B, ctx, g, stream, reps=3):
-    """The global 3-word count by the sample-sort buckets (default) and by the
-    one-row-per-window LSD radix sort it replaced, on the same grammar."""
+    """The global 3-word count by the one-row-per-window LSD radix sort (the
+    default) and by the sample-sort buckets, on the same grammar."""
     import torch
     gh = B.gt_load_grammar(ctx, g, stream)
     out = {}
     with torch.cuda.stream(stream):
-        for name, path in (("bucketed", 0), ("radix_sort", 1)):
+        for name, path in (("bucketed", 2), ("radix_sort", 1)):
             B.gt_set_param(ctx, "seq_path", path)
             B.gt_free_result(B.gt_sequence_count(gh, 0, stream))
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -584,9 +611,24 @@ def sequence_paths(B, ctx, g, stream, reps=3):
             for r in keep:
                 B.gt_free_result(r)
             out[name + "_ms"] = e0.elapsed_time(e1) / reps
-    B.gt_set_param(ctx, "seq_path", 0)
+    B.gt_set_param(ctx, "seq_path", 1)
     B.gt_free_grammar(gh)
     return out
+
+
+def uncompressed_baseline(B, ctx, workload, stream, steps=5):
+    """The workload's step on the uncompressed token stream: the same corpus
+    as a root-only grammar (no rules), run by the same kernels - the GPU
+    uncompressed-analytics baseline the paper compares G-TADOC with (it
+    reports 2x on average).  Device time per step, inputs resident."""
+    from paper_2106_06889_gb300.corpus import load_config, root_only_grammar
+    _, c = load_config(workload, keep_tokens=True)
+    g = root_only_grammar(c.tokens, c.file_lens, c.num_words)
+    del c
+    m = measure(B, ctx, workload, g, steps, 3, 1, stream, autotune=False, e2e_steps=0, clocks=False)
+    return {"value": m["value"], "unit": "tokens/s", "ms_per_step": m["ms_per_step"],
+            "grammar_symbols": m["info"]["num_syms"], "load_ms": m["load"]["ms"],
+            "note": "the corpus as a root-only grammar: every token is a root symbol, no rules"}
 
 
 # ---------------------------------------------------------------------------
@@ -765,7 +807,7 @@ def workload_summary(m: dict) -> dict:
     info = m["info"]
     return {"value": m["value"], "unit": "tokens/s", "ms_per_step": m["ms_per_step"],
             "roofline": m["roofline"], "phases": m["phases"], "load_ms": m["load"], "e2e": m["e2e"],
-            "gpu_launches": m["gpu_launches"], "outputs": m["outputs"],
+            "gpu_launches": m["gpu_launches"], "outputs": m["outputs"], "graph_step": m["graph_step"],
             "grammar": {k: info[k] for k in ("num_tokens", "num_syms", "num_rules", "num_files", "num_edges",
                                              "depth", "owned_windows", "file_pairs")}}
 
@@ -807,6 +849,9 @@ def main():
     extras = {}
     if not args.no_extras and world == 1:
         extras["sequence_count_paths"] = {"corpus": args.workload, **sequence_paths(B, ctx, g, stream)}
+        unc = uncompressed_baseline(B, ctx, args.workload, stream)
+        unc["compressed_over_uncompressed"] = m["value"] / unc["value"]
+        extras["uncompressed_baseline"] = {args.workload: unc}
         extras["small_word_count"] = small_word_count(B, ctx)
         extras["many_files"] = many_files(B, ctx)
         other = "nested_500m" if args.workload != "nested_500m" else None
@@ -816,6 +861,9 @@ def main():
                          e2e_steps=0 if args.no_e2e else 2, clocks=False)
             x = {"workload": other, "desc": WORKLOADS[other]["desc"], "analytics": WORKLOADS[other]["analytics"],
                  **workload_summary(m3), "sequence_count_paths": sequence_paths(B, ctx, g3, stream)}
+            unc = uncompressed_baseline(B, ctx, other, stream, steps=3)
+            unc["compressed_over_uncompressed"] = m3["value"] / unc["value"]
+            extras["uncompressed_baseline"][other] = unc
             if not args.no_cpu_baseline:
                 x["cpu_baseline"] = cpu_baselines(g3, WORKLOADS[other]["analytics"])
             extras[other] = x
@@ -837,6 +885,7 @@ def main():
                            "l2": f"inputs larger than L2 (symbol array {4 * info['num_syms'] / 1e6:.0f} MB > 129 MB)",
                            "autotune": m["autotune"]},
                 "roofline": m["roofline"], "load_ms": m["load"], "phases": m["phases"], "outputs": m["outputs"],
+                "graph_step": m["graph_step"],
                 "extras": extras, "serving": serving, "cpu_baseline": cpu, "e2e": m["e2e"],
                 "gpu_launches": m["gpu_launches"], "clocks": m["clocks"]}
         print(json.dumps(line))

@@ -26,8 +26,10 @@
  *     message for the last failure on a context is available from
  *     gt_last_error.  Failures that only the GPU can detect (a full overflow
  *     list, a row count past its bound, an invalid symbol) are recorded in a
- *     device status word and reported by gt_sync / gt_result_view.  No call
- *     waits on the device inside a kernel.
+ *     device status word and reported by gt_sync / gt_result_view.  The
+ *     only wait inside a kernel is the global sequence count's look-back
+ *     (a CTA polls the published counts of the buckets before its own); it
+ *     gives up after a bounded number of polls with GT_ETIMEOUT.
  *   - There is no CPU fallback: if no usable sm_103a device is present,
  *     gt_create fails with GT_ECUDA.
  */
@@ -46,7 +48,7 @@ typedef int gt_status;
 #define GT_EINVAL 1       /* malformed argument or grammar                      */
 #define GT_ENOMEM 2       /* device or pool allocation failed                   */
 #define GT_ECUDA 3        /* a CUDA runtime call failed                         */
-#define GT_ETIMEOUT 4     /* a bounded device-side wait gave up (none in this version) */
+#define GT_ETIMEOUT 4     /* a bounded device-side wait gave up (the sequence count's look-back) */
 #define GT_ETABLE_FULL 5  /* a device overflow list ran out of room             */
 #define GT_EOVERFLOW 6    /* a size exceeds what the encoding supports          */
 #define GT_EBUSY 7        /* admission refused: not enough free memory / slots  */
@@ -194,6 +196,25 @@ gt_status gt_sequence_count(gt_grammar* g, int per_file, void* stream, gt_result
  * "file" int32[m], "count" uint64[m].  Strategy as for gt_inverted_index. */
 gt_status gt_ranked_index(gt_grammar* g, int n, void* stream, gt_result** out);
 
+/* TF-IDF (the Introduction lists it among the analytics that build on the
+ * six of Section VI): the term vector of every file with, per entry,
+ * tfidf = count * ln(F / df(word)), df(word) = the number of files holding
+ * the word, F = num_files.  Fields "offsets" int64[num_files+1], "word"
+ * int32[], "count" uint64[], "tfidf" float64[] (ascending word per file).
+ * One traversal serves the term vector and the document frequencies;
+ * strategy as for gt_inverted_index.  float64 arithmetic: ln is CUDA's
+ * double-precision log (at most 1 ulp off), the quotient and the product
+ * are correctly rounded. */
+gt_status gt_tfidf(gt_grammar* g, void* stream, gt_result** out);
+
+/* Word co-occurrence within a window of three words: every ordered pair of
+ * words (a, b) with b one or two positions after a inside one file, counted.
+ * Fields "key" uint64[n] = a << 21 | b (ascending), "count" uint64[n]
+ * (requires num_words <= 2^21).  Derived from the 3-word counts of
+ * gt_sequence_count: the (first, second) and (first, third) pairs of every
+ * window, plus the last pair of every file. */
+gt_status gt_cooccurrence(gt_grammar* g, void* stream, gt_result** out);
+
 /* Head and tail buffers (Section IV-C): for every rule, the first two and
  * the last two words of its expansion (word IDs; -1 pads a rule whose
  * expansion has a single word).  d_head, d_tail: device int32[2*num_rules]. */
@@ -215,7 +236,9 @@ typedef enum {
   GT_Q_INVERTED_INDEX = 2,
   GT_Q_TERM_VECTOR = 3,    /* param: top_k (0 = all)                            */
   GT_Q_SEQUENCE_COUNT = 4, /* param: per_file (0 or 1)                          */
-  GT_Q_RANKED_INDEX = 5    /* param: n (1 or 3)                                 */
+  GT_Q_RANKED_INDEX = 5,   /* param: n (1 or 3)                                 */
+  GT_Q_TFIDF = 6,          /* shares the term vector's traversal                */
+  GT_Q_COOCCURRENCE = 7
 } gt_query_kind;
 
 typedef struct {
@@ -226,6 +249,23 @@ typedef struct {
 } gt_query;
 
 gt_status gt_run_batch(gt_ctx* ctx, const gt_query* q, int nq, void* stream, gt_result** out);
+
+/* Plans (the batched form as one launch; not in the paper).  gt_plan_create
+ * runs the batch once on `stream` (and waits for it), then captures the same
+ * batch - every launch, scratch allocation and result copy - into a CUDA
+ * graph.  gt_plan_launch replays that graph on a stream: one graph launch per
+ * step.  Each launch rewrites the plan's results in place; gt_plan_result
+ * gives query i's field (as gt_result_view, waiting for the launch) and is
+ * valid until the next launch; GT_EBUSY before the first launch, GT_ENOTFOUND
+ * for a word count (it writes into its d_counts, rewritten by every launch).
+ * The queries' grammars and word-count buffers must stay valid while the plan
+ * exists.  Launches of one plan must be ordered (one stream, or events).
+ * GT_EINVAL while profiling is enabled. */
+typedef struct gt_plan gt_plan;
+gt_status gt_plan_create(gt_ctx* ctx, const gt_query* q, int nq, void* stream, gt_plan** out);
+gt_status gt_plan_launch(gt_plan* p, void* stream);
+gt_status gt_plan_result(gt_plan* p, int i, const char* field, const void** d_ptr, int64_t* len);
+gt_status gt_plan_destroy(gt_plan* p);
 
 /* ---- serving (not in the paper) ------------------------------------------
  * A server keeps the context's grammars resident and runs submitted requests
@@ -294,6 +334,13 @@ int64_t gt_kernel_launches(void);
  *   "bu_local"      1 (default): bottom-up word rows of grammars whose files
  *                   all have at most 8192 tokens are built per file in shared
  *                   memory; 0: always by the global (file, word) sort.
+ *   "seq_path"      global sequence count: 1 (default) one row per owned window,
+ *                   LSD radix sort by key, segmented sum; 2 sample-sort
+ *                   buckets reduced in shared memory (gt_seqg.cu).  Same
+ *                   results; bench.py times both.
+ *   "seq_table_cap" distinct keys a bucket may hold in shared memory on the
+ *                   bucket path (2..3072, default 3072); fuller buckets are
+ *                   sorted in global memory.
  *   "file_strategy" per-file analytics (term vector, inverted index, per-file
  *                   sequence count, ranked index): 0 (default) picks top-down
  *                   for at most 64 files and bottom-up otherwise (the paper's

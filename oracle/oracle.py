@@ -288,3 +288,43 @@ def ranked_index(g, n: int = 3):
     keys, first = np.unique(k, return_index=True)
     offs = np.append(first, k.shape[0]).astype(np.int64)
     return offs, keys.astype(np.uint64), f.astype(np.int32), c.astype(np.uint64)
+
+
+# ---------------------------------------------------------------------------
+# Advanced analytics on the same traversal (the Introduction and Related Work
+# name TF-IDF and word co-occurrence as the analytics that build on these)
+# ---------------------------------------------------------------------------
+
+def tfidf_text(files):
+    """TF-IDF per file: for every word w of file f, tf = its in-file count and
+    idf = ln(F / df(w)), df(w) = the number of files containing w (F = number
+    of files).  CSR over files, words ascending, values float64 = tf * idf.
+    (Reading: raw counts for tf and the natural log for idf, no smoothing.)"""
+    offs, words, counts = term_vector_text(files)
+    F = len(files)
+    df = np.bincount(words.astype(np.int64), minlength=int(words.max()) + 1 if words.size else 0)
+    idf = np.log(np.float64(F) / df[words.astype(np.int64)].astype(np.float64)) if words.size else np.zeros(0)
+    return offs, words, counts.astype(np.float64) * idf
+
+
+def tfidf(g):
+    return tfidf_text(expand_files(g))
+
+
+def cooccurrence_text(files):
+    """Word co-occurrence within a window of three words: the ordered pairs
+    (t[i], t[j]) with j - i in {1, 2} inside one file, counted.  Keys pack as
+    a << 21 | b, ascending; counts uint64."""
+    keys = []
+    for t in files:
+        t = np.asarray(t, dtype=np.uint64)
+        for d in (1, 2):
+            if t.shape[0] > d:
+                keys.append((t[:-d] << np.uint64(KEY_BITS)) | t[d:])
+    k = np.concatenate(keys) if keys else np.zeros(0, np.uint64)
+    u, c = np.unique(k, return_counts=True)
+    return u.astype(np.uint64), c.astype(np.uint64)
+
+
+def cooccurrence(g):
+    return cooccurrence_text(expand_files(g))

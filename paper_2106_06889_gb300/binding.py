@@ -43,7 +43,7 @@ class gt_query(ctypes.Structure):
 
 
 GT_Q_WORD_COUNT, GT_Q_SORT, GT_Q_INVERTED_INDEX, GT_Q_TERM_VECTOR = 0, 1, 2, 3
-GT_Q_SEQUENCE_COUNT, GT_Q_RANKED_INDEX = 4, 5
+GT_Q_SEQUENCE_COUNT, GT_Q_RANKED_INDEX, GT_Q_TFIDF, GT_Q_COOCCURRENCE = 4, 5, 6, 7
 
 
 class gt_grammar_info(ctypes.Structure):
@@ -79,6 +79,8 @@ def lib() -> ctypes.CDLL:
             "gt_term_vector": [_P, ctypes.c_int, _P, ctypes.POINTER(_P)],
             "gt_sequence_count": [_P, ctypes.c_int, _P, ctypes.POINTER(_P)],
             "gt_ranked_index": [_P, ctypes.c_int, _P, ctypes.POINTER(_P)],
+            "gt_tfidf": [_P, _P, ctypes.POINTER(_P)],
+            "gt_cooccurrence": [_P, _P, ctypes.POINTER(_P)],
             "gt_head_tail": [_P, _P, _P, _P],
             "gt_result_view": [_P, ctypes.c_char_p, ctypes.POINTER(_P), ctypes.POINTER(ctypes.c_int64)],
             "gt_free_result": [_P],
@@ -86,6 +88,10 @@ def lib() -> ctypes.CDLL:
             "gt_set_param": [_P, ctypes.c_char_p, ctypes.c_int64],
             "gt_autotune": [_P, ctypes.c_uint32, ctypes.c_int, _P, _P],
             "gt_run_batch": [_P, _P, ctypes.c_int, _P, _P],
+            "gt_plan_create": [_P, _P, ctypes.c_int, _P, ctypes.POINTER(_P)],
+            "gt_plan_launch": [_P, _P],
+            "gt_plan_result": [_P, ctypes.c_int, ctypes.c_char_p, ctypes.POINTER(_P), ctypes.POINTER(ctypes.c_int64)],
+            "gt_plan_destroy": [_P],
             "gt_server_create": [_P, ctypes.c_int, ctypes.c_size_t, ctypes.POINTER(_P)],
             "gt_submit": [_P, _P, ctypes.c_int, ctypes.POINTER(ctypes.c_uint64)],
             "gt_poll": [_P, ctypes.c_uint64, ctypes.c_int, _P, ctypes.POINTER(ctypes.c_int64)],
@@ -262,9 +268,17 @@ def gt_ranked_index(g: GrammarHandle, n: int = 3, stream=None) -> ResultHandle:
     return _result_call(lib().gt_ranked_index, g, n, stream=stream)
 
 
+def gt_tfidf(g: GrammarHandle, stream=None) -> ResultHandle:
+    return _result_call(lib().gt_tfidf, g, stream=stream)
+
+
+def gt_cooccurrence(g: GrammarHandle, stream=None) -> ResultHandle:
+    return _result_call(lib().gt_cooccurrence, g, stream=stream)
+
+
 # ---- results ------------------------------------------------------------------
 
-_TYPESTR = {"word": "<i4", "file": "<i4", "count": "<u8", "key": "<u8", "offsets": "<i8"}
+_TYPESTR = {"word": "<i4", "file": "<i4", "count": "<u8", "key": "<u8", "offsets": "<i8", "tfidf": "<f8"}
 
 
 class _DeviceArray:
@@ -291,7 +305,8 @@ def result_tensor(r: ResultHandle, field: str):
     if ts == "<u8":
         ts = "<i8"  # counts and keys are < 2^63; torch's int64 views them losslessly
     if n == 0 or ptr == 0:
-        return torch.empty(0, dtype=torch.int32 if ts == "<i4" else torch.int64, device="cuda")
+        empty = {"<i4": torch.int32, "<f8": torch.float64}.get(ts, torch.int64)
+        return torch.empty(0, dtype=empty, device="cuda")
     return torch.as_tensor(_DeviceArray(ptr, n, ts), device="cuda")
 
 
@@ -360,6 +375,44 @@ def gt_run_batch(ctx: Context, queries, stream=None):
     _check(lib().gt_run_batch(ctx.handle, ctypes.cast(arr, ctypes.c_void_p), n, _stream(stream),
                               ctypes.cast(outs, ctypes.c_void_p)), ctx.handle)
     return [ResultHandle(ctypes.c_void_p(outs[i]), ctx) if outs[i] else None for i in range(n)]
+
+
+# ---- plans: a batch captured once as a CUDA graph ---------------------------------
+
+@dataclass
+class Plan:
+    handle: ctypes.c_void_p
+    ctx: Context
+    keep: object  # the query array and its tensors stay referenced while the plan exists
+
+
+def gt_plan_create(ctx: Context, queries, stream=None) -> Plan:
+    arr = _query_array(queries)
+    h = _P()
+    _check(lib().gt_plan_create(ctx.handle, ctypes.cast(arr, ctypes.c_void_p), len(queries), _stream(stream),
+                                ctypes.byref(h)), ctx.handle)
+    return Plan(h, ctx, (arr, [q[3] for q in queries]))
+
+
+def gt_plan_launch(p: Plan, stream=None) -> None:
+    _check(lib().gt_plan_launch(p.handle, _stream(stream)), p.ctx.handle)
+
+
+def plan_result_numpy(p: Plan, i: int, field: str) -> np.ndarray:
+    """Field of query i's result from the plan's last launch, copied to host."""
+    import torch
+    ptr, n = _P(), ctypes.c_int64()
+    _check(lib().gt_plan_result(p.handle, i, field.encode(), ctypes.byref(ptr), ctypes.byref(n)), p.ctx.handle)
+    ts = _TYPESTR[field]
+    if n.value == 0:
+        return np.zeros(0, dtype=np.dtype(ts))
+    t = torch.as_tensor(_DeviceArray(int(ptr.value), int(n.value), "<i8" if ts == "<u8" else ts), device="cuda")
+    a = t.cpu().numpy()
+    return a.astype(np.uint64) if ts == "<u8" else a
+
+
+def gt_plan_destroy(p: Plan) -> None:
+    _check(lib().gt_plan_destroy(p.handle))
 
 
 # ---- serving --------------------------------------------------------------------

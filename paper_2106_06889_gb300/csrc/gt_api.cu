@@ -15,6 +15,7 @@ using gt::fail;
 
 namespace gt {
 std::atomic<long long> g_launches{0};
+thread_local gt_ctx* t_call_ctx = nullptr;
 }
 
 namespace {
@@ -39,7 +40,10 @@ gt_status guard(gt_ctx* ctx, F&& f) {
 
 cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
 
-void use_device(gt_ctx* ctx) { GT_CUDA(cudaSetDevice(ctx->device)); }
+void use_device(gt_ctx* ctx) {
+  GT_CUDA(cudaSetDevice(ctx->device));
+  gt::t_call_ctx = ctx;
+}
 
 gt_status status_to_code(uint32_t st) {
   if (st & gt::ST_INVALID) return GT_EINVAL;
@@ -395,7 +399,10 @@ bool word_count_graph(gt_grammar* g, uint64_t* d_counts, cudaStream_t s) {
 // Word count into d_counts: replayed from a graph when allowed (not while
 // profiling, so that phase timers keep seeing each launch).
 void word_count_any(gt_grammar* g, uint64_t* d_counts, cudaStream_t s) {
-  const bool replayed = g->ctx->param("use_graphs", 1) && !g->ctx->prof_on && word_count_graph(g, d_counts, s);
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  GT_CUDA(cudaStreamIsCapturing(s, &cap));
+  const bool replayed = g->ctx->param("use_graphs", 1) && !g->ctx->prof_on && cap == cudaStreamCaptureStatusNone &&
+                        word_count_graph(g, d_counts, s);
   if (!replayed) word_count_direct(g, d_counts, s);
 }
 
@@ -514,6 +521,24 @@ GT_API gt_status gt_ranked_index(gt_grammar* g, int n, void* stream, gt_result**
   });
 }
 
+GT_API gt_status gt_tfidf(gt_grammar* g, void* stream, gt_result** out) {
+  if (!g || !out) return GT_EINVAL;
+  *out = nullptr;
+  return guard(g->ctx, [&] {
+    use_device(g->ctx);
+    *out = gt::run_tfidf(g, as_stream(stream));
+  });
+}
+
+GT_API gt_status gt_cooccurrence(gt_grammar* g, void* stream, gt_result** out) {
+  if (!g || !out) return GT_EINVAL;
+  *out = nullptr;
+  return guard(g->ctx, [&] {
+    use_device(g->ctx);
+    *out = gt::run_cooccurrence(g, as_stream(stream));
+  });
+}
+
 GT_API gt_status gt_inverted_index(gt_grammar* g, void* stream, gt_result** out) {
   if (!g || !out) return GT_EINVAL;
   *out = nullptr;
@@ -532,7 +557,7 @@ GT_API gt_status gt_run_batch(gt_ctx* ctx, const gt_query* q, int nq, void* stre
   for (int i = 0; i < nq; ++i) {
     out[i] = nullptr;
     if (!q[i].grammar || q[i].grammar->ctx != ctx) return GT_EINVAL;
-    if (q[i].kind < GT_Q_WORD_COUNT || q[i].kind > GT_Q_RANKED_INDEX) return GT_EINVAL;
+    if (q[i].kind < GT_Q_WORD_COUNT || q[i].kind > GT_Q_COOCCURRENCE) return GT_EINVAL;
     if (q[i].kind == GT_Q_SEQUENCE_COUNT && q[i].param != 0 && q[i].param != 1) return GT_EINVAL;
     if (q[i].kind == GT_Q_RANKED_INDEX && q[i].param != 1 && q[i].param != 3) return GT_EINVAL;
     if (q[i].kind == GT_Q_WORD_COUNT && !q[i].d_counts) return GT_EINVAL;
@@ -611,9 +636,9 @@ GT_API gt_status gt_run_batch(gt_ctx* ctx, const gt_query* q, int nq, void* stre
       std::vector<int> tv_idx, tv_k;
       int ii = -1;
       for (int j : same) {
-        if (q[j].kind == GT_Q_TERM_VECTOR) {
+        if (q[j].kind == GT_Q_TERM_VECTOR || q[j].kind == GT_Q_TFIDF) {  // TF-IDF: a term vector with idf
           tv_idx.push_back(j);
-          tv_k.push_back(q[j].param);
+          tv_k.push_back(q[j].kind == GT_Q_TFIDF ? gt::kTfIdf : q[j].param);
         }
         if (q[j].kind == GT_Q_INVERTED_INDEX && ii < 0) ii = j;
       }
@@ -631,6 +656,7 @@ GT_API gt_status gt_run_batch(gt_ctx* ctx, const gt_query* q, int nq, void* stre
         if (q[j].kind == GT_Q_SEQUENCE_COUNT) out[j] = gt::run_sequence_count(g, q[j].param, s);
         if (q[j].kind == GT_Q_RANKED_INDEX)
           out[j] = q[j].param == 3 ? gt::run_ranked_windows(g, s) : gt::run_ranked_words(g, s);
+        if (q[j].kind == GT_Q_COOCCURRENCE) out[j] = gt::run_cooccurrence(g, s);
       }
       for (int j : same) done[j] = true;
     }
@@ -693,6 +719,7 @@ GT_API gt_status gt_free_result(gt_result* r) {
   if (r->done) cudaEventSynchronize(r->done);
   for (void* p : r->owned) cudaFreeAsync(p, nullptr);
   r->ctx->give_back(r->h_lens, r->done);
+  for (gt_result* x : r->deps) gt_free_result(x);  // done before r: same stream, earlier work
   delete r;
   return GT_OK;
 }
@@ -754,4 +781,118 @@ GT_API gt_status gt_set_param(gt_ctx* ctx, const char* name, int64_t value) {
     }
   ctx->last_error = std::string("unknown parameter: ") + name;
   return GT_ENOTFOUND;
+}
+
+// ============================================================================
+// plans: a batch captured once as a CUDA graph and replayed
+// ============================================================================
+
+struct gt_plan {
+  gt_ctx* ctx = nullptr;
+  std::vector<gt_query> q;
+  std::vector<gt_result*> res;  // results of the captured batch, rewritten by every launch
+  cudaGraphExec_t exec = nullptr;
+  long long kernels = 0;         // kernels one launch runs
+  int64_t launches = 0;
+};
+
+GT_API gt_status gt_plan_create(gt_ctx* ctx, const gt_query* q, int nq, void* stream, gt_plan** out) {
+  if (!ctx || !q || nq < 1 || !out) return GT_EINVAL;
+  *out = nullptr;
+  gt_plan* p = new (std::nothrow) gt_plan();
+  if (!p) return GT_ENOMEM;
+  p->ctx = ctx;
+  p->q.assign(q, q + nq);
+  p->res.assign(size_t(nq), nullptr);
+  gt_status st = guard(ctx, [&] {
+    use_device(ctx);
+    if (ctx->prof_on) fail(GT_EINVAL, "plans cannot be captured while profiling is enabled");
+    // one eager run: validates the queries and builds any per-grammar state
+    // that the first call of an analytic creates
+    std::vector<gt_result*> warm(size_t(nq), nullptr);
+    const gt_status w = gt_run_batch(ctx, q, nq, stream, warm.data());
+    if (w != GT_OK) fail(w, ctx->last_error);
+    GT_CUDA(cudaStreamSynchronize(as_stream(stream)));
+    for (gt_result* r : warm)
+      if (r) gt_free_result(r);
+    cudaStream_t cs;
+    GT_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t graph = nullptr;
+    const long long l0 = gt::g_launches.load();
+    gt_status rc = GT_OK;
+    std::string msg;
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      rc = gt_run_batch(ctx, q, nq, cs, p->res.data());
+      msg = ctx->last_error;
+      const cudaError_t e = cudaStreamEndCapture(cs, &graph);
+      if (rc == GT_OK && (e != cudaSuccess || !graph)) {
+        rc = GT_ECUDA;
+        msg = std::string("stream capture failed: ") + cudaGetErrorString(e);
+      }
+    } else {
+      rc = GT_ECUDA;
+      msg = "stream capture could not begin";
+    }
+    p->kernels = gt::g_launches.load() - l0;
+    gt::g_launches.fetch_sub(p->kernels);  // the captured launches did not run
+    if (rc == GT_OK) {
+      // a launch frees the allocations of the previous one: results are
+      // valid until the next launch of the plan
+      const cudaError_t e = cudaGraphInstantiate(&p->exec, graph, cudaGraphInstantiateFlagAutoFreeOnLaunch);
+      if (e != cudaSuccess) {
+        rc = GT_ECUDA;
+        msg = std::string("graph instantiation failed: ") + cudaGetErrorString(e);
+      }
+    }
+    if (graph) cudaGraphDestroy(graph);
+    cudaStreamDestroy(cs);
+    cudaGetLastError();
+    if (rc != GT_OK) fail(rc, msg);
+  });
+  if (st != GT_OK) {
+    for (gt_result* r : p->res)  // captured results hold no memory yet: release the host parts only
+      if (r) {
+        p->ctx->give_back(r->h_lens, r->done);
+        delete r;
+      }
+    delete p;
+    return st;
+  }
+  *out = p;
+  return GT_OK;
+}
+
+GT_API gt_status gt_plan_launch(gt_plan* p, void* stream) {
+  if (!p) return GT_EINVAL;
+  return guard(p->ctx, [&] {
+    use_device(p->ctx);
+    for (gt_result* r : p->res)
+      if (r) r->ready = false;  // lengths are read again after this launch
+    GT_CUDA(cudaGraphLaunch(p->exec, as_stream(stream)));
+    gt::g_launches.fetch_add(p->kernels);
+    ++p->launches;
+  });
+}
+
+GT_API gt_status gt_plan_result(gt_plan* p, int i, const char* field, const void** d_ptr, int64_t* len) {
+  if (!p || i < 0 || i >= int(p->res.size()) || !field || !d_ptr || !len) return GT_EINVAL;
+  if (!p->res[size_t(i)]) return GT_ENOTFOUND;  // a word count writes into the caller's buffer
+  if (p->launches == 0) return GT_EBUSY;       // nothing computed yet
+  return gt_result_view(p->res[size_t(i)], field, d_ptr, len);
+}
+
+GT_API gt_status gt_plan_destroy(gt_plan* p) {
+  if (!p) return GT_EINVAL;
+  cudaSetDevice(p->ctx->device);
+  cudaDeviceSynchronize();
+  for (gt_result* r : p->res) {
+    if (!r) continue;
+    if (p->launches > 0)  // the last launch's allocations are still live
+      for (void* x : r->owned) cudaFreeAsync(x, nullptr);
+    p->ctx->give_back(r->h_lens, r->done);
+    delete r;
+  }
+  if (p->exec) cudaGraphExecDestroy(p->exec);
+  delete p;
+  return GT_OK;
 }

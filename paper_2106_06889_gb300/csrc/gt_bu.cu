@@ -630,7 +630,7 @@ void run_file_batch_bu(gt_grammar* g, const int* tv_topk, int n_tv, gt_result** 
     GT_LAUNCH_CHECK();
     for (int i = 0; i < n_tv; ++i)
       tv_out[i] = tv_from_arrays(g->ctx, wr.word.as<int32_t>(), wr.cnt.as<uint64_t>(), toff.as<int64_t>(),
-                                 wr.total.as<int64_t>(), wr.bound, d.F, tv_topk[i], s);
+                                 wr.total.as<int64_t>(), wr.bound, d.F, tv_topk[i], s, d.V);
   }
   if (ii_out) *ii_out = bu_inverted_index(g, wr, s);
 }

@@ -825,7 +825,7 @@ gt_result* term_vector_from(gt_grammar* g, FileHist& fh, int top_k, cudaStream_t
   const int64_t pieces = int64_t(d.F) * fh.nb;
   const int64_t nb_ = fh.bound;
   TvSlots ts{fh.slot_word.as<int32_t>(), fh.slot_cnt.as<uint32_t>(), fh.nnz.as<int64_t>(), fh.bits.as<uint32_t>()};
-  if (top_k > 0) {
+  if (top_k != 0) {  // top-k selection or TF-IDF: from the gathered arrays
     Buf tw(ctx, size_t(nb_) * 4, s), tc(ctx, size_t(nb_) * 8, s), full_off(ctx, size_t(d.F + 1) * 8, s);
     {
       Phase ph(ctx, "tv_out", s);
@@ -837,7 +837,7 @@ gt_result* term_vector_from(gt_grammar* g, FileHist& fh, int top_k, cudaStream_t
       GT_LAUNCH_CHECK();
     }
     return tv_from_arrays(ctx, tw.as<int32_t>(), tc.as<uint64_t>(), full_off.as<int64_t>(), fh.total.as<int64_t>(),
-                          nb_, d.F, top_k, s);
+                          nb_, d.F, top_k, s, d.V);
   }
   ResultBuilder rb(ctx, s);
   Phase ph(ctx, "tv_out", s);
@@ -935,8 +935,26 @@ __global__ void copy_rows_kernel(const int32_t* __restrict__ w, const uint64_t* 
 
 // Term-vector result from (word, count) rows in (file, word) order with file
 // offsets; top_k > 0 keeps each file's top_k counts (count desc, word asc).
+// df[w] += 1 for every term-vector entry of w (the files containing w).
+__global__ void df_kernel(const int32_t* __restrict__ word, const int64_t* __restrict__ total,
+                          uint32_t* __restrict__ df) {
+  const int64_t n = *total;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    atomicAdd(&df[word[i]], 1u);
+}
+
+// TF-IDF of every term-vector entry: count * ln(F / df(word)).
+__global__ void tfidf_kernel(const int32_t* __restrict__ word, const uint64_t* __restrict__ cnt,
+                             const int64_t* __restrict__ total, const uint32_t* __restrict__ df, int32_t F,
+                             double* __restrict__ out) {
+  const int64_t n = *total;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    out[i] = double(cnt[i]) * log(double(F) / double(df[word[i]]));
+}
+
 gt_result* tv_from_arrays(gt_ctx* ctx, const int32_t* word, const uint64_t* cnt, const int64_t* tv_off_in,
-                          const int64_t* total, int64_t bound, int32_t F, int top_k, cudaStream_t s) {
+                          const int64_t* total, int64_t bound, int32_t F, int top_k, cudaStream_t s,
+                          int32_t V) {
   const int threads = 256, cap = ctx->num_sms * 16;
   ResultBuilder rb(ctx, s);
   Phase ph(ctx, "tv_out", s);
@@ -954,6 +972,19 @@ gt_result* tv_from_arrays(gt_ctx* ctx, const int32_t* word, const uint64_t* cnt,
     rb.field("offsets", tv_off, int64_t(F) + 1);
     rb.field_dyn("word", ow, len);
     rb.field_dyn("count", oc, len);
+    if (top_k == kTfIdf) {
+      if (V <= 0) fail(GT_EINVAL, "TF-IDF needs the vocabulary size");
+      auto* tf = static_cast<double*>(rb.alloc(size_t(bound) * 8));
+      Buf df(ctx, size_t(V) * 4, s);
+      GT_CUDA(cudaMemsetAsync(df.p, 0, size_t(V) * 4, s));
+      if (bound > 0) {
+        df_kernel<<<grid_for(bound, threads, cap), threads, 0, s>>>(ow, total, df.as<uint32_t>());
+        GT_LAUNCH_CHECK();
+        tfidf_kernel<<<grid_for(bound, threads, cap), threads, 0, s>>>(ow, oc, total, df.as<uint32_t>(), F, tf);
+        GT_LAUNCH_CHECK();
+      }
+      rb.field_dyn("tfidf", tf, len);
+    }
   } else {
     Buf k0(ctx, size_t(bound) * 8, s), k1(ctx, size_t(bound) * 8, s), i0(ctx, size_t(bound) * 4, s);
     Buf i1(ctx, size_t(bound) * 4, s), rs(ctx, radix_scratch_bytes(bound, true, 4), s);

@@ -41,6 +41,10 @@ struct Error {
 
 extern std::atomic<long long> g_launches;
 
+// The context of the API call running on this thread (set on entry), for
+// phase timers in primitives that take no context.
+extern thread_local gt_ctx* t_call_ctx;
+
 // Bits of the device status word.
 enum : uint32_t {
   ST_TABLE_FULL = 1u,
@@ -228,6 +232,8 @@ struct gt_result {
   std::vector<Field> fields;
   std::vector<void*> owned;  // device buffers to release
   int64_t* h_lens = nullptr; // pinned host array holding data-dependent lengths
+  int64_t* d_lens = nullptr; // their device copies (slot 0: status word), written by the kernels
+  std::vector<gt_result*> deps;  // results whose buffers this one reads; freed with it
   cudaEvent_t done = nullptr;
   bool ready = false;
 };
@@ -279,7 +285,7 @@ struct Phase {
   cudaEvent_t a = nullptr;
   long long l0 = 0;
   Phase(gt_ctx* c, const char* n, cudaStream_t st) : ctx(c), name(n), s(st) {
-    if (!ctx->prof_on) return;
+    if (!ctx || !ctx->prof_on) return;
     GT_CUDA(cudaEventCreate(&a));
     GT_CUDA(cudaEventRecord(a, s));
     l0 = g_launches.load();
@@ -314,6 +320,7 @@ struct ResultBuilder {
     GT_CUDA(cudaMallocFromPoolAsync(&p, kMaxSlots * sizeof(int64_t), ctx->pool, s));
     r->owned.push_back(p);
     d_lens = static_cast<int64_t*>(p);
+    r->d_lens = d_lens;
     GT_CUDA(cudaMemsetAsync(d_lens, 0, kMaxSlots * sizeof(int64_t), s));
     nslots = 1;
   }
@@ -413,11 +420,24 @@ inline void* grammar_alloc(gt_grammar* g, size_t bytes, cudaStream_t s) {
 // gt_tune.cu: a parameter of this grammar (autotuned value, else the context's)
 int64_t gparam(const gt_grammar* g, const char* name, int64_t dflt);
 // gt_file.cu: term-vector result from (word, count) rows in (file, word) order
+// top_k == kTfIdf: the term vector with a "tfidf" field (float64) instead of top-k selection
+constexpr int kTfIdf = -1;
 gt_result* tv_from_arrays(gt_ctx* ctx, const int32_t* word, const uint64_t* cnt, const int64_t* tv_off_in,
-                          const int64_t* total, int64_t bound, int32_t F, int top_k, cudaStream_t s);
+                          const int64_t* total, int64_t bound, int32_t F, int top_k, cudaStream_t s,
+                          int32_t V = 0);
+// Device pointer of a result field and the device slot holding its length
+// (valid on the result's stream before the result completes).
+void result_device_field(gt_result* r, const char* field, void** ptr, const int64_t** d_len);
 
 // gt_seq.cu: sequence count (l = 3) and ranked inverted index
 gt_result* run_sequence_count(gt_grammar* g, int per_file, cudaStream_t s);
+// gt_adv.cu: TF-IDF (term vector with idf weights) and word co-occurrence
+gt_result* run_tfidf(gt_grammar* g, cudaStream_t s);
+gt_result* run_cooccurrence(gt_grammar* g, cudaStream_t s);
+// gt_seq.cu: rows (key, weight) -> one row per distinct key with the weights
+// summed, ascending key; n rows (host bound), rows past *n_dev hold key_pad
+gt_result* reduce_key_rows(gt_ctx* ctx, Buf& keys, Buf& vals, int64_t n, int key_bits, uint64_t key_pad,
+                           cudaStream_t s, const uint32_t* status_in = nullptr);
 // gt_seqg.cu: the global count (per_file == 0) by sample-sort buckets
 gt_result* run_sequence_count_global(gt_grammar* g, cudaStream_t s);
 gt_result* run_ranked_windows(gt_grammar* g, cudaStream_t s);

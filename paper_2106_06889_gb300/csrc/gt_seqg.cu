@@ -31,6 +31,7 @@
 // Only counts depend on the weights; the order of rows inside a bucket is
 // whatever the atomics give, and the output is the same for every run.
 #include <algorithm>
+#include <cstddef>
 
 #include "gt_device.cuh"
 
@@ -245,51 +246,24 @@ __global__ void __launch_bounds__(kSgThreads) sg_emit_kernel(const __grid_consta
 
 // ---- 3. scatter into coarse buckets ---------------------------------------------
 
-constexpr int kScTile = 2048;  // rows per step of the coarse scatter (4 per thread)
-
-__device__ __forceinline__ uint32_t smem_addr(const void* p) { return uint32_t(__cvta_generic_to_shared(p)); }
-
-// 16-byte asynchronous copy global -> shared (completion by cp_async_wait).
-__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
+constexpr int kScTile = 4096;  // rows per step of the coarse scatter (8 per thread)
 
 struct ScatterShared {
   uint64_t spl[kMaxCoarse];
   uint64_t base[kMaxCoarse];  // next output row of each bucket for this CTA
   uint32_t hist[kMaxCoarse];  // rows of the current step per bucket
-  uint32_t start[kMaxCoarse]; // first staged slot of each bucket
+  uint32_t start[kMaxCoarse]; // first staged row of each bucket
   uint16_t lut[(1 << kLutBitsMax) + 1];
-  uint64_t rkey[2][kScTile];  // rows of the current and the next step (double buffer)
-  uint32_t rval[2][kScTile];
-  uint16_t perm[kScTile];     // staged slot -> row of the step, in bucket order
-  uint16_t bkt[kScTile];      // bucket of each staged slot
+  uint64_t key[kScTile];
+  uint32_t val[kScTile];
+  uint16_t bkt[kScTile];
 };
-
-// Copies the rows of aligned tile g (rows g * kScTile .. + kScTile) into
-// stage buffer st: 1024 chunks of two keys and 512 chunks of four weights.
-__device__ __forceinline__ void scatter_prefetch(ScatterShared& sh, int st, int64_t g, const uint64_t* ikey,
-                                                 const uint32_t* ival) {
-  const uint64_t* kp = ikey + g * kScTile;
-  const uint32_t* vp = ival + g * kScTile;
-  for (int c = threadIdx.x; c < kScTile / 2 + kScTile / 4; c += kSgThreads) {
-    if (c < kScTile / 2) cp_async16(&sh.rkey[st][2 * c], kp + 2 * c);
-    else cp_async16(&sh.rval[st][4 * (c - kScTile / 2)], vp + 4 * (c - kScTile / 2));
-  }
-}
 
 // CTA c re-reads the rows it emitted (its tiles' contiguous row range) and
 // writes each to its bucket's range: off[b * P + c] is the first row of
 // bucket b's rows from CTA c (bucket-major exclusive scan of the counts), so
-// every bucket is one contiguous range.  The rows arrive in aligned steps of
-// kScTile by asynchronous copies, the next step's while the current one is
-// ranked by bucket and written as runs in bucket order.  The row arrays are
-// padded to whole steps.
+// every bucket is one contiguous range.  Rows are staged in shared memory in
+// bucket order and written as runs.
 __global__ void __launch_bounds__(kSgThreads) sg_scatter_kernel(const __grid_constant__ SgArgs a,
                                                                 const int64_t* __restrict__ off,
                                                                 const uint64_t* __restrict__ ikey,
@@ -299,35 +273,35 @@ __global__ void __launch_bounds__(kSgThreads) sg_scatter_kernel(const __grid_con
   extern __shared__ __align__(16) unsigned char sg_smem[];
   ScatterShared& sh = *reinterpret_cast<ScatterShared*>(sg_smem);
   const int nb = a.nspl + 1;
-  int64_t t0, t1;
-  cta_tiles(a.d.ntiles, &t0, &t1);
-  const int64_t r0 = a.tile_off[t0], r1 = a.tile_off[t1];
-  if (r1 <= r0) return;
-  const int64_t g0 = r0 / kScTile, g1 = (r1 - 1) / kScTile;
-  scatter_prefetch(sh, 0, g0, ikey, ival);
-  cp_async_commit();
   for (int i = threadIdx.x; i < a.nspl; i += kSgThreads) sh.spl[i] = a.spl[i];
   for (int i = threadIdx.x; i <= (1 << a.lut_bits); i += kSgThreads) sh.lut[i] = a.lut[i];
   for (int b = threadIdx.x; b < nb; b += kSgThreads) {
     sh.base[b] = uint64_t(off[int64_t(b) * gridDim.x + blockIdx.x]);
     sh.hist[b] = 0;
   }
+  __syncthreads();
+  int64_t t0, t1;
+  cta_tiles(a.d.ntiles, &t0, &t1);
+  const int64_t r0 = a.tile_off[t0], r1 = a.tile_off[t1];
   constexpr int kPer = kScTile / kSgThreads;
-  for (int64_t g = g0; g <= g1; ++g) {
-    const int st = int(g - g0) & 1;
-    if (g < g1) scatter_prefetch(sh, st ^ 1, g + 1, ikey, ival);
-    cp_async_commit();
-    cp_async_wait<1>();  // this step's copies have landed
-    __syncthreads();
+  for (int64_t s0 = r0; s0 < r1; s0 += kScTile) {
+    uint64_t k[kPer];
+    uint32_t w[kPer], rk[kPer];
     int bq[kPer];
-    uint32_t rk[kPer];
 #pragma unroll
     for (int q = 0; q < kPer; ++q) {
-      const int i = q * kSgThreads + threadIdx.x;
-      const int64_t r = g * kScTile + i;
+      const int64_t r = s0 + q * kSgThreads + threadIdx.x;
+      w[q] = 0;
+      if (r < r1) {
+        k[q] = ikey[r];
+        w[q] = ival[r];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
       bq[q] = -1;
-      if (r >= r0 && r < r1 && sh.rval[st][i] != 0) {
-        bq[q] = coarse_bucket(sh.spl, sh.lut, a.lut_shift, sh.rkey[st][i]);
+      if (w[q]) {
+        bq[q] = coarse_bucket(sh.spl, sh.lut, a.lut_shift, k[q]);
         rk[q] = atomicAdd(&sh.hist[bq[q]], 1u);
       }
     }
@@ -338,23 +312,24 @@ __global__ void __launch_bounds__(kSgThreads) sg_scatter_kernel(const __grid_con
     for (int q = 0; q < kPer; ++q)
       if (bq[q] >= 0) {
         const uint32_t p = sh.start[bq[q]] + rk[q];
-        sh.perm[p] = uint16_t(q * kSgThreads + threadIdx.x);
+        sh.key[p] = k[q];
+        sh.val[p] = w[q];
         sh.bkt[p] = uint16_t(bq[q]);
       }
     __syncthreads();
     for (uint32_t p = threadIdx.x; p < T; p += kSgThreads) {
-      const int b = sh.bkt[p], i = sh.perm[p];
+      const int b = sh.bkt[p];
       const uint64_t gpos = sh.base[b] + (p - sh.start[b]);
-      okey[gpos] = sh.rkey[st][i];
-      oval[gpos] = sh.rval[st][i];
+      okey[gpos] = sh.key[p];
+      oval[gpos] = sh.val[p];
     }
     __syncthreads();
     for (int b = threadIdx.x; b < nb; b += kSgThreads) {
       sh.base[b] += sh.hist[b];
       sh.hist[b] = 0;
     }
+    __syncthreads();
   }
-  cp_async_wait<0>();
 }
 
 // ---- 4. fine buckets -----------------------------------------------------------
@@ -861,9 +836,14 @@ __device__ void sample_sort_shared(ReduceShared& sh, int d) {
     const int x = kSub - 1 - b;
     warp_bitonic_sort<1>(sh.tkey + sh.big_start[x], sh.tcnt + sh.big_start[x], int(sh.big_len[x]));
   }
-  for (int b = warp; b < nbig; b += kRdWarps)
-    if (sh.big_len[b] <= uint32_t(kWarpBin))
-      warp_bitonic_sort<8>(sh.tkey + sh.big_start[b], sh.tcnt + sh.big_start[b], int(sh.big_len[b]));
+  for (int b = warp; b < nbig; b += kRdWarps) {  // the smallest network that holds the sub-bucket
+    const uint32_t n = sh.big_len[b];
+    uint64_t* k = sh.tkey + sh.big_start[b];
+    uint32_t* c = sh.tcnt + sh.big_start[b];
+    if (n <= 64) warp_bitonic_sort<2>(k, c, int(n));
+    else if (n <= 128) warp_bitonic_sort<4>(k, c, int(n));
+    else if (n <= uint32_t(kWarpBin)) warp_bitonic_sort<8>(k, c, int(n));
+  }
   __syncthreads();
   for (int b = 0; b < nbig; ++b) {  // CTA-uniform
     const uint32_t s = sh.big_start[b], n = sh.big_len[b];
@@ -1050,28 +1030,11 @@ __global__ void __launch_bounds__(kRdThreads, 2) sg_reduce_kernel(const __grid_c
     }
     __syncthreads();
     // distinct keys in slot order into the first sort buffer; their number
-    // and key range by reductions (no shared counter on the insert path)
+    // by a scan (no shared counter on the insert path)
     constexpr int kPer = kRdSlots / kRdThreads;
     uint32_t c = 0;
-    unsigned long long lo_k = kEmpty, hi_k = 0;
 #pragma unroll
-    for (int q = 0; q < kPer; ++q) {
-      const uint64_t k = sh.tkey[threadIdx.x * kPer + q];
-      if (k != kEmpty) {
-        ++c;
-        lo_k = min(lo_k, (unsigned long long)k);
-        hi_k = max(hi_k, (unsigned long long)k);
-      }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      lo_k = min(lo_k, __shfl_xor_sync(0xffffffffu, lo_k, o));
-      hi_k = max(hi_k, __shfl_xor_sync(0xffffffffu, hi_k, o));
-    }
-    if (lane == 0) {
-      atomicMin(&sh.kmin, lo_k);
-      atomicMax(&sh.kmax, hi_k);
-    }
+    for (int q = 0; q < kPer; ++q) c += sh.tkey[threadIdx.x * kPer + q] != kEmpty;
     uint32_t d;
     uint32_t o = block_scan_u32<kRdThreads>(c, &d);
     if (sh.over || d >= uint32_t(a.cap)) {  // too many distinct keys for the shared path
@@ -1122,9 +1085,15 @@ __global__ void __launch_bounds__(kRdThreads, 2) sg_reduce_kernel(const __grid_c
 const int64_t* seq_tile_offsets(gt_grammar* g, const int32_t* head, const int32_t* tail, int kb, cudaStream_t s) {
   std::lock_guard<std::mutex> lk(g->seq_mu);
   if (g->seq_tile_off) {
-    GT_CUDA(cudaStreamWaitEvent(s, g->seq_tile_ev, 0));
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    GT_CUDA(cudaStreamIsCapturing(s, &cap));
+    if (cap == cudaStreamCaptureStatusNone) GT_CUDA(cudaStreamWaitEvent(s, g->seq_tile_ev, 0));
     return g->seq_tile_off;
   }
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  GT_CUDA(cudaStreamIsCapturing(s, &cap));
+  if (cap != cudaStreamCaptureStatusNone)  // they live as long as the grammar, not as a graph
+    fail(GT_EINVAL, "run the global sequence count once outside stream capture before capturing it");
   const int64_t nt = g->d.ntiles;
   auto* off = static_cast<int64_t*>(grammar_alloc(g, size_t(nt + 1) * 8, s));
   Buf cnt(g->ctx, size_t(nt + 1) * 8, s), sc(g->ctx, scan_scratch_bytes(nt + 1), s);
@@ -1173,8 +1142,7 @@ gt_result* run_sequence_count_global(gt_grammar* g, cudaStream_t s) {
   // rows: emitted in position order into (ke, ve), scattered by coarse bucket
   // into (ka, va), by fine bucket back into (ke, ve); (ka, va) is then the
   // reduction's scratch
-  const int64_t Up = (U + kScTile - 1) / kScTile * kScTile;  // the scatter reads whole aligned steps
-  Buf ke(ctx, size_t(Up) * 8, s), ve(ctx, size_t(Up) * 4, s), ka(ctx, size_t(U) * 8, s), va(ctx, size_t(U) * 4, s);
+  Buf ke(ctx, size_t(U) * 8, s), ve(ctx, size_t(U) * 4, s), ka(ctx, size_t(U) * 8, s), va(ctx, size_t(U) * 4, s);
   // fine bucket descriptors, then the look-back words, the ticket and the
   // number of fine buckets, cleared with one memset
   Buf fd(ctx, size_t(fmax) * 16, s), lb(ctx, size_t(fmax + 2) * 8, s);

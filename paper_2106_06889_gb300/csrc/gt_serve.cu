@@ -84,8 +84,12 @@ size_t query_footprint(const gt_grammar* g, int kind) {
       break;
     case GT_Q_INVERTED_INDEX:
     case GT_Q_TERM_VECTOR:
+    case GT_Q_TFIDF:
       b = 8 * F * nb * 16384 + 2400 * F * nb + 64 * double(g->fentry_bound) + 40 * double(g->fword_bound) +
           2 * double(d.root_len) + 40 * R + 24 * std::min(N, F * nb * 16384) + 16 * V;
+      break;
+    case GT_Q_COOCCURRENCE:  // the 3-word count, then two rows per distinct 3-gram sorted again
+      b = 2 * (160 * Gp + 32 * R);
       break;
     default:
       b = 160 * Gp + 32 * R;
@@ -239,7 +243,7 @@ GT_API gt_status gt_server_create(gt_ctx* ctx, int slots, size_t mem_budget, gt_
 GT_API gt_status gt_submit(gt_server* sv, const gt_query* q, int nq, uint64_t* ticket) {
   if (!sv || !q || nq < 1 || !ticket) return GT_EINVAL;
   for (int i = 0; i < nq; ++i)
-    if (!q[i].grammar || q[i].grammar->ctx != sv->ctx || q[i].kind < GT_Q_WORD_COUNT || q[i].kind > GT_Q_RANKED_INDEX)
+    if (!q[i].grammar || q[i].grammar->ctx != sv->ctx || q[i].kind < GT_Q_WORD_COUNT || q[i].kind > GT_Q_COOCCURRENCE)
       return GT_EINVAL;
   Request* r = new (std::nothrow) Request();
   if (!r) return GT_ENOMEM;

@@ -248,6 +248,7 @@ void launch_downsweep(const uint64_t* ka, uint64_t* kb, const void* va, void* vb
                       int64_t ntiles, const int64_t* offs, cudaStream_t s) {
   constexpr size_t smem = size_t(kRsTile) * (8 + VB);
   GT_CUDA(cudaFuncSetAttribute(radix_downsweep_kernel<VB>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+  Phase ph(t_call_ctx, "radix_pass", s);  // one span per scatter pass
   radix_downsweep_kernel<VB><<<unsigned(ntiles), kRsThreads, smem, s>>>(ka, kb, va, vb, n, shift, mask, offs);
   GT_LAUNCH_CHECK();
 }

@@ -140,3 +140,23 @@ def owned_windows(g):
             n += sum(1 for j in range(len(src) - 2) if src[j] != src[j + 2])
         out.append(n)
     return out
+
+
+def tfidf(g):
+    """Per file: (word, count * ln(F / df)) for its words, ascending word."""
+    import math
+    files, _ = expand_files(g)
+    F = len(files)
+    df = Counter(w for toks in files for w in set(toks))
+    return [[(w, c * math.log(F / df[w])) for w, c in sorted(Counter(toks).items())] for toks in files]
+
+
+def cooccurrence(g):
+    files, _ = expand_files(g)
+    c = Counter()
+    for t in files:
+        for i in range(len(t)):
+            for j in (i + 1, i + 2):
+                if j < len(t):
+                    c[(t[i] << 21) | t[j]] += 1
+    return sorted(c.items())

@@ -75,7 +75,13 @@ def test_null_arguments_are_rejected_before_any_device_call(so):
         "gt_inverted_index": (null, null, null),
         "gt_sequence_count": (null, 0, null, null),
         "gt_ranked_index": (null, 1, null, null),
+        "gt_tfidf": (null, null, null),
+        "gt_cooccurrence": (null, null, null),
         "gt_run_batch": (null, null, 0, null, null),
+        "gt_plan_create": (null, null, 1, null, null),
+        "gt_plan_launch": (null, null),
+        "gt_plan_result": (null, 0, null, null, null),
+        "gt_plan_destroy": (null,),
         "gt_result_view": (null, null, null, null),
         "gt_free_result": (null,),
         "gt_profile_enable": (null, 1),

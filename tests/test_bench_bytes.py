@@ -32,8 +32,9 @@ def test_kernel_bytes_count_only_the_methods_own_data():
     assert kb["expand_words"] == ("expand_words_kernel", 4 * 600)
     assert kb["wc_partition"] == ("wc_partition_kernel", 4 * 1000)
     kb = bench.kernel_bytes("nested_500m", INFO, OUT)
-    assert kb["seq_scatter"] == ("sg_scatter_kernel", 4 * 1000)
-    assert kb["seq_reduce"] == ("sg_reduce_kernel", 32 * 1100 + 16 * 700)
+    assert kb["radix_pass"] == ("radix_downsweep_kernel<4>", 24 * 1100)  # rows read and written once a pass
+    assert kb["seq_scatter"] == ("sg_scatter_kernel", 24 * 1100)
+    assert kb["seq_reduce"] == ("sg_reduce_kernel", 12 * 1100 + 16 * 700)
 
 
 def test_bucket_index_width_matches_the_launch_dispatch():

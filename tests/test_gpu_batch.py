@@ -64,3 +64,39 @@ def test_batch_rejects_bad_query(ctx):
     with pytest.raises(B.GtError):
         B.gt_run_batch(ctx, [(h, 99, 0, None)])
     B.gt_free_grammar(h)
+
+
+def test_plan_replays_the_batch(ctx):
+    """A batch captured as one CUDA graph (gt_plan): every launch gives the
+    oracle's results (word count into the caller's buffer, term vector,
+    inverted index, TF-IDF, sequence count, sort), launch after launch."""
+    import torch
+    m = make_corpus("multi64_50m", scale=0.004)
+    g = sequitur(m.tokens, m.file_lens, m.num_words)
+    gh = B.gt_load_grammar(ctx, g)
+    counts = torch.empty(g.num_words, dtype=torch.int64, device="cuda")
+    qs = [(gh, B.GT_Q_WORD_COUNT, 0, counts), (gh, B.GT_Q_TERM_VECTOR, 0, None), (gh, B.GT_Q_INVERTED_INDEX, 0, None),
+          (gh, B.GT_Q_TFIDF, 0, None), (gh, B.GT_Q_SEQUENCE_COUNT, 0, None), (gh, B.GT_Q_SORT, 1, None)]
+    p = B.gt_plan_create(ctx, qs)
+    try:
+        wc = oracle.word_count(g)
+        tv = oracle.term_vector(g, 0)
+        ii = oracle.inverted_index(g)
+        tf = oracle.tfidf(g)
+        sq = oracle.sequence_count(g, 0)
+        so = oracle.sort_words(g, 1)
+        for launch in range(3):
+            counts.fill_(-1)
+            B.gt_plan_launch(p)
+            assert np.array_equal(B.plan_result_numpy(p, 1, "word"), tv[1]), launch
+            assert np.array_equal(B.plan_result_numpy(p, 1, "count"), tv[2])
+            assert np.array_equal(B.plan_result_numpy(p, 2, "offsets"), ii[0])
+            assert np.array_equal(B.plan_result_numpy(p, 2, "file"), ii[1])
+            np.testing.assert_allclose(B.plan_result_numpy(p, 3, "tfidf"), tf[2], rtol=1e-15, atol=0)
+            assert np.array_equal(B.plan_result_numpy(p, 4, "key"), sq[0])
+            assert np.array_equal(B.plan_result_numpy(p, 4, "count"), sq[1])
+            assert np.array_equal(B.plan_result_numpy(p, 5, "word"), so[0])
+            assert np.array_equal(counts.cpu().numpy().astype(np.uint64), wc)
+    finally:
+        B.gt_plan_destroy(p)
+        B.gt_free_grammar(gh)

@@ -17,6 +17,7 @@ pytestmark = pytest.mark.gpu
 @pytest.fixture
 def ctx():
     c = B.gt_create(0)
+    B.gt_set_param(c, "seq_path", 2)  # the sample-sort bucket path
     yield c
     B.gt_destroy(c)
 
@@ -94,7 +95,7 @@ def test_same_as_sort_path(ctx):
     gh = B.gt_load_grammar(ctx, g)
     try:
         k1, c1 = run(gh)
-        B.gt_set_param(ctx, "seq_path", 1)
+        B.gt_set_param(ctx, "seq_path", 1)  # the radix-sort path
         k2, c2 = run(gh)
         assert np.array_equal(k1, k2) and np.array_equal(c1, c2)
         assert int(c1.sum(dtype=np.uint64)) == B.gt_grammar_info_get(gh)["num_tokens"] - 2

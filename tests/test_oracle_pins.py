@@ -111,6 +111,14 @@ def pin_brute(orc, g):
     assert [tuple(map(int, x)) for x in h] == bh
     assert [tuple(map(int, x)) for x in t] == bt
     assert list(map(int, orc.owned_windows(g))) == brute.owned_windows(g)
+    offs, w, v = orc.tfidf(g)
+    got = [list(zip(map(int, w[offs[f]:offs[f + 1]]), map(float, v[offs[f]:offs[f + 1]])))
+           for f in range(g.num_files)]
+    want = brute.tfidf(g)
+    assert [[x[0] for x in f] for f in got] == [[x[0] for x in f] for f in want]
+    np.testing.assert_allclose([x[1] for f in got for x in f], [x[1] for f in want for x in f], rtol=1e-15, atol=0)
+    k, c = orc.cooccurrence(g)
+    assert list(zip(map(int, k), map(int, c))) == brute.cooccurrence(g)
 
 
 def pin_source(orc, g, toks, lens):
@@ -141,6 +149,34 @@ def pin_closed_forms(orc, g, N_f):
     assert np.all(k[1:] > k[:-1])
     fr, kr, cr = orc.sequence_count(g, 1)
     assert int(cr.astype(np.int64).sum()) == int(cnt.astype(np.int64).sum())
+    # TF-IDF: a word in every file scores 0; one in a single file scores
+    # count * ln F; value / count is the same idf in every file of a word
+    to, tw, tv = orc.tfidf(g)
+    assert np.array_equal(to, offs) and np.array_equal(tw, w)
+    F = len(N_f)
+    df = np.bincount(w.astype(np.int64), minlength=g.num_words)
+    ratio = tv / c.astype(np.float64)
+    every = df[w] == F
+    assert np.all(tv[every] == 0.0)
+    single = df[w] == 1
+    np.testing.assert_allclose(tv[single], c[single].astype(np.float64) * np.log(F), rtol=1e-15)
+    first = np.full(g.num_words, np.nan)
+    first[w[::-1]] = ratio[::-1]  # the idf seen in the word's first file
+    np.testing.assert_allclose(ratio, first[w], rtol=1e-15)
+    # co-occurrence: pairs at distance 1 and 2 inside files; equal to the
+    # 3-word windows' (first, second) and (first, third) pairs plus the last
+    # pair of every file of two or more words
+    ck, cc = orc.cooccurrence(g)
+    assert int(cc.astype(np.int64).sum()) == int(sum(max(n - 1, 0) + max(n - 2, 0) for n in N_f))
+    m = np.uint64((1 << 21) - 1)
+    a, b3, c3 = kr >> np.uint64(42), (kr >> np.uint64(21)) & m, kr & m
+    files = orc.expand_files(g)
+    tails = [((np.uint64(t[-2]) << np.uint64(21)) | np.uint64(t[-1])) for t in files if t.shape[0] >= 2]
+    pk = np.concatenate([(a << np.uint64(21)) | b3, (a << np.uint64(21)) | c3, np.array(tails, np.uint64)])
+    pc = np.concatenate([cr, cr, np.ones(len(tails), np.uint64)]).astype(np.int64)
+    u, inv = np.unique(pk, return_inverse=True)
+    assert np.array_equal(u, ck) and np.array_equal(np.bincount(inv, weights=pc).astype(np.int64),
+                                                    cc.astype(np.int64))
 
 
 def pin_eq1(orc, g):
@@ -449,3 +485,32 @@ def test_key_file_counts_match_ranked_index(n):
         assert np.array_equal(c, np.concatenate(want_c)), name
         checked += 1
     assert checked >= 5
+
+
+def test_planted_idf_inverted():
+    def patch(m):
+        def tfidf_text(files):
+            offs, words, counts = m.term_vector_text(files)
+            df = np.bincount(words.astype(np.int64))
+            return offs, words, counts * np.log(df[words] / np.float64(len(files)))
+        m.tfidf_text = tfidf_text
+    assert _fails(lambda: _pins(broken_oracle(patch)))
+
+
+def test_planted_cooccurrence_misses_distance_two():
+    def patch(m):
+        def cooccurrence_text(files):
+            keys = [(np.asarray(t[:-1], np.uint64) << np.uint64(21)) | np.asarray(t[1:], np.uint64)
+                    for t in files if len(t) > 1]
+            k = np.concatenate(keys) if keys else np.zeros(0, np.uint64)
+            u, c = np.unique(k, return_counts=True)
+            return u, c.astype(np.uint64)
+        m.cooccurrence_text = cooccurrence_text
+    assert _fails(lambda: _pins(broken_oracle(patch)))
+
+
+def test_planted_cooccurrence_across_files():
+    def patch(m):
+        orig = m.cooccurrence_text
+        m.cooccurrence_text = lambda files: orig([np.concatenate(files)] if len(files) else files)
+    assert _fails(lambda: _pins(broken_oracle(patch)))
