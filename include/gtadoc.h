@@ -275,7 +275,11 @@ gt_status gt_plan_destroy(gt_plan* p);
  * footprint fits `mem_budget` bytes (0 = unlimited), groups the admitted
  * queries by grammar so that they share one traversal, and launches each
  * group on a free stream, so that groups overlap on the device.  Results of a
- * request are the same as those of gt_run_batch on the same queries.
+ * request are the same as those of gt_run_batch on the same queries.  The
+ * budget covers requests in flight; a completed request's results belong to
+ * the caller and stay allocated, outside the budget, until they are polled
+ * and freed, so a caller that submits much faster than it collects can still
+ * exhaust device memory.
  *   gt_submit: enqueue; *ticket identifies the request.  GT_EBUSY if the
  *     request's footprint alone exceeds the budget.  Word-count buffers must
  *     stay valid until the request completes.

@@ -869,6 +869,10 @@ GT_API gt_status gt_plan_launch(gt_plan* p, void* stream) {
     for (gt_result* r : p->res)
       if (r) r->ready = false;  // lengths are read again after this launch
     GT_CUDA(cudaGraphLaunch(p->exec, as_stream(stream)));
+    // a record made during capture only orders the captured work: the
+    // completion of each result is recorded here, after the replay
+    for (gt_result* r : p->res)
+      if (r) GT_CUDA(cudaEventRecord(r->done, as_stream(stream)));
     gt::g_launches.fetch_add(p->kernels);
     ++p->launches;
   });

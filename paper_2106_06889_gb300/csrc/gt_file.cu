@@ -229,8 +229,8 @@ struct Chunks {
 // to the chunk's own item range (one entry per word, so it always fits):
 // root words become their 14-bit index (uint16), rule words (index | weight
 // << 16) as uint64.  runs[c * nb + b] = (start, length) of bucket b's entries.
-template <bool kWeighted, int kBits>
-__global__ void __launch_bounds__(ChunkShape<kWeighted>::kThreads) chunk_sort_kernel(
+template <bool kWeighted>
+__global__ void __launch_bounds__(ChunkShape<kWeighted>::kThreads, kWeighted ? 4 : 2) chunk_sort_kernel(
     Chunks ch, const int32_t* __restrict__ items, const uint32_t* __restrict__ wts, int nb, int32_t V,
     void* __restrict__ out, int64_t* __restrict__ run_start, int32_t* __restrict__ run_len) {
   constexpr int kCsThreads = ChunkShape<kWeighted>::kThreads;
@@ -253,27 +253,11 @@ __global__ void __launch_bounds__(ChunkShape<kWeighted>::kThreads) chunk_sort_ke
       const int i = j * kCsThreads + tid;  // warp-contiguous: item order inside a warp is lane order
       w[j] = i < n ? items[base + i] : -1;
     }
-    // rank inside (warp, bucket): lanes with equal buckets found by one ballot
-    // per bucket bit; the lowest of them bumps the warp's counter once
-    const unsigned lt = (1u << lane) - 1u;
+    // rank inside (warp, bucket) by an atomic on the warp's own counter: the
+    // histograms that read the runs do not depend on the order inside a run
 #pragma unroll
-    for (int j = 0; j < kCsItems; ++j) {
-      const bool valid = uint32_t(w[j]) < uint32_t(V);
-      const uint32_t bk = valid ? uint32_t(w[j]) >> kFBLog2 : 0u;
-      unsigned peers = __ballot_sync(0xffffffffu, valid);
-#pragma unroll
-      for (int bit = 0; bit < kBits; ++bit) {
-        const bool on = (bk >> bit) & 1u;
-        const unsigned bal = __ballot_sync(0xffffffffu, on);
-        peers &= on ? bal : ~bal;
-      }
-      const uint32_t before = wcnt[warp][bk];
-      const uint32_t r = __popc(peers & lt);
-      rank[j] = before + r;
-      __syncwarp();
-      if (valid && r == 0) wcnt[warp][bk] = before + __popc(peers);
-      __syncwarp();
-    }
+    for (int j = 0; j < kCsItems; ++j)
+      if (uint32_t(w[j]) < uint32_t(V)) rank[j] = atomicAdd(&wcnt[warp][uint32_t(w[j]) >> kFBLog2], 1u);
     __syncthreads();
     // exclusive prefix over (bucket, warp): warp b0.. scans bucket b over the 16 warps
     for (int b = warp; b < nb; b += kCsWarps) {
@@ -334,31 +318,12 @@ __global__ void __launch_bounds__(ChunkShape<kWeighted>::kThreads) chunk_sort_ke
   }
 }
 
-// Launch the chunk sort with the bucket index width as a compile-time
-// constant (nb <= kMaxNb = 128 buckets: at most 7 bits), so the ranking's
-// per-bit ballots unroll.
 template <bool kWeighted>
 void launch_chunk_sort(unsigned grid, cudaStream_t s, const Chunks& ch, const int32_t* items, const uint32_t* wts,
                        int nb, int32_t V, void* out, int64_t* run_start, int32_t* run_len) {
-  const int nbits = nb > 1 ? 32 - __builtin_clz(unsigned(nb - 1)) : 0;
-  constexpr int kT = ChunkShape<kWeighted>::kThreads;
-#define GT_CHUNK_SORT_CASE(B)                                                                       \
-  case B:                                                                                           \
-    chunk_sort_kernel<kWeighted, B><<<grid, kT, 0, s>>>(ch, items, wts, nb, V, out, run_start, run_len); \
-    break;
-  switch (nbits) {
-    GT_CHUNK_SORT_CASE(0)
-    GT_CHUNK_SORT_CASE(1)
-    GT_CHUNK_SORT_CASE(2)
-    GT_CHUNK_SORT_CASE(3)
-    GT_CHUNK_SORT_CASE(4)
-    GT_CHUNK_SORT_CASE(5)
-    GT_CHUNK_SORT_CASE(6)
-    GT_CHUNK_SORT_CASE(7)
-    default:
-      fail(GT_EOVERFLOW, "more than 128 word buckets");
-  }
-#undef GT_CHUNK_SORT_CASE
+  if (nb > kMaxNb) fail(GT_EOVERFLOW, "more than 128 word buckets");
+  chunk_sort_kernel<kWeighted><<<grid, ChunkShape<kWeighted>::kThreads, 0, s>>>(ch, items, wts, nb, V, out, run_start,
+                                                                               run_len);
   GT_LAUNCH_CHECK();
 }
 

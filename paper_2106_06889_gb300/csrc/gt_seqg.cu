@@ -1,4 +1,7 @@
-// Global 3-word sequence count (l = 3, Section IV-C/D) by sample-sort buckets.
+// Global 3-word sequence count (l = 3, Section IV-C/D) by sample-sort buckets
+// (selected by the "seq_path" parameter; the default is the one-row-per-
+// window radix sort of gt_seq.cu, which measured faster on the 500M-token
+// corpus: the per-bucket sort below is bound by its instruction count).
 //
 // Every owned window (Eq. 1: the windows a rule's body crosses, built from
 // the body, a two-symbol look-ahead and the children's head/tail buffers; see
@@ -11,19 +14,22 @@
 //      sorted in one CTA; up to 1023 equally spaced sample keys become the
 //      bounds of the coarse buckets (sample sort, so a skewed - Zipf - key
 //      distribution still gives buckets of similar size);
-//   2. count: every CTA of a persistent grid counts its tiles' rows per coarse
-//      bucket; a scan gives each (bucket, CTA) its output range;
-//   3. scatter: a second pass over the grammar stages each tile's rows in
-//      shared memory in bucket order and writes them as runs;
+//   2. emit: every CTA of a persistent grid writes its tiles' windows as rows
+//      in position order (row offsets per tile are structure, built once per
+//      grammar) and counts them per coarse bucket; a scan gives each
+//      (bucket, CTA) its output range;
+//   3. scatter: each CTA re-reads its own rows, stages them in shared memory
+//      in bucket order and writes them as runs;
 //   4. fine split: one CTA per coarse bucket sorts a sample of its rows, cuts
 //      the bucket into fine buckets of about kFineRows rows, counts and
 //      scatters the rows into them (staged the same way);
 //   5. reduce: a persistent kernel takes the fine buckets in key order; a CTA
 //      sums the weights of equal keys in a shared-memory hash table (equal
 //      keys of a warp merged first with __match_any_sync, so a hot 3-gram is
-//      one update per warp), sorts the distinct keys in shared memory (LSD
-//      radix, 8-bit digits, ballot ranking) and writes them at the position a
-//      decoupled look-back over the preceding fine buckets gives.  A bucket
+//      one update per warp), sorts the distinct keys in shared memory (sample
+//      sort into 256 sub-buckets, finished by threads or warps) and writes
+//      them at the position a decoupled look-back over the preceding fine
+//      buckets gives.  A bucket
 //      with more distinct keys than the table holds is sorted in place in
 //      global memory by the same CTA instead (correct for any input; the
 //      sample makes it rare).
