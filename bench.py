@@ -132,22 +132,22 @@ def step_bytes(workload: str, info: dict, out: dict) -> int:
 
 def kernel_bytes(workload: str, info: dict, out: dict) -> dict:
     """Per timed single-kernel phase: (kernel, bytes of the method's own input
-    or output that kernel moves).  chunk_sort_kernel<0, bits>: the root
-    symbols it reads (4 B each); tv_hist_kernel: the term-vector pairs it
-    writes (12 B each); expand_words_kernel: the rule bodies it reads (4 B per
-    rule symbol); wc_partition_kernel and sg_scatter_kernel: the symbol stream
-    (4 B per body symbol).  On the 3-gram workload the rows of owned windows
+    or output that kernel moves).  chunk_sort_kernel<0>: the root symbols it
+    reads (4 B each); tv_hist_kernel: the term-vector pairs it writes (12 B
+    each); chunk_sort_kernel<1>: the per-file rule weights (4 B per (file,
+    rule) pair) and the rule bodies (4 B per rule symbol) it reads;
+    wc_partition_kernel and sg_scatter_kernel: the symbol stream (4 B per body
+    symbol).  On the 3-gram workload the rows of owned windows
     (8 B key + 4 B weight) stand in for the per-window table updates of the
     paper's sequence support (Section IV-D): radix_downsweep_kernel<4> and sg_scatter_kernel read and write
     every row once per launch (24 B), sg_reduce_kernel reads them (12 B) and
     writes the distinct 3-grams (16 B each)."""
     G, V = info["num_syms"], info["num_words"]
     root_len = out["root_len"]
-    nb = (V + 16383) // 16384
     if workload == "multi64_50m":
-        return {"chunk_sort_root": (f"chunk_sort_kernel<0, {max(nb - 1, 0).bit_length()}>", 4 * root_len),
+        return {"chunk_sort_root": ("chunk_sort_kernel<0>", 4 * root_len),
                 "tv_hist_kernel": ("tv_hist_kernel", 12 * out["tv_pairs"]),
-                "expand_words": ("expand_words_kernel", 4 * (G - root_len)),
+                "chunk_sort_rules": ("chunk_sort_kernel<1>", 4 * info["file_pairs"] + 4 * (G - root_len)),
                 "wc_partition": ("wc_partition_kernel", 4 * G)}
     U = info["owned_windows"]
     return {"radix_pass": ("radix_downsweep_kernel<4>", 24 * U),
@@ -156,7 +156,7 @@ def kernel_bytes(workload: str, info: dict, out: dict) -> dict:
             "wc_partition": ("wc_partition_kernel", 4 * G)}
 
 
-PHASES = ("weights", "wc_partition", "wc_hist", "sort_canon", "file_weights", "expand_words", "tv_hist",
+PHASES = ("weights", "wc_partition", "wc_hist", "sort_canon", "file_weights", "tv_hist", "weigh_entries",
           "chunk_sort_root", "chunk_sort_rules", "tv_hist_kernel", "tv_out", "ii_out", "wc_from_files",
           "seq_headtail", "seq_emit", "seq_sort", "radix_pass", "seq_part", "seq_scatter", "seq_fine", "seq_reduce",
           "tv_out", "cooc_rows", "rows_sort")
@@ -260,7 +260,8 @@ def load_timed(B, ctx, g, stream, reps=2):
     return gh, load, pinned, HostG
 
 
-def measure(B, ctx, workload, g, steps, warmup, world, stream, autotune=True, e2e_steps=3, clocks=True):
+def measure(B, ctx, workload, g, steps, warmup, world, stream, autotune=True, e2e_steps=3, clocks=True,
+            eager=False):
     """Device-timed steps of one workload on a resident grammar, with its
     step-level and dominant-kernel rooflines, phases, load time and the
     end-to-end figure through the public API from host buffers."""
@@ -292,6 +293,22 @@ def measure(B, ctx, workload, g, steps, warmup, world, stream, autotune=True, e2
         for r in keep:
             B.gt_free_result(r)
         keep.clear()
+        # ---- the timed step: the batch captured once as a CUDA graph
+        # (gt_plan_create) and replayed, one graph launch per step; every
+        # launch recomputes every result from the grammar ----
+        # (eager: the timed loop launches kernel by kernel instead, for
+        # profilers that replay single kernels)
+        plan = None if eager else B.gt_plan_create(ctx, qs, stream)
+
+        def step():
+            if plan is None:
+                run_step(B, ctx, qs, stream, keep)
+            else:
+                B.gt_plan_launch(plan, stream)
+
+        for _ in range(max(warmup, 3)):
+            step()
+        torch.cuda.synchronize()
         launches0 = B.gt_kernel_launches()
         barrier()
         torch.cuda.synchronize()
@@ -300,13 +317,30 @@ def measure(B, ctx, workload, g, steps, warmup, world, stream, autotune=True, e2
         torch.cuda.nvtx.range_push("timed_steps")  # lets a profiler select the timed launches
         ev0.record(stream)
         for _ in range(steps):
-            run_step(B, ctx, qs, stream, keep)
+            step()
         ev1.record(stream)
         torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
         barrier()
         clk = sampler.stop() if sampler else None
         launches = B.gt_kernel_launches() - launches0
+        if plan is not None:
+            B.gt_plan_destroy(plan)
+        for r in keep:
+            B.gt_free_result(r)
+        keep.clear()
+        # ---- the same step launched kernel by kernel (gt_run_batch) ----
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = B.gt_kernel_launches()
+        barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(steps):
+            run_step(B, ctx, qs, stream, keep)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        eager_launches = B.gt_kernel_launches() - l0
         for r in keep:
             B.gt_free_result(r)
         keep.clear()
@@ -323,27 +357,10 @@ def measure(B, ctx, workload, g, steps, warmup, world, stream, autotune=True, e2
         keep.clear()
     ms = max_over_ranks(ev0.elapsed_time(ev1), world)
     ms_step = ms / steps
-    # ---- the same step as one graph launch (gt_plan: the batch captured once) ----
-    graph_step = None
-    try:
-        plan = B.gt_plan_create(ctx, qs, stream)
-        with torch.cuda.stream(stream):
-            for _ in range(3):
-                B.gt_plan_launch(plan, stream)
-            torch.cuda.synchronize()
-            g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            l0 = B.gt_kernel_launches()
-            g0.record(stream)
-            for _ in range(steps):
-                B.gt_plan_launch(plan, stream)
-            g1.record(stream)
-            torch.cuda.synchronize()
-        gms = max_over_ranks(g0.elapsed_time(g1), world) / steps
-        graph_step = {"ms_per_step": gms, "value": job_throughput(world, N, 1, gms / 1e3), "unit": "tokens/s",
-                      "kernels_per_launch": (B.gt_kernel_launches() - l0) // steps, "graph_launches_per_step": 1}
-        B.gt_plan_destroy(plan)
-    except B.GtError as e:
-        graph_step = {"error": str(e)}
+    ems = max_over_ranks(e0.elapsed_time(e1), world) / steps
+    eager_step = {"ms_per_step": ems, "value": job_throughput(world, N, 1, ems / 1e3), "unit": "tokens/s",
+                  "kernels_per_step": eager_launches // steps,
+                  "note": "gt_run_batch per step: the same kernels launched one by one from the host"}
     phases = {}
     for ph in PHASES:
         tot, spans, la = B.gt_profile_read(ctx, ph)
@@ -405,7 +422,7 @@ def measure(B, ctx, workload, g, steps, warmup, world, stream, autotune=True, e2
     B.gt_free_grammar(gh)
     return {"value": job_throughput(world, N, steps, ms / 1e3), "ms_per_step": ms_step, "tokens": N,
             "info": info, "outputs": outs, "roofline": roofline, "phases": phases, "load": load, "e2e": e2e,
-            "gpu_launches": launches, "clocks": clk, "autotune": tune, "graph_step": graph_step}
+            "gpu_launches": launches, "clocks": clk, "autotune": tune, "eager_step": eager_step}
 
 
 # ---------------------------------------------------------------------------
@@ -622,13 +639,15 @@ def many_files(B, ctx, reps=3):
 
 def sequence_paths(B, ctx, g, stream, reps=3):
     """The global 3-word count by the one-row-per-window LSD radix sort (the
-    default) and by the sample-sort buckets, on the same grammar."""
+    default, with scatter tiles of 2048 and of 4096 keys) and by the
+    sample-sort buckets, on the same grammar."""
     import torch
     gh = B.gt_load_grammar(ctx, g, stream)
     out = {}
     with torch.cuda.stream(stream):
-        for name, path in (("bucketed", 2), ("radix_sort", 1)):
+        for name, path, items in (("bucketed", 2, 8), ("radix_sort_tile4096", 1, 16), ("radix_sort", 1, 8)):
             B.gt_set_param(ctx, "seq_path", path)
+            B.gt_set_param(ctx, "radix_items", items)
             B.gt_free_result(B.gt_sequence_count(gh, 0, stream))
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             keep = []
@@ -805,6 +824,13 @@ def cpu_baselines(g, analytics, budget_s=20.0):
 # main
 # ---------------------------------------------------------------------------
 
+def workload_config(args, g) -> dict:
+    """The line's config: what the workload is (both arms print the same)."""
+    wl = WORKLOADS[args.workload]
+    return {"workload": args.workload, "analytics": wl["analytics"], "desc": wl["desc"], "scale": args.scale,
+            "l2": f"inputs larger than L2 (symbol array {4 * len(g.sym) / 1e6:.0f} MB > 129 MB)"}
+
+
 def reference_arm(args, rank):
     """The oracle as it stands, one core, a bounded sample of the workload per
     step (rank 0 only)."""
@@ -812,7 +838,7 @@ def reference_arm(args, rank):
     if rank != 0:
         return
     wl = WORKLOADS[args.workload]
-    g, _ = load_config(args.workload)
+    g, _ = load_config(args.workload, scale=args.scale)
     runs = []
     for i in range(args.warmup + args.steps):
         r = oracle_sample(g, wl["analytics"], budget_s=4.0)
@@ -823,8 +849,7 @@ def reference_arm(args, rank):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "tokens/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * s[3],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
-            "data": "synthetic", "config": {"workload": args.workload, "analytics": wl["analytics"],
-                                            "desc": wl["desc"]},
+            "data": "synthetic", "config": workload_config(args, g),
             "cpu_baseline": {"value": v, "unit": "tokens/s", "cores": 1, "kind": "oracle", "nproc": os.cpu_count(),
                              "sample": f"{' + '.join(wl['analytics'])} on {s[1]} ({s[2]} tokens) per step"},
             "e2e": {"value": v, "unit": "tokens/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -836,7 +861,7 @@ def workload_summary(m: dict) -> dict:
     info = m["info"]
     return {"value": m["value"], "unit": "tokens/s", "ms_per_step": m["ms_per_step"],
             "roofline": m["roofline"], "phases": m["phases"], "load_ms": m["load"], "e2e": m["e2e"],
-            "gpu_launches": m["gpu_launches"], "outputs": m["outputs"], "graph_step": m["graph_step"],
+            "gpu_launches": m["gpu_launches"], "outputs": m["outputs"], "eager_step": m["eager_step"],
             "grammar": {k: info[k] for k in ("num_tokens", "num_syms", "num_rules", "num_files", "num_edges",
                                              "depth", "owned_windows", "file_pairs")}}
 
@@ -854,6 +879,8 @@ def main():
     ap.add_argument("--no-c3", action="store_true", help="skip the 500M-token 3-gram workload in the extras")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving (p50/p99) measurement")
     ap.add_argument("--no-autotune", action="store_true", help="time the default launch configuration")
+    ap.add_argument("--eager", action="store_true",
+                    help="time the step launched kernel by kernel instead of as one graph (profiling captures)")
     ap.add_argument("--scale", type=float, default=1.0,
                     help="corpus scale for profiling captures of a smaller case (1.0 = the workload as stated)")
     args = ap.parse_args()
@@ -876,7 +903,8 @@ def main():
     ctx = B.gt_create(local)
     stream = torch.cuda.Stream()
     m = measure(B, ctx, args.workload, g, args.steps, args.warmup, world, stream,
-                autotune=not args.no_autotune, e2e_steps=0 if args.no_e2e else max(2, min(args.steps, 5)))
+                autotune=not args.no_autotune, e2e_steps=0 if args.no_e2e else max(2, min(args.steps, 5)),
+                eager=args.eager)
     extras = {}
 
     def fresh(fn):
@@ -939,14 +967,14 @@ def main():
         line = {"metric": METRIC, "value": m["value"], "unit": "tokens/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": m["ms_per_step"], "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-                "config": {"workload": args.workload, "analytics": wl["analytics"], "desc": wl["desc"],
-                           "scale": args.scale,
-                           "tokens": m["tokens"], "grammar_symbols": info["num_syms"], "rules": info["num_rules"],
-                           "files": info["num_files"],
-                           "l2": f"inputs larger than L2 (symbol array {4 * info['num_syms'] / 1e6:.0f} MB > 129 MB)",
-                           "autotune": m["autotune"]},
+                "config": workload_config(args, g),
+                "execution": "gt_plan: the step's batch captured once as a CUDA graph, one graph launch per "
+                             "step recomputing every result (eager_step: the same batch by gt_run_batch)",
+                "grammar": {"tokens": m["tokens"], "grammar_symbols": info["num_syms"], "rules": info["num_rules"],
+                            "files": info["num_files"]},
+                "autotune": m["autotune"],
                 "roofline": m["roofline"], "load_ms": m["load"], "phases": m["phases"], "outputs": m["outputs"],
-                "graph_step": m["graph_step"],
+                "eager_step": m["eager_step"],
                 "extras": extras, "serving": serving, "cpu_baseline": cpu, "e2e": m["e2e"],
                 "gpu_launches": m["gpu_launches"], "clocks": m["clocks"]}
         print(json.dumps(line))

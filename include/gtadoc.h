@@ -345,6 +345,10 @@ int64_t gt_kernel_launches(void);
  *   "seq_table_cap" distinct keys a bucket may hold in shared memory on the
  *                   bucket path (2..3072, default 3072); fuller buckets are
  *                   sorted in global memory.
+ *   "radix_items"   keys per thread of the LSD radix sort's scatter passes:
+ *                   8 (default, tiles of 2048 keys) or 16 (tiles of 4096:
+ *                   longer runs per digit in each tile's writes); GT_EINVAL
+ *                   otherwise.  Same results.
  *   "file_strategy" per-file analytics (term vector, inverted index, per-file
  *                   sequence count, ranked index): 0 (default) picks top-down
  *                   for at most 64 files and bottom-up otherwise (the paper's

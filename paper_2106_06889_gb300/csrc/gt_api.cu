@@ -226,13 +226,15 @@ GT_API gt_status gt_load_grammar(gt_ctx* ctx, const gt_grammar_desc* desc, void*
     d.F = F;
     d.G = G;
     d.root_len = root_len;
-    // symbols padded to whole tiles with -1 (never a word, never a rule);
-    // uploads go straight from the caller's arrays (DMA when they are pinned)
+    // symbols padded to whole tiles, plus 16 bytes, with -1 (never a word,
+    // never a rule): a 16-byte vector load that starts at a symbol stays in
+    // the array; uploads go straight from the caller's arrays (DMA when they
+    // are pinned)
     const cudaMemcpyKind up = desc->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     auto upload_phase = std::make_unique<gt::Phase>(ctx, "load_upload", s);
-    const int64_t Gp = std::max<int64_t>((G + gt::kTile - 1) / gt::kTile, 1) * gt::kTile;
+    const int64_t Gp = std::max<int64_t>((G + gt::kTile - 1) / gt::kTile, 1) * gt::kTile + 4;
     void* p = gt::grammar_alloc(g, size_t(Gp) * 4, s);
-    if (Gp > G) GT_CUDA(cudaMemsetAsync(static_cast<int32_t*>(p) + G, 0xff, size_t(Gp - G) * 4, s));
+    GT_CUDA(cudaMemsetAsync(static_cast<int32_t*>(p) + G, 0xff, size_t(Gp - G) * 4, s));
     if (G > 0) GT_CUDA(cudaMemcpyAsync(p, desc->sym, size_t(G) * 4, up, s));
     d.sym = static_cast<int32_t*>(p);
     p = gt::grammar_alloc(g, size_t(R + 1) * 8, s);
@@ -247,9 +249,9 @@ GT_API gt_status gt_load_grammar(gt_ctx* ctx, const gt_grammar_desc* desc, void*
       std::vector<int32_t> cl;
       for (int32_t f = 0; f < F; ++f) {
         cf[f] = int64_t(cs.size());
-        for (int64_t q = foff[f]; q < foff[f + 1]; q += gt::kFileChunk) {
+        for (int64_t q = foff[f]; q < foff[f + 1]; q += gt::kRootChunk) {
           cs.push_back(q);
-          cl.push_back(int32_t(std::min<int64_t>(gt::kFileChunk, foff[f + 1] - q)));
+          cl.push_back(int32_t(std::min<int64_t>(gt::kRootChunk, foff[f + 1] - q)));
         }
       }
       const int64_t nc = int64_t(cs.size());
@@ -773,7 +775,11 @@ GT_API int64_t gt_kernel_launches(void) { return gt::g_launches.load(); }
 GT_API gt_status gt_set_param(gt_ctx* ctx, const char* name, int64_t value) {
   if (!ctx || !name) return GT_EINVAL;
   static const char* known[] = {"wc_aggregate", "use_graphs", "file_strategy", "wc_slices", "bu_local", "seq_path",
-                                "seq_table_cap"};
+                                "seq_table_cap", "radix_items"};
+  if (std::strcmp(name, "radix_items") == 0 && value != 8 && value != 16) {
+    ctx->last_error = "radix_items must be 8 or 16";
+    return GT_EINVAL;
+  }
   for (const char* k : known)
     if (std::strcmp(k, name) == 0) {
       ctx->params[name] = value;

@@ -63,11 +63,6 @@ __global__ void fmask_edges_kernel(const int32_t* __restrict__ lchild, const int
   }
 }
 
-__global__ void popc_kernel(const unsigned long long* __restrict__ mask, int32_t R, int64_t* __restrict__ cnt) {
-  for (int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; r < R; r += int64_t(gridDim.x) * blockDim.x)
-    cnt[r] = r == 0 ? 0 : __popcll(mask[r]);
-}
-
 __global__ void mask_totals_kernel(const unsigned long long* __restrict__ mask, const int32_t* __restrict__ W,
                                    const int32_t* __restrict__ S, int32_t R, unsigned long long* __restrict__ out) {
   unsigned long long a = 0, x = 0, y = 0;
@@ -89,65 +84,239 @@ __global__ void mask_totals_kernel(const unsigned long long* __restrict__ mask, 
   }
 }
 
-// The root's per-file references give the first part of every weight.
-__global__ void fweight_root_kernel(const int64_t* __restrict__ rfile_off, const int32_t* __restrict__ rfile_f,
-                                    const uint32_t* __restrict__ rfile_m, int32_t R, const int64_t* __restrict__ off,
-                                    const unsigned long long* __restrict__ mask, uint32_t* __restrict__ w) {
-  for (int64_t c = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; c < R; c += int64_t(gridDim.x) * blockDim.x) {
-    const int64_t e1 = rfile_off[c + 1];
-    const int64_t o = off[c];
-    const unsigned long long cm = mask[c];
-#pragma unroll 4
-    for (int64_t e = rfile_off[c]; e < e1; ++e)
-      w[o + __popcll(cm & ((1ull << rfile_f[e]) - 1ull))] = rfile_m[e];
+// Per-file weights are computed level by level from a structure built at
+// load: every (rule, file) slot has a row listing, for each non-root parent
+// p of the rule that holds the file, p's slot for that file and the edge's
+// multiplicity.  A level pass then computes, per slot, its starting value (the
+// root's references of that file, copied in) plus the sum of mult times the
+// parent slots' weights (parents are on lower levels, so their weights are
+// final).  A rule with few parent edges ("light": at most kHeavyParents, the
+// root's included) has rows of at most that many entries and gets one thread
+// per slot; the rows of a "heavy" rule (a frequent digram used by up to
+// thousands of rules) are summed by a warp each.
+constexpr int kHeavyParents = 4;
+
+__device__ __forceinline__ bool heavy_rule(const int64_t* __restrict__ pedge_off, int32_t r) {
+  return r != 0 && pedge_off[r + 1] - pedge_off[r] > kHeavyParents;
+}
+
+// Slot layout: the light rules' slots level by level (rules in level order,
+// each rule's files ascending), then the heavy rules' slots, also level by
+// level, so that the slots of one class and level are contiguous.  cnt[k] =
+// slots of the k-th rule in level order of the selected class.
+__global__ void level_popc_kernel(const int32_t* __restrict__ lvl_order, const unsigned long long* __restrict__ mask,
+                                  const int64_t* __restrict__ pedge_off, int32_t R, int64_t* __restrict__ cnt_light,
+                                  int64_t* __restrict__ cnt_heavy) {
+  for (int64_t k = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; k < R; k += int64_t(gridDim.x) * blockDim.x) {
+    const int32_t r = lvl_order[k];
+    const int64_t n = r == 0 ? 0 : __popcll(mask[r]);
+    const bool h = heavy_rule(pedge_off, r);
+    cnt_light[k] = h ? 0 : n;
+    cnt_heavy[k] = h ? n : 0;
   }
 }
 
-// One level: every non-root parent edge adds mult * (parent's weight in file f)
-// to the child's slot for f.
-__global__ void fweight_edges_kernel(const int32_t* __restrict__ lchild, const int32_t* __restrict__ lpar,
-                                     const uint32_t* __restrict__ lmult, int64_t a, int64_t b,
-                                     const int64_t* __restrict__ off, const unsigned long long* __restrict__ mask,
-                                     uint32_t* __restrict__ w) {
-  for (int64_t i = a + blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < b; i += int64_t(gridDim.x) * blockDim.x) {
-    const int32_t p = lpar[i];
-    if (p == 0) continue;
-    const int32_t c = lchild[i];
-    const uint32_t m = lmult[i];
-    unsigned long long pm = mask[p];
+// off[r] from the scans (heavy slots after all light ones) and the owner
+// (rule, file) of every slot.
+__global__ void slot_owner_kernel(const int32_t* __restrict__ lvl_order, const int64_t* __restrict__ scan_light,
+                                  const int64_t* __restrict__ scan_heavy, const int64_t* __restrict__ n_light,
+                                  const unsigned long long* __restrict__ mask, const int64_t* __restrict__ pedge_off,
+                                  int32_t R, int64_t* __restrict__ off, int32_t* __restrict__ slot_rule,
+                                  uint8_t* __restrict__ slot_file) {
+  const int64_t nl = *n_light;
+  for (int64_t k = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; k < R; k += int64_t(gridDim.x) * blockDim.x) {
+    const int32_t r = lvl_order[k];
+    int64_t o = heavy_rule(pedge_off, r) ? nl + scan_heavy[k] : scan_light[k];
+    off[r] = o;
+    unsigned long long m = r == 0 ? 0ull : mask[r];
+    while (m) {
+      const int f = __ffsll(m) - 1;
+      m &= m - 1;
+      slot_rule[o] = r;
+      slot_file[o] = uint8_t(f);
+      ++o;
+    }
+  }
+}
+
+// Per level l: first light slot lvl_slot[l] = scan_light[lvl_off[l]] and
+// first heavy slot lvl_heavy[l] = n_light + scan_heavy[lvl_off[l]]; index
+// depth holds the ends.
+__global__ void level_slot_off_kernel(const int64_t* __restrict__ lvl_off, int32_t depth,
+                                      const int64_t* __restrict__ scan_light, const int64_t* __restrict__ scan_heavy,
+                                      const int64_t* __restrict__ n, int32_t R, int64_t* __restrict__ lvl_slot,
+                                      int64_t* __restrict__ lvl_heavy) {
+  for (int l = threadIdx.x; l <= depth; l += blockDim.x) {
+    lvl_slot[l] = lvl_off[l] < R ? scan_light[lvl_off[l]] : n[0];
+    lvl_heavy[l] = n[0] + (lvl_off[l] < R ? scan_heavy[lvl_off[l]] : n[1]);
+  }
+}
+
+// Rows, edge-parallel over the non-root parent edges p -> c: every file f
+// of p gets an entry (p's slot for f, mult) in the row of c's slot for f.
+// With fill == false only the row lengths are counted; with fill == true the
+// entries are placed (their order inside a row is whatever the atomics give:
+// the row is a sum of integers).
+template <bool kFill>
+__global__ void slot_rows_kernel(const int32_t* __restrict__ lchild, const int32_t* __restrict__ lpar,
+                                 const uint32_t* __restrict__ lmult, int64_t E, const int64_t* __restrict__ off,
+                                 const unsigned long long* __restrict__ mask, uint32_t* __restrict__ cnt,
+                                 const int64_t* __restrict__ row_off, uint2* __restrict__ entries) {
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < E; e += int64_t(gridDim.x) * blockDim.x) {
+    const int32_t p = lpar[e];
+    if (p == 0) continue;  // the root's references are the starting values
+    const int32_t c = lchild[e];
     const unsigned long long cm = mask[c];
+    unsigned long long pm = mask[p];
     const int64_t po = off[p], co = off[c];
-    int k = 0;
-    while (pm) {  // 4 files at a time: their parent weights are loaded together
-      int f[4];
+    for (int k = 0; pm; ++k) {
+      const int f = __ffsll(pm) - 1;
+      pm &= pm - 1;
+      const int64_t slot = co + __popcll(cm & ((1ull << f) - 1ull));
+      const uint32_t at = atomicAdd(&cnt[slot], 1u);
+      if (kFill) entries[row_off[slot] + at] = make_uint2(uint32_t(po + k), lmult[e]);
+    }
+  }
+}
+
+__global__ void widen_u32_kernel(const uint32_t* __restrict__ x, int64_t n, int64_t* __restrict__ y) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    y[i] = x[i];
+}
+
+__global__ void narrow_off_kernel(const int64_t* __restrict__ x, int64_t n, uint32_t* __restrict__ y) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i <= n; i += int64_t(gridDim.x) * blockDim.x)
+    y[i] = uint32_t(x[i]);
+}
+
+
+struct WeightRows {
+  const uint32_t* row_off;  // [slots + 1]
+  const uint2* entries;     // (parent slot, mult)
+  const uint4* pieces;      // heavy rows cut into pieces: (slot, first entry, end entry, 0)
+};
+
+// Heavy rows are cut into pieces of at most kPieceEntries entries, one warp
+// each, so that a rule with thousands of parents does not set the length of
+// its level's pass; the pieces of a slot add their sums atomically.
+constexpr uint32_t kPieceEntries = 128;
+
+// At load: pieces of the heavy slots [h0, h1) (counted with fill == false).
+template <bool kFill>
+__global__ void row_pieces_kernel(const uint32_t* __restrict__ row_off, int64_t h0, int64_t h1,
+                                  int64_t* __restrict__ cnt, const int64_t* __restrict__ pscan,
+                                  uint4* __restrict__ pieces) {
+  for (int64_t i = h0 + blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < h1; i += int64_t(gridDim.x) * blockDim.x) {
+    const uint32_t r0 = row_off[i], r1 = row_off[i + 1];
+    const int64_t np = (int64_t(r1 - r0) + kPieceEntries - 1) / kPieceEntries;
+    if (!kFill) {
+      cnt[i - h0] = np;
+      continue;
+    }
+    int64_t o = pscan[i - h0];
+    for (uint32_t e = r0; e < r1; e += kPieceEntries, ++o)
+      pieces[o] = make_uint4(uint32_t(i), e, min(e + kPieceEntries, r1), 0u);
+  }
+}
+
+// At load: the root's references in the slot layout, w0[slot (c, f)] = how
+// often the root of file f references rule c (0 if it does not): the
+// starting value of every per-file weight.
+__global__ void root_slots_kernel(const int64_t* __restrict__ rfile_off, const int32_t* __restrict__ rfile_f,
+                                  const uint32_t* __restrict__ rfile_m, int32_t R, const int64_t* __restrict__ off,
+                                  const unsigned long long* __restrict__ mask, uint32_t* __restrict__ w0) {
+  for (int64_t c = 1 + blockIdx.x * int64_t(blockDim.x) + threadIdx.x; c < R; c += int64_t(gridDim.x) * blockDim.x) {
+    const unsigned long long cm = mask[c];
+    const int64_t o = off[c];
+    for (int64_t e = rfile_off[c]; e < rfile_off[c + 1]; ++e)
+      w0[o + __popcll(cm & ((1ull << rfile_f[e]) - 1ull))] = rfile_m[e];
+  }
+}
+
+// One level: blocks [0, light_blocks) take the light slots [a, b), one
+// thread per slot (rows of at most kHeavyParents entries, all loads issued
+// together); the other blocks take the pieces [ha, hb) of the heavy slots'
+// rows, one warp per piece.  Every slot already holds the root's references
+// of its file.
+__global__ void __launch_bounds__(256) fweight_level_kernel(WeightRows L, int64_t a, int64_t b, int light_blocks,
+                                                            int64_t ha, int64_t hb, uint32_t* __restrict__ w) {
+  if (int(blockIdx.x) < light_blocks) {
+    for (int64_t i = a + blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < b;
+         i += int64_t(light_blocks) * blockDim.x) {
+      const uint32_t r0 = L.row_off[i], n = L.row_off[i + 1] - r0;  // <= kHeavyParents
+      if (n == 0) continue;
+      uint2 en[kHeavyParents];
+#pragma unroll
+      for (int k = 0; k < kHeavyParents; ++k) en[k] = k < int(n) ? L.entries[r0 + k] : make_uint2(0u, 0u);
+      uint32_t x[kHeavyParents];
+#pragma unroll
+      for (int k = 0; k < kHeavyParents; ++k) x[k] = k < int(n) ? w[en[k].x] : 0u;
+      uint32_t v = w[i];
+#pragma unroll
+      for (int k = 0; k < kHeavyParents; ++k) v += en[k].y * x[k];
+      w[i] = v;
+    }
+    return;
+  }
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = int64_t(int(gridDim.x) - light_blocks) * (blockDim.x >> 5);
+  for (int64_t q = ha + (int64_t(int(blockIdx.x) - light_blocks) * blockDim.x + threadIdx.x) / 32; q < hb;
+       q += nwarps) {
+    const uint4 pc = L.pieces[q];
+    uint32_t v = 0;
+    for (uint32_t e0 = pc.y; e0 < pc.z; e0 += 4 * 32) {  // four entries per lane in flight
+      uint2 en[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        f[u] = pm ? __ffsll(pm) - 1 : -1;
-        pm &= pm - 1;
+        const uint32_t e = e0 + u * 32 + lane;
+        en[u] = e < pc.z ? L.entries[e] : make_uint2(0u, 0u);
       }
-      uint32_t pw[4];
+      uint32_t x[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) pw[u] = f[u] >= 0 ? w[po + k + u] : 0u;
+      for (int u = 0; u < 4; ++u) x[u] = en[u].y ? w[en[u].x] : 0u;
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
-        if (f[u] >= 0) atomicAdd(&w[co + __popcll(cm & ((1ull << f[u]) - 1ull))], m * pw[u]);
-      k += 4;
+      for (int u = 0; u < 4; ++u) v += en[u].y * x[u];
     }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0 && v) atomicAdd(&w[pc.x], v);
   }
 }
 
 // (file << 32 | rule) keys of every (rule, file) slot, rule-major.
+// Pairs of rules without words of their own get file F: sorted after every
+// file's pairs, they stay out of the rule-word chunks.
 __global__ void fentry_keys_kernel(const unsigned long long* __restrict__ mask, const int64_t* __restrict__ off,
-                                   int32_t R, uint64_t* __restrict__ keys) {
+                                   const int32_t* __restrict__ W, int32_t R, int32_t F, uint64_t* __restrict__ keys) {
   for (int64_t r = 1 + blockIdx.x * int64_t(blockDim.x) + threadIdx.x; r < R; r += int64_t(gridDim.x) * blockDim.x) {
     unsigned long long m = mask[r];
     int64_t o = off[r];
+    const bool none = W[r] == 0;
     while (m) {
       const int f = __ffsll(m) - 1;
       m &= m - 1;
-      keys[o++] = (uint64_t(f) << 32) | uint64_t(r);
+      keys[o++] = (uint64_t(none ? F : f) << 32) | uint64_t(r);
     }
   }
+}
+
+// The rules' own words, rule after rule (the root's excluded): rule r's are
+// rule_words[woff[r], woff[r] + W_r).  They are at most N < 2^32.
+__global__ void rule_words_kernel(DevGrammar d, const int64_t* __restrict__ woff64, uint32_t* __restrict__ woff,
+                                  int32_t* __restrict__ rule_words) {
+  for (int64_t r = 1 + blockIdx.x * int64_t(blockDim.x) + threadIdx.x; r < d.R; r += int64_t(gridDim.x) * blockDim.x) {
+    int64_t o = woff64[r];
+    woff[r] = uint32_t(o);
+    for (int64_t j = d.rule_off[r]; j < d.rule_off[r + 1]; ++j) {
+      const int32_t sy = d.sym[j];
+      if (sy < d.V) rule_words[o++] = sy;
+    }
+  }
+}
+
+__global__ void rule_word_counts_kernel(const int32_t* __restrict__ W, int32_t R, int64_t* __restrict__ cnt) {
+  for (int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; r < R; r += int64_t(gridDim.x) * blockDim.x)
+    cnt[r] = r == 0 ? 0 : W[r];
 }
 
 __global__ void entry_words_kernel(const uint64_t* __restrict__ keys, int64_t n, const int32_t* __restrict__ W,
@@ -156,35 +325,9 @@ __global__ void entry_words_kernel(const uint64_t* __restrict__ keys, int64_t n,
     cnt[i] = int32_t(keys[i] >> 32) < F ? W[uint32_t(keys[i])] : 0;
 }
 
-// Each (file, rule) entry writes the rule's own words with the entry's weight.
-__global__ void expand_words_kernel(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ wts, int64_t n,
-                                    const int64_t* __restrict__ pos, DevGrammar d, int32_t* __restrict__ xw,
-                                    uint32_t* __restrict__ xwt) {
-  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
-    if (int32_t(keys[i] >> 32) >= d.F) continue;  // padding
-    const int32_t r = int32_t(uint32_t(keys[i]));
-    const uint32_t wt = wts[i];
-    int64_t o = pos[i];
-    for (int64_t j = d.rule_off[r]; j < d.rule_off[r + 1]; ++j) {
-      const int32_t s = d.sym[j];
-      if (s < d.V) {
-        xw[o] = s;
-        xwt[o] = wt;
-        ++o;
-      }
-    }
-  }
-}
-
 __global__ void iota_u32_kernel(uint32_t* __restrict__ x, int64_t n) {
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
     x[i] = uint32_t(i);
-}
-
-__global__ void gather_w_kernel(const uint32_t* __restrict__ w, const uint32_t* __restrict__ slot, int64_t n,
-                                uint32_t* __restrict__ out) {
-  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
-    out[i] = w[slot[i]];
 }
 
 // xoff[f] = position of file f's first emitted word.
@@ -204,62 +347,146 @@ struct TvSlots {
 };
 
 constexpr int kChunk = 4096;  // rule words per chunk of the weighted sort
-constexpr int kCsItems = 8;   // items per thread in the chunk sort
 // root chunks (kFileChunk symbols) are sorted by 1024-thread CTAs, rule-word
 // chunks (kChunk words) by 512-thread CTAs: 8 items per thread either way
 template <bool kWeighted>
 struct ChunkShape {
   static constexpr int kItemsPerChunk = kWeighted ? kChunk : kFileChunk;
-  static constexpr int kThreads = kItemsPerChunk / kCsItems;
+  static constexpr int kThreads = kWeighted ? 512 : 1024;
+  static constexpr int kPer = kItemsPerChunk / kThreads;
   static constexpr int kWarps = kThreads / 32;
+  static_assert(kPer * kThreads == kItemsPerChunk, "whole items per thread");
 };
 constexpr int kMaxNb = 128;
 
 // A stream of (file-ordered) word items cut into chunks that never cross a
 // file: chunk c covers items [start[c], start[c] + len[c]) of file file_of(c);
-// the chunks of file f are [foff[f], foff[f+1]).
+// the chunks of file f are [foff[f], foff[f+1]).  For the rule words, chunk c
+// also names the (file, rule) pairs whose words overlap it: [p0[c], p1[c]).
 struct Chunks {
   const int64_t* start;
   const int32_t* len;
   const int64_t* foff;
   const int64_t* count;  // device: number of chunks
+  const int64_t* p0 = nullptr;
+  const int64_t* p1 = nullptr;
+};
+
+// Where the rule words of a chunk come from: the (file, rule) pairs in
+// file-major order (rule in the key's low half), the weight slot of each pair,
+// the position of its first word, the per-file weights, and the rules' own
+// words (rule r's at rule_words[woff[r]], W_r of them).
+struct PairWords {
+  const uint32_t* wbeg;   // [pairs]: the pair's rule's first own word in rule_words
+  const uint32_t* slot;   // [pairs]: the pair's weight slot
+  const uint32_t* pos;    // [pairs + 1]: first word of each pair in the file-major stream (< N < 2^32)
+  const uint32_t* w;      // per-file weights (slot layout)
+  const int32_t* rule_words;
 };
 
 // Counting sort of one chunk by word bucket, in shared memory, written back
 // to the chunk's own item range (one entry per word, so it always fits):
 // root words become their 14-bit index (uint16), rule words (index | weight
 // << 16) as uint64.  runs[c * nb + b] = (start, length) of bucket b's entries.
+// Root chunks read their words from the root body.  A rule-word chunk first
+// expands the (file, rule) pairs that overlap it into shared memory: each
+// pair writes its rule's own words (a contiguous run of the words-only rule
+// array) with the pair's weight at their positions in the chunk; pairs are
+// contiguous in the word stream, so a pair's words end where the next pair's
+// begin.
 template <bool kWeighted>
-__global__ void __launch_bounds__(ChunkShape<kWeighted>::kThreads, kWeighted ? 4 : 2) chunk_sort_kernel(
-    Chunks ch, const int32_t* __restrict__ items, const uint32_t* __restrict__ wts, int nb, int32_t V,
-    void* __restrict__ out, int64_t* __restrict__ run_start, int32_t* __restrict__ run_len) {
+__global__ void __launch_bounds__(ChunkShape<kWeighted>::kThreads, kWeighted ? 3 : 2) chunk_sort_kernel(
+    Chunks ch, const int32_t* __restrict__ items, PairWords pw, int nb, int32_t V, void* __restrict__ out,
+    int64_t* __restrict__ run_start, int32_t* __restrict__ run_len) {
   constexpr int kCsThreads = ChunkShape<kWeighted>::kThreads;
   constexpr int kCsWarps = ChunkShape<kWeighted>::kWarps;
   constexpr int kItems = ChunkShape<kWeighted>::kItemsPerChunk;
+  constexpr int kPer = ChunkShape<kWeighted>::kPer;
   __shared__ uint32_t wcnt[kCsWarps][kMaxNb + 1];
   __shared__ uint32_t bstart[kMaxNb + 1];
-  __shared__ __align__(16) unsigned char stage_raw[kItems * (kWeighted ? 8 : 2)];
+  // rule chunks: the expanded (word, weight) items, then the sorted entries
+  __shared__ __align__(16) unsigned char stage_raw[size_t(kItems) * (kWeighted ? 8 : 2)];
+  int32_t* const ex_word = reinterpret_cast<int32_t*>(stage_raw);
+  uint32_t* const ex_wt = reinterpret_cast<uint32_t*>(stage_raw) + kItems;
   const int64_t nch = *ch.count;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int64_t c = blockIdx.x; c < nch; c += gridDim.x) {
     for (int i = tid; i < kCsWarps * (kMaxNb + 1); i += kCsThreads) (&wcnt[0][0])[i] = 0;
-    __syncthreads();
     const int64_t base = ch.start[c];
     const int n = ch.len[c];
-    int32_t w[kCsItems];
-    uint32_t rank[kCsItems];
+    if (kWeighted) {
+      const int64_t q0 = ch.p0[c], q1 = ch.p1[c];
+      // two pairs per thread at a time: every load of a level is issued
+      // before the next level's (slot -> weight)
+      for (int64_t k0 = q0; k0 < q1; k0 += 2 * kCsThreads) {
+        uint32_t wb[2], sl[2], wv[2];
+        int64_t a[2], b[2];
 #pragma unroll
-    for (int j = 0; j < kCsItems; ++j) {
-      const int i = j * kCsThreads + tid;  // warp-contiguous: item order inside a warp is lane order
-      w[j] = i < n ? items[base + i] : -1;
+        for (int u = 0; u < 2; ++u) {
+          const int64_t q = k0 + u * kCsThreads + tid;
+          const bool in = q < q1;
+          wb[u] = in ? pw.wbeg[q] : 0u;
+          sl[u] = in ? pw.slot[q] : 0u;
+          a[u] = in ? int64_t(pw.pos[q]) - base : 0;
+          b[u] = in ? int64_t(pw.pos[q + 1]) - base : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) wv[u] = a[u] < b[u] ? pw.w[sl[u]] : 0u;
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int64_t j0 = a[u] > 0 ? a[u] : 0, j1 = b[u] < n ? b[u] : n;  // clipped to the chunk
+          for (int64_t j = j0; j < j1; ++j) {
+            ex_word[j] = pw.rule_words[wb[u] + uint32_t(j - a[u])];
+            ex_wt[j] = wv[u];
+          }
+        }
+      }
+    }
+    __syncthreads();
+    // item j of this thread: word (21 bits, V <= 2^21) | rank inside its
+    // (warp, bucket) << 21 (a warp holds 256 items, so the rank takes 8
+    // bits); kNone for no item or a rule reference
+    constexpr uint32_t kNone = 0xffffffffu;
+    static_assert(32 * kPer <= 256, "rank fits 8 bits");
+    uint32_t it[kPer];
+    uint32_t wt[kWeighted ? kPer : 1];
+    if (kWeighted) {
+#pragma unroll
+      for (int j = 0; j < kPer; ++j) {
+        const int i = j * kCsThreads + tid;  // warp-contiguous: item order inside a warp is lane order
+        const int32_t x = i < n ? ex_word[i] : -1;
+        wt[j] = i < n ? ex_wt[i] : 0u;
+        it[j] = uint32_t(x) < uint32_t(V) ? uint32_t(x) : kNone;
+      }
+    } else {
+      // the chunk's 16-byte-aligned window (from at most 3 symbols before the
+      // chunk), read as int4: only vectors that start inside the window, so
+      // the last read ends at most 3 symbols past the chunk (the array is
+      // padded by 4); symbols outside the chunk are dropped
+      const int64_t a0 = base & ~int64_t(3);
+      const int lead = int(base - a0);
+      static_assert(kPer % 4 == 0, "whole vectors per thread");
+#pragma unroll
+      for (int j = 0; j < kPer / 4; ++j) {
+        const int v = j * kCsThreads + tid;
+        const int4 q = 4 * v < lead + n ? *reinterpret_cast<const int4*>(items + a0 + 4 * int64_t(v))
+                                        : make_int4(-1, -1, -1, -1);
+        const int32_t xs[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int i = 4 * v + u - lead;  // position in the chunk
+          const int32_t x = (i >= 0 && i < n) ? xs[u] : -1;
+          it[4 * j + u] = uint32_t(x) < uint32_t(V) ? uint32_t(x) : kNone;
+        }
+      }
     }
     // rank inside (warp, bucket) by an atomic on the warp's own counter: the
     // histograms that read the runs do not depend on the order inside a run
 #pragma unroll
-    for (int j = 0; j < kCsItems; ++j)
-      if (uint32_t(w[j]) < uint32_t(V)) rank[j] = atomicAdd(&wcnt[warp][uint32_t(w[j]) >> kFBLog2], 1u);
-    __syncthreads();
-    // exclusive prefix over (bucket, warp): warp b0.. scans bucket b over the 16 warps
+    for (int j = 0; j < kPer; ++j)
+      if (it[j] != kNone) it[j] |= atomicAdd(&wcnt[warp][it[j] >> kFBLog2], 1u) << 21;
+    __syncthreads();  // also: the expanded items are in registers, the stage may be overwritten
+    // exclusive prefix over (bucket, warp): warp b0.. scans bucket b over the warps
     for (int b = warp; b < nb; b += kCsWarps) {
       const uint32_t x = lane < kCsWarps ? wcnt[lane][b] : 0u;
       uint32_t incl = x;
@@ -285,7 +512,9 @@ __global__ void __launch_bounds__(ChunkShape<kWeighted>::kThreads, kWeighted ? 4
         }
         if (b < nb) {
           bstart[b] = run + incl - x;
-          run_start[c * nb + b] = base + run + incl - x;
+          // rule chunks are written back to their own item range, root
+          // chunks to slot c of kFileChunk entries (16-byte aligned)
+          run_start[c * nb + b] = (kWeighted ? base : c * int64_t(kFileChunk)) + run + incl - x;
           run_len[c * nb + b] = int32_t(x);
         }
         run += __shfl_sync(0xffffffffu, incl, 31);
@@ -294,14 +523,14 @@ __global__ void __launch_bounds__(ChunkShape<kWeighted>::kThreads, kWeighted ? 4
     }
     __syncthreads();
 #pragma unroll
-    for (int j = 0; j < kCsItems; ++j) {
-      if (uint32_t(w[j]) >= uint32_t(V)) continue;
-      const int b = w[j] >> kFBLog2;
-      const uint32_t pos = bstart[b] + wcnt[warp][b] + rank[j];
-      const uint32_t local = uint32_t(w[j]) & (kFBucket - 1);
+    for (int j = 0; j < kPer; ++j) {
+      if (it[j] == kNone) continue;
+      const uint32_t word = it[j] & ((1u << 21) - 1u);
+      const int b = int(word >> kFBLog2);
+      const uint32_t pos = bstart[b] + wcnt[warp][b] + (it[j] >> 21);
+      const uint32_t local = word & (kFBucket - 1);
       if (kWeighted)
-        reinterpret_cast<uint64_t*>(stage_raw)[pos] =
-            (uint64_t(wts[base + j * kCsThreads + tid]) << 16) | local;
+        reinterpret_cast<uint64_t*>(stage_raw)[pos] = (uint64_t(wt[j]) << 16) | local;
       else
         reinterpret_cast<uint16_t*>(stage_raw)[pos] = uint16_t(local);
     }
@@ -311,19 +540,20 @@ __global__ void __launch_bounds__(ChunkShape<kWeighted>::kThreads, kWeighted ? 4
       uint64_t* o = static_cast<uint64_t*>(out) + base;
       for (uint32_t i = tid; i < total; i += kCsThreads) o[i] = reinterpret_cast<uint64_t*>(stage_raw)[i];
     } else {
-      uint16_t* o = static_cast<uint16_t*>(out) + base;
-      for (uint32_t i = tid; i < total; i += kCsThreads) o[i] = reinterpret_cast<uint16_t*>(stage_raw)[i];
+      static_assert(kItems == 8 * kCsThreads, "one 16-byte store per thread");
+      int4* o = reinterpret_cast<int4*>(static_cast<uint16_t*>(out) + c * int64_t(kFileChunk));
+      if (8 * uint32_t(tid) < total) o[tid] = reinterpret_cast<const int4*>(stage_raw)[tid];
     }
     __syncthreads();
   }
 }
 
 template <bool kWeighted>
-void launch_chunk_sort(unsigned grid, cudaStream_t s, const Chunks& ch, const int32_t* items, const uint32_t* wts,
+void launch_chunk_sort(unsigned grid, cudaStream_t s, const Chunks& ch, const int32_t* items, const PairWords& pw,
                        int nb, int32_t V, void* out, int64_t* run_start, int32_t* run_len) {
   if (nb > kMaxNb) fail(GT_EOVERFLOW, "more than 128 word buckets");
-  chunk_sort_kernel<kWeighted><<<grid, ChunkShape<kWeighted>::kThreads, 0, s>>>(ch, items, wts, nb, V, out, run_start,
-                                                                               run_len);
+  chunk_sort_kernel<kWeighted><<<grid, ChunkShape<kWeighted>::kThreads, 0, s>>>(ch, items, pw, nb, V, out,
+                                                                               run_start, run_len);
   GT_LAUNCH_CHECK();
 }
 
@@ -356,12 +586,52 @@ __global__ void rule_chunks_kernel(const int64_t* __restrict__ xoff, int32_t F, 
   }
 }
 
+// The pairs whose words overlap each rule-word chunk: p0 = the pair holding
+// the chunk's first word (the last pair starting at or before it; pairs
+// without words start where the next one does, so it is never one of them),
+// p1 = the first pair starting at or after the chunk's end.
+__global__ void chunk_pairs_kernel(const int64_t* __restrict__ start, const int32_t* __restrict__ len,
+                                   const int64_t* __restrict__ count, const int64_t* __restrict__ pos, int64_t n,
+                                   int64_t* __restrict__ p0, int64_t* __restrict__ p1) {
+  const int64_t nch = *count;
+  for (int64_t c = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; c < nch; c += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t s0 = start[c], s1 = s0 + len[c];
+    int64_t lo = 0, hi = n;  // first i with pos[i] > s0
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (pos[mid] <= s0) lo = mid + 1;
+      else hi = mid;
+    }
+    p0[c] = lo - 1;
+    lo = 0, hi = n;  // first i with pos[i] >= s1
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (pos[mid] < s1) lo = mid + 1;
+      else hi = mid;
+    }
+    p1[c] = lo;
+  }
+}
+
+// Per pair, what the rule-word chunks read: the first own word of its rule
+// and its first word in the stream as uint32 (both below N < 2^32).
+__global__ void pair_records_kernel(const uint64_t* __restrict__ keys, const int64_t* __restrict__ pos, int64_t n,
+                                    const uint32_t* __restrict__ woff, uint32_t* __restrict__ wbeg,
+                                    uint32_t* __restrict__ pos32) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i <= n; i += int64_t(gridDim.x) * blockDim.x) {
+    pos32[i] = uint32_t(pos[i]);
+    if (i < n) wbeg[i] = woff[uint32_t(keys[i])];
+  }
+}
+
 // CTA (f, b): dense histogram of file f's words in bucket b, from the bucket-b
 // runs of f's root chunks and rule-word chunks.  Run descriptors are staged
 // in shared memory a batch at a time, so each warp's next run starts without
 // a dependent global load.
 constexpr int kTvBatch = kTvThreads;
 
+// Root entries (uint16) add 1; rule-word entries (uint64) carry their weight
+// above the 16-bit index.
 template <typename E>
 __device__ __forceinline__ void tv_runs(uint32_t* hist, int64_t c0, int64_t c1, int nb, int b,
                                         const int64_t* __restrict__ rs, const int32_t* __restrict__ rl,
@@ -399,13 +669,35 @@ __device__ __forceinline__ void tv_runs(uint32_t* hist, int64_t c0, int64_t c1, 
   }
 }
 
+// Rule-word entries of this query: the load-time entries (pair slot above
+// the index) with the slot replaced by that slot's weight, a streaming pass
+// with eight independent gathers per thread in flight.
+constexpr int kWeighPer = 8;
+
+__global__ void __launch_bounds__(256) weigh_entries_kernel(const uint64_t* __restrict__ in, int64_t n,
+                                                            const uint32_t* __restrict__ w,
+                                                            uint64_t* __restrict__ out) {
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t i0 = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x); i0 < n; i0 += kWeighPer * stride) {
+    uint64_t e[kWeighPer];
+#pragma unroll
+    for (int u = 0; u < kWeighPer; ++u) e[u] = i0 + u * stride < n ? __ldcs(in + i0 + u * stride) : 0ull;
+    uint32_t x[kWeighPer];
+#pragma unroll
+    for (int u = 0; u < kWeighPer; ++u) x[u] = i0 + u * stride < n ? __ldg(w + uint32_t(e[u] >> 16)) : 0u;
+#pragma unroll
+    for (int u = 0; u < kWeighPer; ++u)
+      if (i0 + u * stride < n) out[i0 + u * stride] = (uint64_t(x[u]) << 16) | (e[u] & 0xffffull);
+  }
+}
+
 __global__ void __launch_bounds__(kTvThreads) tv_hist_kernel(int32_t F, int nb, Chunks rc, const int64_t* __restrict__ rrs,
                                                              const int32_t* __restrict__ rrl,
                                                              const uint16_t* __restrict__ rent, Chunks xc,
                                                              const int64_t* __restrict__ xrs,
                                                              const int32_t* __restrict__ xrl,
-                                                             const uint64_t* __restrict__ xent, const int32_t* __restrict__ order,
-                                                             TvSlots out) {
+                                                             const uint64_t* __restrict__ xent,
+                                                             const int32_t* __restrict__ order, TvSlots out) {
   __shared__ uint32_t hist[kFBucket];
   __shared__ int64_t warp_tot[kTvThreads / 32 + 1];
   __shared__ int64_t s_start[kTvBatch];
@@ -596,7 +888,9 @@ int bits_for(int64_t x) {
 }  // namespace
 
 // At load: the file masks once, to size every per-file buffer exactly (pairs,
-// their words, their body symbols).  Grammars with more than 64 files keep 0.
+// their words, their body symbols), and the structure the per-file weights
+// and the rule-word chunks are computed over.  Grammars with more than 64
+// files keep 0.
 void file_sizes(gt_grammar* g, cudaStream_t s) {
   gt_ctx* ctx = g->ctx;
   const DevGrammar& d = g->d;
@@ -608,7 +902,9 @@ void file_sizes(gt_grammar* g, cudaStream_t s) {
   auto* M = static_cast<unsigned long long*>(p);
   auto* off = reinterpret_cast<int64_t*>(M + d.R);
   auto* nnz = off + d.R;
-  Buf tot(ctx, 32, s), cnt(ctx, size_t(d.R) * 8, s), sc(ctx, scan_scratch_bytes(d.R), s);
+  Buf tot(ctx, 32, s), sc(ctx, scan_scratch_bytes(d.R), s), ntot(ctx, 32, s);
+  Buf cl(ctx, size_t(d.R) * 8, s), ch(ctx, size_t(d.R) * 8, s);
+  Buf sl(ctx, size_t(d.R) * 8, s), sh(ctx, size_t(d.R) * 8, s);
   fmask_root_kernel<<<grid_for(d.R, threads, cap), threads, 0, s>>>(d.rfile_off, d.rfile_f, d.R, M);
   GT_LAUNCH_CHECK();
   for (int lv = 2; lv < d.depth; ++lv) {
@@ -618,26 +914,126 @@ void file_sizes(gt_grammar* g, cudaStream_t s) {
       GT_LAUNCH_CHECK();
     }
   }
-  popc_kernel<<<grid_for(d.R, threads, cap), threads, 0, s>>>(M, d.R, cnt.as<int64_t>());
+  // slots level by level, light rules first: popcounts in level order, scanned
+  auto* nl = ntot.as<int64_t>();  // [0] light slots, [1] heavy slots
+  level_popc_kernel<<<grid_for(d.R, threads, cap), threads, 0, s>>>(d.lvl_order, M, d.pedge_off, d.R,
+                                                                     cl.as<int64_t>(), ch.as<int64_t>());
   GT_LAUNCH_CHECK();
-  exclusive_scan_i64(cnt.as<int64_t>(), off, d.R, sc.p, s);
-  last_total_kernel<<<1, 1, 0, s>>>(off, cnt.as<int64_t>(), d.R, nnz, nullptr);
+  exclusive_scan_i64(cl.as<int64_t>(), sl.as<int64_t>(), d.R, sc.p, s);
+  last_total_kernel<<<1, 1, 0, s>>>(sl.as<int64_t>(), cl.as<int64_t>(), d.R, nl, nullptr);
+  GT_LAUNCH_CHECK();
+  exclusive_scan_i64(ch.as<int64_t>(), sh.as<int64_t>(), d.R, sc.p, s);
+  last_total_kernel<<<1, 1, 0, s>>>(sh.as<int64_t>(), ch.as<int64_t>(), d.R, nl + 1, nullptr);
   GT_LAUNCH_CHECK();
   GT_CUDA(cudaMemsetAsync(tot.p, 0, 32, s));
   mask_totals_kernel<<<grid_for(d.R, threads, cap), threads, 0, s>>>(M, d.nwords, d.nrefs, d.R,
                                                                       tot.as<unsigned long long>());
   GT_LAUNCH_CHECK();
   unsigned long long h[3];
+  int64_t hn[2];
   GT_CUDA(cudaMemcpyAsync(h, tot.p, 24, cudaMemcpyDeviceToHost, s));
+  GT_CUDA(cudaMemcpyAsync(hn, nl, 16, cudaMemcpyDeviceToHost, s));
   GT_CUDA(cudaStreamSynchronize(s));
   g->fentry_bound = int64_t(h[0]);
   g->fword_bound = int64_t(h[1]);
   g->fsym_bound = int64_t(h[2]);
+  const int64_t EB = g->fentry_bound;
+  if (hn[0] + hn[1] != EB) fail(GT_EINVAL, "per-file slot count mismatch");
+  if (EB >= (int64_t(1) << 32)) fail(GT_EOVERFLOW, "2^32 or more (rule, file) pairs");
+  g->light_slots = hn[0];
+  GT_CUDA(cudaMemcpyAsync(nnz, &EB, 8, cudaMemcpyHostToDevice, s));
+  // owners of the slots and each level's first light and heavy slot
+  void* po = grammar_alloc(g, size_t(2 * (d.depth + 1)) * 8 + size_t(EB) * 5 + 64, s);
+  auto* lslot = static_cast<int64_t*>(po);
+  auto* lheavy = lslot + d.depth + 1;
+  auto* srule = reinterpret_cast<int32_t*>(lheavy + d.depth + 1);
+  auto* sfile = reinterpret_cast<uint8_t*>(srule + EB);
+  slot_owner_kernel<<<grid_for(d.R, threads, cap), threads, 0, s>>>(d.lvl_order, sl.as<int64_t>(), sh.as<int64_t>(),
+                                                                     nl, M, d.pedge_off, d.R, off, srule, sfile);
+  GT_LAUNCH_CHECK();
+  {
+    Buf loff(ctx, size_t(d.depth + 1) * 8, s);
+    GT_CUDA(cudaMemcpyAsync(loff.p, g->lvl_off.data(), size_t(d.depth + 1) * 8, cudaMemcpyHostToDevice, s));
+    level_slot_off_kernel<<<1, 128, 0, s>>>(loff.as<int64_t>(), d.depth, sl.as<int64_t>(), sh.as<int64_t>(), nl, d.R,
+                                            lslot, lheavy);
+    GT_LAUNCH_CHECK();
+    g->lvl_slot.assign(size_t(d.depth + 1), 0);
+    g->lvl_heavy.assign(size_t(d.depth + 1), 0);
+    GT_CUDA(cudaMemcpyAsync(g->lvl_slot.data(), lslot, size_t(d.depth + 1) * 8, cudaMemcpyDeviceToHost, s));
+    GT_CUDA(cudaMemcpyAsync(g->lvl_heavy.data(), lheavy, size_t(d.depth + 1) * 8, cudaMemcpyDeviceToHost, s));
+    GT_CUDA(cudaStreamSynchronize(s));  // loff, EB and lvl_off's host copy are read by now
+  }
+  g->slot_rule = srule;
+  g->slot_file = sfile;
+  // the root's references in slot layout (every weight's starting value)
+  {
+    auto* w0 = static_cast<uint32_t*>(grammar_alloc(g, size_t(EB) * 4 + 16, s));
+    if (EB > 0) GT_CUDA(cudaMemsetAsync(w0, 0, size_t(EB) * 4, s));
+    root_slots_kernel<<<grid_for(d.R, threads, cap), threads, 0, s>>>(d.rfile_off, d.rfile_f, d.rfile_m, d.R, off, M,
+                                                                       w0);
+    GT_LAUNCH_CHECK();
+    g->root_slots = w0;
+  }
+  // every slot's row of (parent slot, mult): counted, scanned, filled
+  {
+    Buf rc(ctx, size_t(EB) * 4 + 16, s), rc64(ctx, size_t(EB) * 8 + 16, s), ro64(ctx, size_t(EB + 1) * 8, s);
+    Buf sc5(ctx, scan_scratch_bytes(EB), s);
+    if (EB > 0) GT_CUDA(cudaMemsetAsync(rc.p, 0, size_t(EB) * 4, s));
+    slot_rows_kernel<false><<<grid_for(d.E, threads, cap), threads, 0, s>>>(
+        d.ledge_child, d.ledge_par, d.ledge_mult, d.E, off, M, rc.as<uint32_t>(), nullptr, nullptr);
+    GT_LAUNCH_CHECK();
+    widen_u32_kernel<<<grid_for(EB, threads, cap), threads, 0, s>>>(rc.as<uint32_t>(), EB, rc64.as<int64_t>());
+    GT_LAUNCH_CHECK();
+    exclusive_scan_i64(rc64.as<int64_t>(), ro64.as<int64_t>(), EB, sc5.p, s);
+    last_total_kernel<<<1, 1, 0, s>>>(ro64.as<int64_t>(), rc64.as<int64_t>(), EB, ro64.as<int64_t>() + EB, nullptr);
+    GT_LAUNCH_CHECK();
+    int64_t nent = 0;
+    GT_CUDA(cudaMemcpyAsync(&nent, ro64.as<int64_t>() + EB, 8, cudaMemcpyDeviceToHost, s));
+    GT_CUDA(cudaStreamSynchronize(s));
+    if (nent >= (int64_t(1) << 32)) fail(GT_EOVERFLOW, "per-file weight rows hold 2^32 entries or more");
+    void* pr = grammar_alloc(g, size_t(EB + 1) * 4 + 16 + size_t(nent) * 8 + 16, s);
+    auto* roff = static_cast<uint32_t*>(pr);
+    auto* ent = reinterpret_cast<uint2*>(roff + ((EB + 1 + 3) / 4) * 4);
+    narrow_off_kernel<<<grid_for(EB + 1, threads, cap), threads, 0, s>>>(ro64.as<int64_t>(), EB, roff);
+    GT_LAUNCH_CHECK();
+    if (EB > 0) GT_CUDA(cudaMemsetAsync(rc.p, 0, size_t(EB) * 4, s));
+    slot_rows_kernel<true><<<grid_for(d.E, threads, cap), threads, 0, s>>>(
+        d.ledge_child, d.ledge_par, d.ledge_mult, d.E, off, M, rc.as<uint32_t>(), ro64.as<int64_t>(), ent);
+    GT_LAUNCH_CHECK();
+    g->row_off = roff;
+    g->row_entries = ent;
+    // the heavy slots' rows in pieces, and each level's first piece
+    const int64_t NL = hn[0], NH = EB - NL;
+    Buf pc(ctx, size_t(NH) * 8 + 16, s), ps(ctx, size_t(NH + 1) * 8, s), sc6(ctx, scan_scratch_bytes(NH), s);
+    int64_t npieces = 0;
+    if (NH > 0) {
+      row_pieces_kernel<false><<<grid_for(NH, threads, cap), threads, 0, s>>>(roff, NL, EB, pc.as<int64_t>(),
+                                                                               nullptr, nullptr);
+      GT_LAUNCH_CHECK();
+      exclusive_scan_i64(pc.as<int64_t>(), ps.as<int64_t>(), NH, sc6.p, s);
+      last_total_kernel<<<1, 1, 0, s>>>(ps.as<int64_t>(), pc.as<int64_t>(), NH, ps.as<int64_t>() + NH, nullptr);
+      GT_LAUNCH_CHECK();
+      GT_CUDA(cudaMemcpyAsync(&npieces, ps.as<int64_t>() + NH, 8, cudaMemcpyDeviceToHost, s));
+      GT_CUDA(cudaStreamSynchronize(s));
+    }
+    auto* pieces = static_cast<uint4*>(grammar_alloc(g, size_t(npieces) * 16 + 16, s));
+    if (npieces > 0) {
+      row_pieces_kernel<true><<<grid_for(NH, threads, cap), threads, 0, s>>>(roff, NL, EB, nullptr,
+                                                                              ps.as<int64_t>(), pieces);
+      GT_LAUNCH_CHECK();
+    }
+    g->row_pieces = pieces;
+    g->lvl_piece.assign(size_t(d.depth + 1), 0);
+    for (int l = 0; l <= d.depth; ++l) {
+      const int64_t h = g->lvl_heavy[size_t(l)] - NL;  // heavy slots before level l
+      if (NH > 0) GT_CUDA(cudaMemcpyAsync(&g->lvl_piece[size_t(l)], ps.as<int64_t>() + h, 8, cudaMemcpyDeviceToHost, s));
+    }
+    GT_CUDA(cudaStreamSynchronize(s));  // the scratch above is released on return
+  }
   g->fmask = M;
   g->foff = off;
   g->fnnz = nnz;
   // the pairs in file-major order with their word offsets (persistent)
-  const int64_t EB = g->fentry_bound;
   const size_t qbytes = size_t(EB) * 8 + size_t(EB) * 4 + size_t(EB + 1) * 8 + size_t(d.F + 1) * 8 + 64;
   void* q = grammar_alloc(g, qbytes, s);
   auto* fkeys = static_cast<uint64_t*>(q);
@@ -647,7 +1043,8 @@ void file_sizes(gt_grammar* g, cudaStream_t s) {
   Buf keys(ctx, size_t(EB) * 8, s), slot0(ctx, size_t(EB) * 4, s), rs(ctx, radix_scratch_bytes(EB, true, 4), s);
   Buf wcnt(ctx, size_t(EB) * 8, s), sc2(ctx, scan_scratch_bytes(EB), s), fstart(ctx, size_t(d.F + 1) * 8, s);
   if (EB > 0) {
-    fentry_keys_kernel<<<grid_for(d.R, threads, cap), threads, 0, s>>>(M, off, d.R, keys.as<uint64_t>());
+    fentry_keys_kernel<<<grid_for(d.R, threads, cap), threads, 0, s>>>(M, off, d.nwords, d.R, d.F,
+                                                                        keys.as<uint64_t>());
     GT_LAUNCH_CHECK();
     iota_u32_kernel<<<grid_for(EB, threads, cap), threads, 0, s>>>(slot0.as<uint32_t>(), EB);
     GT_LAUNCH_CHECK();
@@ -663,11 +1060,80 @@ void file_sizes(gt_grammar* g, cudaStream_t s) {
   csr_offsets_hi(fkeys, EB, d.F, fstart.as<int64_t>(), s);
   file_starts_kernel<<<1, 128, 0, s>>>(fstart.as<int64_t>(), fpos, wcnt.as<int64_t>(), EB, d.F, fxoff);
   GT_LAUNCH_CHECK();
-  GT_CUDA(cudaStreamSynchronize(s));
   g->fe_keys = fkeys;
   g->fe_slot = fslot;
   g->fe_pos = fpos;
   g->fe_xoff = fxoff;
+  // the rule words cut into chunks of at most kChunk words inside each file,
+  // with the pairs that overlap each chunk
+  const int64_t nxc = g->fword_bound / kChunk + d.F + 1;  // bound on the chunks
+  void* pc = grammar_alloc(g, size_t(nxc) * 28 + size_t(d.F + 1) * 8 + 64, s);
+  auto* xcs = static_cast<int64_t*>(pc);
+  auto* xp0 = xcs + nxc;
+  auto* xp1 = xp0 + nxc;
+  auto* xcf = xp1 + nxc;
+  auto* xcn = xcf + d.F + 1;
+  auto* xcl = reinterpret_cast<int32_t*>(xcn + 1);
+  rule_chunks_kernel<<<1, 128, 0, s>>>(fxoff, d.F, xcs, xcl, xcf, xcn);
+  GT_LAUNCH_CHECK();
+  chunk_pairs_kernel<<<grid_for(nxc, threads, cap), threads, 0, s>>>(xcs, xcl, xcn, fpos, EB, xp0, xp1);
+  GT_LAUNCH_CHECK();
+  GT_CUDA(cudaMemcpyAsync(&g->rule_chunks, xcn, 8, cudaMemcpyDeviceToHost, s));
+  // the rules' own words, for the chunks' expansion
+  {
+    Buf wc(ctx, size_t(d.R) * 8, s), wo(ctx, size_t(d.R) * 8 + 8, s), sc4(ctx, scan_scratch_bytes(d.R), s);
+    rule_word_counts_kernel<<<grid_for(d.R, threads, cap), threads, 0, s>>>(d.nwords, d.R, wc.as<int64_t>());
+    GT_LAUNCH_CHECK();
+    exclusive_scan_i64(wc.as<int64_t>(), wo.as<int64_t>(), d.R, sc4.p, s);
+    last_total_kernel<<<1, 1, 0, s>>>(wo.as<int64_t>(), wc.as<int64_t>(), d.R, wo.as<int64_t>() + d.R, nullptr);
+    GT_LAUNCH_CHECK();
+    int64_t nw = 0;
+    GT_CUDA(cudaMemcpyAsync(&nw, wo.as<int64_t>() + d.R, 8, cudaMemcpyDeviceToHost, s));
+    GT_CUDA(cudaStreamSynchronize(s));
+    void* pwds = grammar_alloc(g, size_t(d.R) * 4 + size_t(nw) * 4 + 64, s);
+    auto* woff = static_cast<uint32_t*>(pwds);
+    auto* rw = reinterpret_cast<int32_t*>(woff + d.R + (d.R & 3 ? 4 - (d.R & 3) : 0));
+    rule_words_kernel<<<grid_for(d.R, threads, cap), threads, 0, s>>>(d, wo.as<int64_t>(), woff, rw);
+    GT_LAUNCH_CHECK();
+    g->rule_woff = woff;
+    g->rule_words = rw;
+    auto* rec = static_cast<uint32_t*>(grammar_alloc(g, size_t(EB) * 8 + 16, s));
+    pair_records_kernel<<<grid_for(EB + 1, threads, cap), threads, 0, s>>>(fkeys, fpos, EB, woff, rec, rec + EB);
+    GT_LAUNCH_CHECK();
+    g->fe_wbeg = rec;
+    g->fe_pos32 = rec + EB;
+    GT_CUDA(cudaStreamSynchronize(s));  // the scratch above is released on return
+  }
+  g->xch_start = xcs;
+  g->xch_len = xcl;
+  g->xch_foff = xcf;
+  g->xch_count = xcn;
+  g->xch_p0 = xp0;
+  g->xch_p1 = xp1;
+  GT_CUDA(cudaStreamSynchronize(s));
+  // the rule words of every file sorted by 16k-word bucket, each entry the
+  // slot of its (file, rule) pair above its 16-bit index (structure: a query
+  // gathers its weights through the slots)
+  {
+    const int nb = int((d.V + kFBucket - 1) / kFBucket);
+    const int64_t nxc2 = g->rule_chunks;
+    void* px = grammar_alloc(g, size_t(g->fword_bound) * 8 + 16 + size_t(nxc2) * nb * 12 + 64, s);
+    auto* xent = static_cast<uint64_t*>(px);
+    auto* xrs = reinterpret_cast<int64_t*>(xent + g->fword_bound + 2);
+    auto* xrl = reinterpret_cast<int32_t*>(xrs + nxc2 * nb);
+    if (nxc2 > 0) {
+      Buf ident(ctx, size_t(EB) * 4 + 16, s);
+      iota_u32_kernel<<<grid_for(EB, threads, cap), threads, 0, s>>>(ident.as<uint32_t>(), EB);
+      GT_LAUNCH_CHECK();
+      Chunks xc{xcs, xcl, xcf, xcn, xp0, xp1};
+      const PairWords pw{g->fe_wbeg, g->fe_slot, g->fe_pos32, ident.as<uint32_t>(), g->rule_words};
+      launch_chunk_sort<true>(unsigned(std::min<int64_t>(nxc2, 65535)), s, xc, nullptr, pw, nb, d.V, xent, xrs, xrl);
+      GT_CUDA(cudaStreamSynchronize(s));  // ident is released on return
+    }
+    g->xent = xent;
+    g->xrun_start = xrs;
+    g->xrun_len = xrl;
+  }
   // files by length, longest first (launch order of per-file work)
   std::vector<uint64_t> hl(size_t(d.F));
   if (d.F > 0) {
@@ -677,17 +1143,17 @@ void file_sizes(gt_grammar* g, cudaStream_t s) {
   std::vector<int32_t> ord(size_t(d.F));
   for (int32_t f = 0; f < d.F; ++f) ord[size_t(f)] = f;
   std::stable_sort(ord.begin(), ord.end(), [&](int32_t a, int32_t b) { return hl[size_t(a)] > hl[size_t(b)]; });
-  void* po = grammar_alloc(g, size_t(d.F) * 4 + 16, s);
-  if (d.F > 0) GT_CUDA(cudaMemcpyAsync(po, ord.data(), size_t(d.F) * 4, cudaMemcpyHostToDevice, s));
+  void* pf = grammar_alloc(g, size_t(d.F) * 4 + 16, s);
+  if (d.F > 0) GT_CUDA(cudaMemcpyAsync(pf, ord.data(), size_t(d.F) * 4, cudaMemcpyHostToDevice, s));
   GT_CUDA(cudaStreamSynchronize(s));  // ord is a host temporary
-  g->file_order = static_cast<const int32_t*>(po);
+  g->file_order = static_cast<const int32_t*>(pf);
 }
 
 void file_weights(gt_grammar* g, cudaStream_t s, FileWeights& fw) {
   gt_ctx* ctx = g->ctx;
   const DevGrammar& d = g->d;
   const int threads = 256, cap = ctx->num_sms * 16;
-  const int32_t R = d.R, F = d.F, V = d.V;
+  const int32_t F = d.F, V = d.V;
   if (F > 64) fail(GT_EOVERFLOW, "the top-down per-file strategy holds at most 64 files (file_strategy 0 or 2 selects bottom-up)");
   if (d.N >= (uint64_t(1) << 32)) fail(GT_EOVERFLOW, "per-file analytics need fewer than 2^32 tokens per grammar");
   if (V > (1 << 21)) fail(GT_EOVERFLOW, "per-file analytics support num_words <= 2^21");
@@ -697,17 +1163,19 @@ void file_weights(gt_grammar* g, cudaStream_t s, FileWeights& fw) {
   fw.off = g->foff;
   fw.nnz = g->fnnz;
   fw.w = Buf(ctx, size_t(EB) * 4, s);
-  if (EB > 0) GT_CUDA(cudaMemsetAsync(fw.w.p, 0, size_t(EB) * 4, s));
-  fweight_root_kernel<<<grid_for(R, threads, cap), threads, 0, s>>>(d.rfile_off, d.rfile_f, d.rfile_m, R, fw.off,
-                                                                     fw.mask, fw.w.as<uint32_t>());
-  GT_LAUNCH_CHECK();
+  // every weight starts as the root's references of its file
+  if (EB > 0) GT_CUDA(cudaMemcpyAsync(fw.w.p, g->root_slots, size_t(EB) * 4, cudaMemcpyDeviceToDevice, s));
+  const WeightRows L{g->row_off, g->row_entries, g->row_pieces};
+  // level by level from the root's children down; level-1 rules have no
+  // parent but the root, so their weights are complete already
   for (int lv = 2; lv < d.depth; ++lv) {
-    const int64_t a = g->ledge_off[lv], b = g->ledge_off[lv + 1];
-    if (b > a) {
-      fweight_edges_kernel<<<grid_for(b - a, threads, cap), threads, 0, s>>>(
-          d.ledge_child, d.ledge_par, d.ledge_mult, a, b, fw.off, fw.mask, fw.w.as<uint32_t>());
-      GT_LAUNCH_CHECK();
-    }
+    const int64_t a = g->lvl_slot[size_t(lv)], b = g->lvl_slot[size_t(lv) + 1];
+    const int64_t ha = g->lvl_piece[size_t(lv)], hb = g->lvl_piece[size_t(lv) + 1];
+    if (b <= a && hb <= ha) continue;
+    const int lb = b > a ? int(grid_for(b - a, threads, cap)) : 0;
+    const int hblk = hb > ha ? int(grid_for((hb - ha) * 32, threads, cap)) : 0;  // a warp per heavy piece
+    fweight_level_kernel<<<unsigned(lb + hblk), threads, 0, s>>>(L, a, b, lb, ha, hb, fw.w.as<uint32_t>());
+    GT_LAUNCH_CHECK();
   }
 }
 
@@ -716,26 +1184,11 @@ namespace {
 void file_hist(gt_grammar* g, cudaStream_t s, FileHist& fh) {
   gt_ctx* ctx = g->ctx;
   const DevGrammar& d = g->d;
-  const int threads = 256, cap = ctx->num_sms * 16;
   const int32_t F = d.F, V = d.V;
-  const int64_t EB = g->fentry_bound, XB = g->fword_bound;
-  Phase ph(ctx, "file_weights", s);
   FileWeights fwt;
-  file_weights(g, s, fwt);
-  Buf& w = fwt.w;
-  // ---- rule words per file (file-major): the pairs' order comes from load,
-  // each pair's weight is gathered from its rule-major slot ----
-  Buf swt(ctx, size_t(EB) * 4, s), xw(ctx, size_t(XB) * 4, s), xwt(ctx, size_t(XB) * 4, s);
-  const int64_t* pos = g->fe_pos;
-  const int64_t* xoff = g->fe_xoff;
-  if (EB > 0) {
-    gather_w_kernel<<<grid_for(EB, threads, cap), threads, 0, s>>>(w.as<uint32_t>(), g->fe_slot, EB,
-                                                                    swt.as<uint32_t>());
-    GT_LAUNCH_CHECK();
-    Phase ph1(ctx, "expand_words", s);
-    expand_words_kernel<<<grid_for(EB, threads, cap), threads, 0, s>>>(g->fe_keys, swt.as<uint32_t>(), EB, pos, d,
-                                                                        xw.as<int32_t>(), xwt.as<uint32_t>());
-    GT_LAUNCH_CHECK();
+  {
+    Phase ph(ctx, "file_weights", s);
+    file_weights(g, s, fwt);
   }
   // ---- bucket-sorted chunks, then dense (file, bucket) histograms ----
   const int nb = int((V + kFBucket - 1) / kFBucket);
@@ -753,28 +1206,28 @@ void file_hist(gt_grammar* g, cudaStream_t s, FileHist& fh) {
     Phase ph2(ctx, "tv_hist", s);
     const int64_t nrc = g->root_chunks;
     Chunks rc{d.rch_start, d.rch_len, d.rch_foff, d.rch_count};
-    Buf rent(ctx, size_t(d.root_len) * 2 + 16, s), rrs(ctx, size_t(nrc) * nb * 8, s), rrl(ctx, size_t(nrc) * nb * 4, s);
+    Chunks xc{g->xch_start, g->xch_len, g->xch_foff, g->xch_count, g->xch_p0, g->xch_p1};
+    const PairWords pw{};  // unused by the root chunks
+    Buf rent(ctx, size_t(nrc) * kFileChunk * 2 + 16, s), rrs(ctx, size_t(nrc) * nb * 8, s),
+        rrl(ctx, size_t(nrc) * nb * 4, s);
     if (nrc > 0) {
       Phase ph4(ctx, "chunk_sort_root", s);
-      launch_chunk_sort<false>(unsigned(std::min<int64_t>(nrc, 65535)), s, rc, d.sym, nullptr, nb, V, rent.p,
+      launch_chunk_sort<false>(unsigned(std::min<int64_t>(nrc, 65535)), s, rc, d.sym, pw, nb, V, rent.p,
                                rrs.as<int64_t>(), rrl.as<int32_t>());
     }
-    const int64_t nxc = XB / kChunk + F + 1;  // bound on the rule-word chunks
-    Buf xcs(ctx, size_t(nxc) * 8, s), xcl(ctx, size_t(nxc) * 4, s), xcf(ctx, size_t(F + 1) * 8, s), xcn(ctx, 8, s);
-    Buf xent(ctx, size_t(XB) * 8 + 16, s), xrs(ctx, size_t(nxc) * nb * 8, s), xrl(ctx, size_t(nxc) * nb * 4, s);
-    rule_chunks_kernel<<<1, 128, 0, s>>>(xoff, F, xcs.as<int64_t>(), xcl.as<int32_t>(), xcf.as<int64_t>(),
-                                        xcn.as<int64_t>());
-    GT_LAUNCH_CHECK();
-    Chunks xc{xcs.as<int64_t>(), xcl.as<int32_t>(), xcf.as<int64_t>(), xcn.as<int64_t>()};
-    {
-      Phase ph5(ctx, "chunk_sort_rules", s);
-      launch_chunk_sort<true>(unsigned(std::min<int64_t>(nxc, 65535)), s, xc, xw.as<int32_t>(), xwt.as<uint32_t>(),
-                              nb, V, xent.p, xrs.as<int64_t>(), xrl.as<int32_t>());
+    // the rule words: bucket-sorted at load, weighted here through their slots
+    const int64_t XB = g->fword_bound;
+    Buf xent(ctx, size_t(XB) * 8 + 16, s);
+    if (XB > 0) {
+      Phase ph6(ctx, "weigh_entries", s);
+      weigh_entries_kernel<<<grid_for((XB + kWeighPer - 1) / kWeighPer, 256, ctx->num_sms * 8), 256, 0, s>>>(
+          g->xent, XB, fwt.w.as<uint32_t>(), xent.as<uint64_t>());
+      GT_LAUNCH_CHECK();
     }
     Phase ph3(ctx, "tv_hist_kernel", s);
     tv_hist_kernel<<<unsigned(pieces), kTvThreads, 0, s>>>(F, nb, rc, rrs.as<int64_t>(), rrl.as<int32_t>(),
-                                                           rent.as<uint16_t>(), xc, xrs.as<int64_t>(),
-                                                           xrl.as<int32_t>(), xent.as<uint64_t>(), g->file_order, ts);
+                                                           rent.as<uint16_t>(), xc, g->xrun_start, g->xrun_len,
+                                                           xent.as<uint64_t>(), g->file_order, ts);
     GT_LAUNCH_CHECK();
   }
   Buf sc3(ctx, scan_scratch_bytes(pieces), s);

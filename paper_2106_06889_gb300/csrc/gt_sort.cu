@@ -91,14 +91,16 @@ __global__ void __launch_bounds__(kScanThreads) scan_apply_kernel(const int64_t*
 
 constexpr int kRsThreads = 256;  // one thread per digit value in the per-tile bookkeeping
 constexpr int kRsWarps = kRsThreads / 32;
-constexpr int kRsItems = 8;      // keys per thread; 8 x 256 threads with 4 CTAs per SM measured fastest
-constexpr int kRsTile = kRsThreads * kRsItems;  // keys per tile
+constexpr int kRsItems = 8;      // keys per thread by default ("radix_items" 16 doubles the tile)
+constexpr int kRsTile = kRsThreads * kRsItems;  // keys per tile (the smallest tile: scratch is sized for it)
 
 // Per-tile digit counts, stored tile-major (hist[tile * 256 + d]) so that
 // each CTA writes one contiguous row.
+template <int ITEMS>
 __global__ void __launch_bounds__(kRsThreads) radix_upsweep_kernel(const uint64_t* __restrict__ keys, int64_t n,
                                                                    int shift, uint32_t mask,
                                                                    uint32_t* __restrict__ hist) {
+  constexpr int kRsItems = ITEMS, kRsTile = kRsThreads * ITEMS;
   __shared__ uint32_t h[kRsWarps][256];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int i = threadIdx.x; i < kRsWarps * 256; i += kRsThreads) h[i / 256][i % 256] = 0;
@@ -159,12 +161,11 @@ __global__ void __launch_bounds__(256) radix_chunk_offsets_kernel(const uint32_t
 // and digits give every key its place in the tile sorted by digit.  The tile
 // is rearranged in shared memory in that order and written out with
 // consecutive threads writing consecutive addresses of each digit's run.
-constexpr int kRsMinBlocks = 4;
-
-template <int VB>
-__global__ void __launch_bounds__(kRsThreads, kRsMinBlocks) radix_downsweep_kernel(
+template <int VB, int ITEMS>
+__global__ void __launch_bounds__(kRsThreads, ITEMS == 8 ? 4 : 2) radix_downsweep_kernel(
     const uint64_t* __restrict__ kin, uint64_t* __restrict__ kout, const void* __restrict__ vin,
     void* __restrict__ vout, int64_t n, int shift, uint32_t mask, const int64_t* __restrict__ offs) {
+  constexpr int kRsItems = ITEMS, kRsTile = kRsThreads * ITEMS;
   __shared__ uint32_t wcnt[kRsWarps][256];
   __shared__ uint32_t dstart[256];
   __shared__ uint32_t wsum[kRsWarps];
@@ -243,14 +244,50 @@ __global__ void __launch_bounds__(kRsThreads, kRsMinBlocks) radix_downsweep_kern
   }
 }
 
-template <int VB>
+template <int VB, int ITEMS>
 void launch_downsweep(const uint64_t* ka, uint64_t* kb, const void* va, void* vb, int64_t n, int shift, uint32_t mask,
                       int64_t ntiles, const int64_t* offs, cudaStream_t s) {
-  constexpr size_t smem = size_t(kRsTile) * (8 + VB);
-  GT_CUDA(cudaFuncSetAttribute(radix_downsweep_kernel<VB>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+  constexpr size_t smem = size_t(kRsThreads) * ITEMS * (8 + VB);
+  GT_CUDA(cudaFuncSetAttribute(radix_downsweep_kernel<VB, ITEMS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               int(smem)));
   Phase ph(t_call_ctx, "radix_pass", s);  // one span per scatter pass
-  radix_downsweep_kernel<VB><<<unsigned(ntiles), kRsThreads, smem, s>>>(ka, kb, va, vb, n, shift, mask, offs);
+  radix_downsweep_kernel<VB, ITEMS><<<unsigned(ntiles), kRsThreads, smem, s>>>(ka, kb, va, vb, n, shift, mask, offs);
   GT_LAUNCH_CHECK();
+}
+
+template <int ITEMS>
+void radix_passes(uint64_t* ka, uint64_t* kb, void* va, void* vb, int value_bytes, int64_t n, const int* pass_shift,
+                  const int* pass_bits, int npass, void* scratch, cudaStream_t s, bool& swapped) {
+  constexpr int tile = kRsThreads * ITEMS;
+  const int64_t ntiles = (n + tile - 1) / tile;
+  const int64_t nchunks = (ntiles + kRsChunk - 1) / kRsChunk;
+  const int64_t m = 256 * ntiles, mc = 256 * nchunks;
+  uint32_t* hist = static_cast<uint32_t*>(scratch);
+  int64_t* offs = reinterpret_cast<int64_t*>(static_cast<char*>(scratch) + ((size_t(m) * 4 + 15) / 16 * 16));
+  int64_t* csum = offs + m;
+  int64_t* cpre = csum + mc;
+  void* sscratch = cpre + mc;
+  swapped = false;
+  for (int p = 0; p < npass; ++p) {
+    const int shift = pass_shift[p];
+    const uint32_t mask = (1u << pass_bits[p]) - 1u;
+    radix_upsweep_kernel<ITEMS><<<unsigned(ntiles), kRsThreads, 0, s>>>(ka, n, shift, mask, hist);
+    GT_LAUNCH_CHECK();
+    radix_chunk_sum_kernel<<<unsigned(nchunks), 256, 0, s>>>(hist, ntiles, nchunks, csum);
+    GT_LAUNCH_CHECK();
+    exclusive_scan_i64(csum, cpre, mc, sscratch, s);
+    radix_chunk_offsets_kernel<<<unsigned(nchunks), 256, 0, s>>>(hist, cpre, ntiles, nchunks, offs);
+    GT_LAUNCH_CHECK();
+    if (value_bytes == 4)
+      launch_downsweep<4, ITEMS>(ka, kb, va, vb, n, shift, mask, ntiles, offs, s);
+    else if (value_bytes == 8)
+      launch_downsweep<8, ITEMS>(ka, kb, va, vb, n, shift, mask, ntiles, offs, s);
+    else
+      launch_downsweep<0, ITEMS>(ka, kb, nullptr, nullptr, n, shift, mask, ntiles, offs, s);
+    std::swap(ka, kb);
+    std::swap(va, vb);
+    swapped = !swapped;
+  }
 }
 
 }  // namespace
@@ -303,37 +340,17 @@ void radix_sort_u64_split(uint64_t* keys_in, uint64_t* keys_out, void* vals_in, 
       pass_bits[npass++] = hi - shift < 8 ? hi - shift : 8;
     }
   }
-  const int64_t ntiles = (n + kRsTile - 1) / kRsTile;
-  const int64_t nchunks = (ntiles + kRsChunk - 1) / kRsChunk;
-  const int64_t m = 256 * ntiles, mc = 256 * nchunks;
-  uint32_t* hist = static_cast<uint32_t*>(scratch);
-  int64_t* offs = reinterpret_cast<int64_t*>(static_cast<char*>(scratch) + ((size_t(m) * 4 + 15) / 16 * 16));
-  int64_t* csum = offs + m;
-  int64_t* cpre = csum + mc;
-  void* sscratch = cpre + mc;
-  uint64_t* ka = keys_in;
-  uint64_t* kb = keys_out;
-  void* va = vals_in;
-  void* vb = vals_out;
-  for (int p = 0; p < npass; ++p) {
-    const int shift = pass_shift[p];
-    const uint32_t mask = (1u << pass_bits[p]) - 1u;
-    radix_upsweep_kernel<<<unsigned(ntiles), kRsThreads, 0, s>>>(ka, n, shift, mask, hist);
-    GT_LAUNCH_CHECK();
-    radix_chunk_sum_kernel<<<unsigned(nchunks), 256, 0, s>>>(hist, ntiles, nchunks, csum);
-    GT_LAUNCH_CHECK();
-    exclusive_scan_i64(csum, cpre, mc, sscratch, s);
-    radix_chunk_offsets_kernel<<<unsigned(nchunks), 256, 0, s>>>(hist, cpre, ntiles, nchunks, offs);
-    GT_LAUNCH_CHECK();
-    if (value_bytes == 4)
-      launch_downsweep<4>(ka, kb, va, vb, n, shift, mask, ntiles, offs, s);
-    else if (value_bytes == 8)
-      launch_downsweep<8>(ka, kb, va, vb, n, shift, mask, ntiles, offs, s);
-    else
-      launch_downsweep<0>(ka, kb, nullptr, nullptr, n, shift, mask, ntiles, offs, s);
-    std::swap(ka, kb);
-    std::swap(va, vb);
-  }
+  // digit passes over tiles of 2048 keys, or 4096 with "radix_items" 16
+  const int items = t_call_ctx ? int(t_call_ctx->param("radix_items", kRsItems)) : kRsItems;
+  bool swapped = false;
+  if (items == 16)
+    radix_passes<16>(keys_in, keys_out, vals_in, vals_out, value_bytes, n, pass_shift, pass_bits, npass, scratch, s,
+                     swapped);
+  else
+    radix_passes<8>(keys_in, keys_out, vals_in, vals_out, value_bytes, n, pass_shift, pass_bits, npass, scratch, s,
+                    swapped);
+  uint64_t* ka = swapped ? keys_out : keys_in;
+  void* va = swapped ? vals_out : vals_in;
   // after the loop the sorted data is in ka / va
   if (ka != keys_out) {
     GT_CUDA(cudaMemcpyAsync(keys_out, ka, size_t(n) * 8, cudaMemcpyDeviceToDevice, s));

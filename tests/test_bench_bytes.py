@@ -26,22 +26,15 @@ def test_step_bytes_per_workload():
 
 def test_kernel_bytes_count_only_the_methods_own_data():
     kb = bench.kernel_bytes("multi64_50m", INFO, OUT)
-    # the root chunk sort's kernel name carries the bucket index width (5 bits for 31 buckets)
-    assert kb["chunk_sort_root"] == ("chunk_sort_kernel<0, 5>", 4 * 400)
+    assert kb["chunk_sort_root"] == ("chunk_sort_kernel<0>", 4 * 400)
     assert kb["tv_hist_kernel"] == ("tv_hist_kernel", 12 * 90)
-    assert kb["expand_words"] == ("expand_words_kernel", 4 * 600)
+    # the rule-word chunks read every (file, rule) weight and the rule bodies
+    assert kb["chunk_sort_rules"] == ("chunk_sort_kernel<1>", 4 * 20 + 4 * 600)
     assert kb["wc_partition"] == ("wc_partition_kernel", 4 * 1000)
     kb = bench.kernel_bytes("nested_500m", INFO, OUT)
     assert kb["radix_pass"] == ("radix_downsweep_kernel<4>", 24 * 1100)  # rows read and written once a pass
     assert kb["seq_scatter"] == ("sg_scatter_kernel", 24 * 1100)
     assert kb["seq_reduce"] == ("sg_reduce_kernel", 12 * 1100 + 16 * 700)
-
-
-def test_bucket_index_width_matches_the_launch_dispatch():
-    # width = bits of (nb - 1), 0 for a single bucket, as the launcher computes it
-    for V, bits in ((1, 0), (16384, 0), (16385, 1), (32768, 1), (49152, 2), (500_000, 5), (1 << 21, 7)):
-        name = bench.kernel_bytes("multi64_50m", dict(INFO, num_words=V), OUT)["chunk_sort_root"][0]
-        assert name == f"chunk_sort_kernel<0, {bits}>", (V, name)
 
 
 def small_grammar(lens, seed=5):

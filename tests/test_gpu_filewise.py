@@ -33,7 +33,32 @@ def grammars():
     return out
 
 
-GRAMMARS = grammars()
+def heavy_parents_grammar(seed=12, F=8, H=3000, C=1500, V=4000):
+    """Rules with many parents: B = (w0 w1) is used by H rules A_k = (B w_k),
+    and A_0 by C rules C_j = (A_0 w_j); the root's files reference every A_k
+    and C_j (round robin) and some words.  B's per-file weights sum over
+    several thousand parent edges (more than one edge task), A_0's over
+    1,500 plus the root's references."""
+    rng = np.random.default_rng(seed)
+    B_, A0, C0 = 1, 2, 2 + H
+    rules = [None, [0, 1]]
+    rules += [[V + B_, 2 + k % (V - 2)] for k in range(H)]
+    rules += [[V + A0, 2 + j % (V - 2)] for j in range(C)]
+    refs = [V + A0 + k for k in range(H)] + [V + C0 + j for j in range(C)]
+    files = [[] for _ in range(F)]
+    for i, r in enumerate(refs):
+        files[i % F].append(r)
+    for f in range(F):
+        extra = rng.choice(refs, size=200).tolist() + rng.integers(0, V, size=100).tolist()
+        body = files[f] + extra
+        rng.shuffle(body)
+        files[f] = body
+    rules[0] = [x for b in files for x in b]
+    off = np.concatenate([[0], np.cumsum([len(b) for b in files])])
+    return grammar_from_rules(V, rules, off)
+
+
+GRAMMARS = grammars() + [("heavy_parents", heavy_parents_grammar())]
 IDS = [n for n, _ in GRAMMARS]
 
 

@@ -101,3 +101,29 @@ def test_same_as_sort_path(ctx):
         assert int(c1.sum(dtype=np.uint64)) == B.gt_grammar_info_get(gh)["num_tokens"] - 2
     finally:
         B.gt_free_grammar(gh)
+
+
+@pytest.mark.parametrize("name,g", [c for c in CASES if c[0] in ("nested2m", "multi500k", "one_key", "steep_root")],
+                         ids=["nested2m", "multi500k", "one_key", "steep_root"])
+def test_radix_tile_sizes(name, g):
+    """The radix-sort path with tiles of 2048 and of 4096 keys per scatter
+    pass ("radix_items" 8 and 16): the 3-word counts and the word sort equal
+    the oracle's; an unsupported size is refused."""
+    c = B.gt_create(0)
+    try:
+        with pytest.raises(B.GtError):
+            B.gt_set_param(c, "radix_items", 12)
+        B.gt_set_param(c, "seq_path", 1)
+        gh = B.gt_load_grammar(c, g)
+        want = oracle.sequence_count(g, 0)
+        ww, wc = oracle.sort_words(g, 1)
+        for items in (8, 16):
+            B.gt_set_param(c, "radix_items", items)
+            k, n = run(gh)
+            assert np.array_equal(k, want[0]) and np.array_equal(n, want[1]), items
+            r = B.gt_sort(gh, 1)
+            assert np.array_equal(B.result_numpy(r, "word"), ww) and np.array_equal(B.result_numpy(r, "count"), wc)
+            B.gt_free_result(r)
+        B.gt_free_grammar(gh)
+    finally:
+        B.gt_destroy(c)
