@@ -156,7 +156,7 @@ def kernel_bytes(workload: str, info: dict, out: dict) -> dict:
             "wc_partition": ("wc_partition_kernel", 4 * G)}
 
 
-PHASES = ("weights", "wc_partition", "wc_hist", "sort_canon", "file_weights", "tv_hist", "weigh_entries",
+PHASES = ("weights", "wc_partition", "wc_hist", "sort_canon", "file_weights", "tv_hist",
           "chunk_sort_root", "chunk_sort_rules", "tv_hist_kernel", "tv_out", "ii_out", "wc_from_files",
           "seq_headtail", "seq_emit", "seq_sort", "radix_pass", "seq_part", "seq_scatter", "seq_fine", "seq_reduce",
           "tv_out", "cooc_rows", "rows_sort")

@@ -191,9 +191,10 @@ __global__ void narrow_off_kernel(const int64_t* __restrict__ x, int64_t n, uint
 
 
 struct WeightRows {
-  const uint32_t* row_off;  // [slots + 1]
-  const uint2* entries;     // (parent slot, mult)
-  const uint4* pieces;      // heavy rows cut into pieces: (slot, first entry, end entry, 0)
+  const uint32_t* row_off;    // [slots + 1]
+  const uint2* entries;       // (parent's pair, mult)
+  const uint4* pieces;        // heavy rows cut into pieces: (pair, first entry, end entry, 0)
+  const uint32_t* slot_pair;  // [slots]: the pair of each slot (weights are kept by pair)
 };
 
 // Heavy rows are cut into pieces of at most kPieceEntries entries, one warp
@@ -233,6 +234,30 @@ __global__ void root_slots_kernel(const int64_t* __restrict__ rfile_off, const i
   }
 }
 
+// At load, once the pairs are in file-major order: every slot's pair (the
+// weights of a query live in pair order, so that the rule-word entries of a
+// chunk, which come from a run of consecutive pairs, gather them from a
+// small window), the root's references in pair order, and the rows' and
+// pieces' slots replaced by their pairs.
+__global__ void slot_pair_kernel(const uint32_t* __restrict__ pair_slot, int64_t n, uint32_t* __restrict__ slot_pair) {
+  for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < n; q += int64_t(gridDim.x) * blockDim.x)
+    slot_pair[pair_slot[q]] = uint32_t(q);
+}
+
+__global__ void pair_gather_kernel(const uint32_t* __restrict__ by_slot, const uint32_t* __restrict__ pair_slot,
+                                   int64_t n, uint32_t* __restrict__ by_pair) {
+  for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < n; q += int64_t(gridDim.x) * blockDim.x)
+    by_pair[q] = by_slot[pair_slot[q]];
+}
+
+__global__ void rows_to_pairs_kernel(uint2* __restrict__ entries, int64_t ne, uint4* __restrict__ pieces, int64_t np,
+                                     const uint32_t* __restrict__ slot_pair) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < ne + np; i += int64_t(gridDim.x) * blockDim.x) {
+    if (i < ne) entries[i].x = slot_pair[entries[i].x];
+    else pieces[i - ne].x = slot_pair[pieces[i - ne].x];
+  }
+}
+
 // One level: blocks [0, light_blocks) take the light slots [a, b), one
 // thread per slot (rows of at most kHeavyParents entries, all loads issued
 // together); the other blocks take the pieces [ha, hb) of the heavy slots'
@@ -251,10 +276,11 @@ __global__ void __launch_bounds__(256) fweight_level_kernel(WeightRows L, int64_
       uint32_t x[kHeavyParents];
 #pragma unroll
       for (int k = 0; k < kHeavyParents; ++k) x[k] = k < int(n) ? w[en[k].x] : 0u;
-      uint32_t v = w[i];
+      const uint32_t q = L.slot_pair[i];
+      uint32_t v = w[q];
 #pragma unroll
       for (int k = 0; k < kHeavyParents; ++k) v += en[k].y * x[k];
-      w[i] = v;
+      w[q] = v;
     }
     return;
   }
@@ -630,12 +656,15 @@ __global__ void pair_records_kernel(const uint64_t* __restrict__ keys, const int
 // a dependent global load.
 constexpr int kTvBatch = kTvThreads;
 
-// Root entries (uint16) add 1; rule-word entries (uint64) carry their weight
-// above the 16-bit index.
+// Root entries (uint16) add 1; rule-word entries (uint64) carry their
+// (file, rule) pair above the 16-bit index and add that pair's weight: the
+// entries of a run come from one chunk, a run of consecutive pairs, so the
+// gathers fall in a small window of the weights.
 template <typename E>
 __device__ __forceinline__ void tv_runs(uint32_t* hist, int64_t c0, int64_t c1, int nb, int b,
                                         const int64_t* __restrict__ rs, const int32_t* __restrict__ rl,
-                                        const E* __restrict__ ent, int64_t* s_start, int32_t* s_len) {
+                                        const E* __restrict__ ent, const uint32_t* __restrict__ wts,
+                                        int64_t* s_start, int32_t* s_len) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int64_t cb = c0; cb < c1; cb += kTvBatch) {
     const int nbatch = int(min(int64_t(kTvBatch), c1 - cb));
@@ -648,7 +677,7 @@ __device__ __forceinline__ void tv_runs(uint32_t* hist, int64_t c0, int64_t c1, 
     for (int q = warp; q < nbatch; q += kTvThreads / 32) {
       const int64_t s0 = s_start[q];
       const int32_t n = s_len[q];
-      // 4 independent loads per lane in flight before the histogram updates
+      // 4 independent loads per lane in flight, then their weights
       for (int i0 = 0; i0 < n; i0 += 128) {
         E e[4];
 #pragma unroll
@@ -656,38 +685,17 @@ __device__ __forceinline__ void tv_runs(uint32_t* hist, int64_t c0, int64_t c1, 
           const int i = i0 + k * 32 + lane;
           e[k] = i < n ? ent[s0 + i] : E(0);
         }
+        uint32_t x[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          x[k] = sizeof(E) == 2 ? 1u : (i0 + k * 32 + lane < n ? __ldg(wts + uint32_t(uint64_t(e[k]) >> 16)) : 0u);
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           if (i0 + k * 32 + lane >= n) break;
-          if (sizeof(E) == 2)
-            atomicAdd(&hist[uint32_t(e[k])], 1u);
-          else
-            atomicAdd(&hist[uint32_t(e[k]) & (kFBucket - 1)], uint32_t(uint64_t(e[k]) >> 16));
+          atomicAdd(&hist[uint32_t(e[k]) & (kFBucket - 1)], x[k]);
         }
       }
     }
-  }
-}
-
-// Rule-word entries of this query: the load-time entries (pair slot above
-// the index) with the slot replaced by that slot's weight, a streaming pass
-// with eight independent gathers per thread in flight.
-constexpr int kWeighPer = 8;
-
-__global__ void __launch_bounds__(256) weigh_entries_kernel(const uint64_t* __restrict__ in, int64_t n,
-                                                            const uint32_t* __restrict__ w,
-                                                            uint64_t* __restrict__ out) {
-  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-  for (int64_t i0 = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x); i0 < n; i0 += kWeighPer * stride) {
-    uint64_t e[kWeighPer];
-#pragma unroll
-    for (int u = 0; u < kWeighPer; ++u) e[u] = i0 + u * stride < n ? __ldcs(in + i0 + u * stride) : 0ull;
-    uint32_t x[kWeighPer];
-#pragma unroll
-    for (int u = 0; u < kWeighPer; ++u) x[u] = i0 + u * stride < n ? __ldg(w + uint32_t(e[u] >> 16)) : 0u;
-#pragma unroll
-    for (int u = 0; u < kWeighPer; ++u)
-      if (i0 + u * stride < n) out[i0 + u * stride] = (uint64_t(x[u]) << 16) | (e[u] & 0xffffull);
   }
 }
 
@@ -697,6 +705,7 @@ __global__ void __launch_bounds__(kTvThreads) tv_hist_kernel(int32_t F, int nb, 
                                                              const int64_t* __restrict__ xrs,
                                                              const int32_t* __restrict__ xrl,
                                                              const uint64_t* __restrict__ xent,
+                                                             const uint32_t* __restrict__ xw,
                                                              const int32_t* __restrict__ order, TvSlots out) {
   __shared__ uint32_t hist[kFBucket];
   __shared__ int64_t warp_tot[kTvThreads / 32 + 1];
@@ -707,8 +716,8 @@ __global__ void __launch_bounds__(kTvThreads) tv_hist_kernel(int32_t F, int nb, 
   const int64_t piece = int64_t(f) * nb + b;
   const int tid = threadIdx.x;
   for (int i = tid; i < kFBucket; i += kTvThreads) hist[i] = 0;
-  tv_runs<uint16_t>(hist, rc.foff[f], rc.foff[f + 1], nb, b, rrs, rrl, rent, s_start, s_len);
-  tv_runs<uint64_t>(hist, xc.foff[f], xc.foff[f + 1], nb, b, xrs, xrl, xent, s_start, s_len);
+  tv_runs<uint16_t>(hist, rc.foff[f], rc.foff[f + 1], nb, b, rrs, rrl, rent, nullptr, s_start, s_len);
+  tv_runs<uint64_t>(hist, xc.foff[f], xc.foff[f + 1], nb, b, xrs, xrl, xent, xw, s_start, s_len);
   __syncthreads();
   // compaction in word order: warp w owns bins [1024 w, 1024 w + 1024), read
   // 32 consecutive bins per round (no bank conflicts); the round masks are the
@@ -759,13 +768,19 @@ __global__ void __launch_bounds__(kTvThreads) tv_hist_kernel(int32_t F, int nb, 
 }
 
 // Copy every (file, bucket) piece to its place in the term vector.
+// Copy every (file, bucket) piece to its place in the term vector; with wc
+// (zeroed), each entry's count is also added to its word's count (the word
+// count as the sum of the files' counts, one reduction per entry).
 __global__ void tv_gather_kernel(TvSlots in, const int64_t* __restrict__ off, int32_t* __restrict__ word,
-                                 uint64_t* __restrict__ cnt) {
+                                 uint64_t* __restrict__ cnt, unsigned long long* __restrict__ wc) {
   const int64_t slot = int64_t(blockIdx.x) * kFBucket;
   const int64_t n = in.nnz[blockIdx.x], o = off[blockIdx.x];
   for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-    word[o + i] = in.word[slot + i];
-    cnt[o + i] = in.cnt[slot + i];
+    const int32_t w = in.word[slot + i];
+    const uint32_t c = in.cnt[slot + i];
+    word[o + i] = w;
+    cnt[o + i] = c;
+    if (wc) atomicAdd(&wc[w], (unsigned long long)c);
   }
 }
 
@@ -1002,6 +1017,7 @@ void file_sizes(gt_grammar* g, cudaStream_t s) {
     GT_LAUNCH_CHECK();
     g->row_off = roff;
     g->row_entries = ent;
+    g->row_entries_n = nent;
     // the heavy slots' rows in pieces, and each level's first piece
     const int64_t NL = hn[0], NH = EB - NL;
     Buf pc(ctx, size_t(NH) * 8 + 16, s), ps(ctx, size_t(NH + 1) * 8, s), sc6(ctx, scan_scratch_bytes(NH), s);
@@ -1023,6 +1039,7 @@ void file_sizes(gt_grammar* g, cudaStream_t s) {
       GT_LAUNCH_CHECK();
     }
     g->row_pieces = pieces;
+    g->row_pieces_n = npieces;
     g->lvl_piece.assign(size_t(d.depth + 1), 0);
     for (int l = 0; l <= d.depth; ++l) {
       const int64_t h = g->lvl_heavy[size_t(l)] - NL;  // heavy slots before level l
@@ -1064,6 +1081,26 @@ void file_sizes(gt_grammar* g, cudaStream_t s) {
   g->fe_slot = fslot;
   g->fe_pos = fpos;
   g->fe_xoff = fxoff;
+  // weights by pair: each slot's pair, the root's references by pair, and the
+  // rows and pieces re-addressed to pairs
+  {
+    auto* sp = static_cast<uint32_t*>(grammar_alloc(g, size_t(EB) * 8 + 32, s));
+    auto* r0 = sp + EB + 4;
+    if (EB > 0) {
+      slot_pair_kernel<<<grid_for(EB, threads, cap), threads, 0, s>>>(fslot, EB, sp);
+      GT_LAUNCH_CHECK();
+      pair_gather_kernel<<<grid_for(EB, threads, cap), threads, 0, s>>>(g->root_slots, fslot, EB, r0);
+      GT_LAUNCH_CHECK();
+    }
+    const int64_t ne = g->row_entries_n, np = g->row_pieces_n;
+    if (ne + np > 0) {
+      rows_to_pairs_kernel<<<grid_for(ne + np, threads, cap), threads, 0, s>>>(
+          const_cast<uint2*>(g->row_entries), ne, const_cast<uint4*>(g->row_pieces), np, sp);
+      GT_LAUNCH_CHECK();
+    }
+    g->slot_pair = sp;
+    g->root_pairs = r0;
+  }
   // the rule words cut into chunks of at most kChunk words inside each file,
   // with the pairs that overlap each chunk
   const int64_t nxc = g->fword_bound / kChunk + d.F + 1;  // bound on the chunks
@@ -1112,8 +1149,8 @@ void file_sizes(gt_grammar* g, cudaStream_t s) {
   g->xch_p1 = xp1;
   GT_CUDA(cudaStreamSynchronize(s));
   // the rule words of every file sorted by 16k-word bucket, each entry the
-  // slot of its (file, rule) pair above its 16-bit index (structure: a query
-  // gathers its weights through the slots)
+  // index of its (file, rule) pair above its 16-bit index (structure: a query
+  // gathers its weights by pair)
   {
     const int nb = int((d.V + kFBucket - 1) / kFBucket);
     const int64_t nxc2 = g->rule_chunks;
@@ -1126,7 +1163,8 @@ void file_sizes(gt_grammar* g, cudaStream_t s) {
       iota_u32_kernel<<<grid_for(EB, threads, cap), threads, 0, s>>>(ident.as<uint32_t>(), EB);
       GT_LAUNCH_CHECK();
       Chunks xc{xcs, xcl, xcf, xcn, xp0, xp1};
-      const PairWords pw{g->fe_wbeg, g->fe_slot, g->fe_pos32, ident.as<uint32_t>(), g->rule_words};
+      // "weight" of pair q = ident[ident[q]] = q: every entry carries its pair
+      const PairWords pw{g->fe_wbeg, ident.as<uint32_t>(), g->fe_pos32, ident.as<uint32_t>(), g->rule_words};
       launch_chunk_sort<true>(unsigned(std::min<int64_t>(nxc2, 65535)), s, xc, nullptr, pw, nb, d.V, xent, xrs, xrl);
       GT_CUDA(cudaStreamSynchronize(s));  // ident is released on return
     }
@@ -1163,9 +1201,10 @@ void file_weights(gt_grammar* g, cudaStream_t s, FileWeights& fw) {
   fw.off = g->foff;
   fw.nnz = g->fnnz;
   fw.w = Buf(ctx, size_t(EB) * 4, s);
-  // every weight starts as the root's references of its file
-  if (EB > 0) GT_CUDA(cudaMemcpyAsync(fw.w.p, g->root_slots, size_t(EB) * 4, cudaMemcpyDeviceToDevice, s));
-  const WeightRows L{g->row_off, g->row_entries, g->row_pieces};
+  fw.slot_pair = g->slot_pair;
+  // every weight starts as the root's references of its file (weights by pair)
+  if (EB > 0) GT_CUDA(cudaMemcpyAsync(fw.w.p, g->root_pairs, size_t(EB) * 4, cudaMemcpyDeviceToDevice, s));
+  const WeightRows L{g->row_off, g->row_entries, g->row_pieces, g->slot_pair};
   // level by level from the root's children down; level-1 rules have no
   // parent but the root, so their weights are complete already
   for (int lv = 2; lv < d.depth; ++lv) {
@@ -1215,19 +1254,11 @@ void file_hist(gt_grammar* g, cudaStream_t s, FileHist& fh) {
       launch_chunk_sort<false>(unsigned(std::min<int64_t>(nrc, 65535)), s, rc, d.sym, pw, nb, V, rent.p,
                                rrs.as<int64_t>(), rrl.as<int32_t>());
     }
-    // the rule words: bucket-sorted at load, weighted here through their slots
-    const int64_t XB = g->fword_bound;
-    Buf xent(ctx, size_t(XB) * 8 + 16, s);
-    if (XB > 0) {
-      Phase ph6(ctx, "weigh_entries", s);
-      weigh_entries_kernel<<<grid_for((XB + kWeighPer - 1) / kWeighPer, 256, ctx->num_sms * 8), 256, 0, s>>>(
-          g->xent, XB, fwt.w.as<uint32_t>(), xent.as<uint64_t>());
-      GT_LAUNCH_CHECK();
-    }
+    // the rule words: bucket-sorted at load, weighted here by their pairs
     Phase ph3(ctx, "tv_hist_kernel", s);
     tv_hist_kernel<<<unsigned(pieces), kTvThreads, 0, s>>>(F, nb, rc, rrs.as<int64_t>(), rrl.as<int32_t>(),
                                                            rent.as<uint16_t>(), xc, g->xrun_start, g->xrun_len,
-                                                           xent.as<uint64_t>(), g->file_order, ts);
+                                                           g->xent, fwt.w.as<uint32_t>(), g->file_order, ts);
     GT_LAUNCH_CHECK();
   }
   Buf sc3(ctx, scan_scratch_bytes(pieces), s);
@@ -1237,7 +1268,9 @@ void file_hist(gt_grammar* g, cudaStream_t s, FileHist& fh) {
   GT_LAUNCH_CHECK();
 }
 
-gt_result* term_vector_from(gt_grammar* g, FileHist& fh, int top_k, cudaStream_t s) {
+// With wc (top_k == 0 only), the word counts are written too: the sum over
+// files of the term vectors' counts, added while the pieces are copied.
+gt_result* term_vector_from(gt_grammar* g, FileHist& fh, int top_k, cudaStream_t s, uint64_t* wc = nullptr) {
   gt_ctx* ctx = g->ctx;
   const DevGrammar& d = g->d;
   const int64_t pieces = int64_t(d.F) * fh.nb;
@@ -1248,7 +1281,7 @@ gt_result* term_vector_from(gt_grammar* g, FileHist& fh, int top_k, cudaStream_t
     {
       Phase ph(ctx, "tv_out", s);
       tv_gather_kernel<<<unsigned(pieces), 256, 0, s>>>(ts, fh.off.as<int64_t>(), tw.as<int32_t>(),
-                                                        tc.as<uint64_t>());
+                                                        tc.as<uint64_t>(), nullptr);
       GT_LAUNCH_CHECK();
       tv_file_off_kernel<<<1, 256, 0, s>>>(fh.off.as<int64_t>(), fh.nb, d.F, fh.total.as<int64_t>(),
                                            full_off.as<int64_t>());
@@ -1263,7 +1296,9 @@ gt_result* term_vector_from(gt_grammar* g, FileHist& fh, int top_k, cudaStream_t
   auto* word = static_cast<int32_t*>(rb.alloc(size_t(nb_) * 4));
   auto* cnt = static_cast<uint64_t*>(rb.alloc(size_t(nb_) * 8));
   int64_t* len = rb.new_len_slot();
-  tv_gather_kernel<<<unsigned(pieces), 256, 0, s>>>(ts, fh.off.as<int64_t>(), word, cnt);
+  if (wc) GT_CUDA(cudaMemsetAsync(wc, 0, size_t(d.V) * 8, s));
+  tv_gather_kernel<<<unsigned(pieces), 256, 0, s>>>(ts, fh.off.as<int64_t>(), word, cnt,
+                                                    reinterpret_cast<unsigned long long*>(wc));
   GT_LAUNCH_CHECK();
   tv_file_off_kernel<<<1, 256, 0, s>>>(fh.off.as<int64_t>(), fh.nb, d.F, fh.total.as<int64_t>(), tv_off);
   GT_LAUNCH_CHECK();
@@ -1328,7 +1363,8 @@ gt_result* run_ranked_words(gt_grammar* g, cudaStream_t s) {
   TvSlots ts{fh.slot_word.as<int32_t>(), fh.slot_cnt.as<uint32_t>(), fh.nnz.as<int64_t>(), fh.bits.as<uint32_t>()};
   Buf tw(ctx, size_t(bound) * 4, s), tc(ctx, size_t(bound) * 8, s), toff(ctx, size_t(d.F + 1) * 8, s);
   Buf rkey(ctx, size_t(bound) * 8, s), rfile(ctx, size_t(bound) * 4, s);
-  tv_gather_kernel<<<unsigned(pieces), 256, 0, s>>>(ts, fh.off.as<int64_t>(), tw.as<int32_t>(), tc.as<uint64_t>());
+  tv_gather_kernel<<<unsigned(pieces), 256, 0, s>>>(ts, fh.off.as<int64_t>(), tw.as<int32_t>(), tc.as<uint64_t>(),
+                                                    nullptr);
   GT_LAUNCH_CHECK();
   tv_file_off_kernel<<<1, 256, 0, s>>>(fh.off.as<int64_t>(), fh.nb, d.F, fh.total.as<int64_t>(), toff.as<int64_t>());
   GT_LAUNCH_CHECK();
@@ -1479,9 +1515,14 @@ bool run_file_batch(gt_grammar* g, const int* tv_topk, int n_tv, gt_result** tv_
   }
   FileHist fh;
   file_hist(g, s, fh);
-  for (int i = 0; i < n_tv; ++i) tv_out[i] = term_vector_from(g, fh, tv_topk[i], s);
+  // the word count rides on the first full term vector's copy when there is one
+  int fused = -1;
+  for (int i = 0; i < n_tv && wc_out && fused < 0; ++i)
+    if (tv_topk[i] == 0) fused = i;
+  for (int i = 0; i < n_tv; ++i) tv_out[i] = term_vector_from(g, fh, tv_topk[i], s, i == fused ? wc_out : nullptr);
   if (ii_out) *ii_out = inverted_index_from(g, fh, s);
   if (!wc_out) return false;
+  if (fused >= 0) return true;
   gt_ctx* ctx = g->ctx;
   const DevGrammar& d = g->d;
   Phase ph(ctx, "wc_from_files", s);

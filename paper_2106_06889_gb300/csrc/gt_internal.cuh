@@ -207,6 +207,13 @@ struct gt_grammar {
   const uint4* row_pieces = nullptr;
   std::vector<int64_t> lvl_piece;
   const uint32_t* root_slots = nullptr;  // [slots]: the root's references of each (rule, file)
+  // per-file weights of a query are kept in pair order (file-major):
+  // slot_pair[slot] = its pair, root_pairs[pair] = the root's references; the
+  // rows' entries and the pieces hold pairs
+  const uint32_t* slot_pair = nullptr;
+  const uint32_t* root_pairs = nullptr;
+  int64_t row_entries_n = 0;
+  int64_t row_pieces_n = 0;
   // the (rule, file) pairs in file-major order: (file << 32 | rule), the
   // rule-major slot of each, the offset of its rule words, file starts
   const uint64_t* fe_keys = nullptr;
@@ -225,7 +232,7 @@ struct gt_grammar {
   const uint32_t* fe_wbeg = nullptr;
   const uint32_t* fe_pos32 = nullptr;
   // the rule words of each file sorted by 16k-word bucket per rule-word chunk:
-  // entry = pair slot << 16 | index in bucket, runs per (chunk, bucket)
+  // entry = pair << 16 | index in bucket, runs per (chunk, bucket)
   const uint64_t* xent = nullptr;
   const int64_t* xrun_start = nullptr;
   const int32_t* xrun_len = nullptr;
@@ -483,6 +490,10 @@ gt_result* reduce_key_rows(gt_ctx* ctx, Buf& keys, Buf& vals, int64_t n, int key
                            cudaStream_t s, const uint32_t* status_in = nullptr);
 // gt_seqg.cu: the global count (per_file == 0) by sample-sort buckets
 gt_result* run_sequence_count_global(gt_grammar* g, cudaStream_t s);
+// owned windows of every tile of kTile symbols, exclusive scan [ntiles + 1]:
+// structure, built by the first call and kept with the grammar (outside
+// stream capture; GT_EINVAL if the first call is captured)
+const int64_t* seq_tile_offsets(gt_grammar* g, const int32_t* head, const int32_t* tail, int kb, cudaStream_t s);
 gt_result* run_ranked_windows(gt_grammar* g, cudaStream_t s);
 // rows (key, file, count) -> ranked index; keys are compact 3-word keys
 // (windows = true, kb bits per word) or word ids (windows = false)
@@ -494,12 +505,14 @@ gt_result* run_ranked_words(gt_grammar* g, cudaStream_t s);
 // gt_file.cu: per-file analytics (top-down strategy, up to 64 files)
 gt_result* run_term_vector(gt_grammar* g, int top_k, cudaStream_t s);
 // Top-down per-file weights (<= 64 files): rule r's files are the set bits of
-// mask[r]; its weight in its k-th file (ascending) is w[off[r] + k].
+// mask[r]; its weight in its k-th file (ascending) is w[slot_pair[off[r] + k]]
+// (weights are kept in file-major pair order).
 struct FileWeights {
   const unsigned long long* mask = nullptr;  // [R] files holding each rule (the grammar's, from load)
   const int64_t* off = nullptr;              // [R] first (rule, file) slot of each rule (from load)
   const int64_t* nnz = nullptr;              // number of (rule, file) pairs (from load)
-  Buf w;                                     // uint32 [pairs]: per-file weights of this query
+  const uint32_t* slot_pair = nullptr;       // [pairs] the pair of each slot (from load)
+  Buf w;                                     // uint32 [pairs]: per-file weights of this query, by pair
 };
 void file_weights(gt_grammar* g, cudaStream_t s, FileWeights& fw);
 // at load: exact sizes of the per-file buffers (<= 64 files)

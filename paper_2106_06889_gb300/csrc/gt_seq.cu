@@ -26,9 +26,10 @@ namespace gt {
 namespace {
 
 // Global counts, compacted: every owned window gets one row, in body
-// position order.  One CTA per tile of kTile symbols (4 per thread); pass 1
-// counts the windows of each tile, an exclusive scan over tiles gives each
-// tile its first row, and pass 2 ranks the windows inside the tile.
+// position order.  One CTA per tile of kTile symbols (4 per thread); each
+// tile's first row comes from the per-grammar tile offsets (the windows of
+// every tile counted and scanned once, seq_tile_offsets), and the emit pass
+// ranks the windows inside the tile.
 constexpr int kWinThreads = kTile / 4;
 
 // Exclusive prefix of v over the CTA (kWinThreads threads); *total gets the sum.
@@ -53,16 +54,6 @@ __device__ __forceinline__ int cta_excl_scan(int v, int* total) {
   __syncthreads();
   *total = all;
   return before + incl - v;
-}
-
-__global__ void __launch_bounds__(kWinThreads) win_tile_count_kernel(DevGrammar d, const int32_t* __restrict__ head,
-                                                                     const int32_t* __restrict__ tail, int kb,
-                                                                     int64_t* __restrict__ tile_cnt) {
-  TileWin t;
-  const int c = tile_windows(d, head, tail, kb, int64_t(blockIdx.x) * kTile + threadIdx.x * 4, t);
-  int total;
-  cta_excl_scan(c, &total);
-  if (threadIdx.x == 0) tile_cnt[blockIdx.x] = total;
 }
 
 // Rows of rules nothing references (weight 0) get the pad key.  Rows past
@@ -113,7 +104,8 @@ __global__ void win_count_file_kernel(DevGrammar d, const int32_t* __restrict__ 
 // Pass 2: write (file << 32 | slot) and the key of every entry.
 __global__ void win_emit_file_kernel(DevGrammar d, const int32_t* __restrict__ head, const int32_t* __restrict__ tail,
                                      const unsigned long long* __restrict__ mask, const int64_t* __restrict__ woff,
-                                     const uint32_t* __restrict__ fw, int kb, const int64_t* __restrict__ pos,
+                                     const uint32_t* __restrict__ slot_pair, const uint32_t* __restrict__ fw, int kb,
+                                     const int64_t* __restrict__ pos,
                                      uint64_t* __restrict__ keys, uint64_t* __restrict__ fkeys,
                                      uint32_t* __restrict__ vals) {
   for (int64_t j = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; j < d.G; j += int64_t(gridDim.x) * blockDim.x) {
@@ -135,7 +127,7 @@ __global__ void win_emit_file_kernel(DevGrammar d, const int32_t* __restrict__ h
       while (m) {
         const int ff = __ffsll(m) - 1;
         m &= m - 1;
-        const uint32_t w = fw[slot++];
+        const uint32_t w = fw[slot_pair[slot++]];
         for (int i = 0; i < n; ++i, ++o) {
           keys[o] = k[i];
           fkeys[o] = uint64_t(uint32_t(ff));
@@ -414,18 +406,14 @@ void sorted_windows(gt_grammar* g, bool per_file, cudaStream_t s, Windows& out, 
       Buf wt(ctx, size_t(d.R) * 8, s);
       run_rule_weights(g, wt.as<uint64_t>(), s);
       const int64_t nt = d.ntiles;
-      Buf tcnt(ctx, size_t(nt + 1) * 8, s), toff(ctx, size_t(nt + 1) * 8, s), tsc(ctx, scan_scratch_bytes(nt + 1), s);
-      GT_CUDA(cudaMemsetAsync(tcnt.as<int64_t>() + nt, 0, 8, s));
-      win_tile_count_kernel<<<unsigned(nt), kWinThreads, 0, s>>>(d, head.as<int32_t>(), tail.as<int32_t>(), kb,
-                                                                  tcnt.as<int64_t>());
-      GT_LAUNCH_CHECK();
-      exclusive_scan_i64(tcnt.as<int64_t>(), toff.as<int64_t>(), nt + 1, tsc.p, s);
+      // each tile's first row: structure of the grammar, counted once and kept
+      const int64_t* toff = seq_tile_offsets(g, head.as<int32_t>(), tail.as<int32_t>(), kb, s);
       win_emit_kernel<<<unsigned(nt), kWinThreads, 0, s>>>(d, head.as<int32_t>(), tail.as<int32_t>(),
-                                                            wt.as<uint64_t>(), kb, out.key_pad, toff.as<int64_t>(), n,
+                                                            wt.as<uint64_t>(), kb, out.key_pad, toff, n,
                                                             k0.as<uint64_t>(), v0.as<uint32_t>(), status);
       GT_LAUNCH_CHECK();
       pad_tail_kernel<<<grid_for(n, threads, cap), threads, 0, s>>>(k0.as<uint64_t>(), nullptr, v0.as<uint32_t>(),
-                                                                     toff.as<int64_t>() + nt, n, out.key_pad, 0);
+                                                                     toff + nt, n, out.key_pad, 0);
       GT_LAUNCH_CHECK();
     }
     Phase ph(ctx, "seq_sort", s);
@@ -457,7 +445,7 @@ void sorted_windows(gt_grammar* g, bool per_file, cudaStream_t s, Windows& out, 
     last_total2_kernel<<<1, 1, 0, s>>>(pos.as<int64_t>(), cnt.as<int64_t>(), d.G, nd.as<int64_t>(), nullptr);
     GT_LAUNCH_CHECK();
     win_emit_file_kernel<<<grid_for(d.G, threads, cap), threads, 0, s>>>(
-        d, head.as<int32_t>(), tail.as<int32_t>(), fw.mask, fw.off,
+        d, head.as<int32_t>(), tail.as<int32_t>(), fw.mask, fw.off, fw.slot_pair,
         fw.w.as<uint32_t>(), kb, pos.as<int64_t>(), k0.as<uint64_t>(), f0.as<uint64_t>(), v0.as<uint32_t>());
     GT_LAUNCH_CHECK();
   }

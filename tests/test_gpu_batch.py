@@ -30,7 +30,9 @@ def test_mixed_batch_two_grammars(ctx):
           (hs[1], B.GT_Q_INVERTED_INDEX, 0, None), (hs[0], B.GT_Q_INVERTED_INDEX, 0, None),
           (hs[2], B.GT_Q_SORT, 1, None), (hs[0], B.GT_Q_TERM_VECTOR, 4, None),
           (hs[2], B.GT_Q_WORD_COUNT, 0, wc[2]), (hs[1], B.GT_Q_SORT, 0, None),
-          (hs[0], B.GT_Q_INVERTED_INDEX, 0, None)]
+          (hs[0], B.GT_Q_INVERTED_INDEX, 0, None),
+          # a word count with an inverted index and no full term vector: summed from the files' pieces
+          (hs[1], B.GT_Q_WORD_COUNT, 0, wc[1])]
     outs = B.gt_run_batch(ctx, qs)
     gs = {id(hs[0]): g1, id(hs[1]): g2, id(hs[2]): g3}
     for (gh, kind, param, counts), r in zip(qs, outs):
