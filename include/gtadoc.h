@@ -27,9 +27,10 @@
  *     gt_last_error.  Failures that only the GPU can detect (a full overflow
  *     list, a row count past its bound, an invalid symbol) are recorded in a
  *     device status word and reported by gt_sync / gt_result_view.  The
- *     only wait inside a kernel is the global sequence count's look-back
- *     (a CTA polls the published counts of the buckets before its own); it
- *     gives up after a bounded number of polls with GT_ETIMEOUT.
+ *     only waits inside kernels are decoupled look-backs (the global
+ *     sequence count's bucket path and the inverted index: a CTA polls the
+ *     published totals of the items taken before its own); each gives up
+ *     after a bounded number of polls with GT_ETIMEOUT.
  *   - There is no CPU fallback: if no usable sm_103a device is present,
  *     gt_create fails with GT_ECUDA.
  */
@@ -48,7 +49,7 @@ typedef int gt_status;
 #define GT_EINVAL 1       /* malformed argument or grammar                      */
 #define GT_ENOMEM 2       /* device or pool allocation failed                   */
 #define GT_ECUDA 3        /* a CUDA runtime call failed                         */
-#define GT_ETIMEOUT 4     /* a bounded device-side wait gave up (the sequence count's look-back) */
+#define GT_ETIMEOUT 4     /* a bounded device-side wait gave up (a decoupled look-back) */
 #define GT_ETABLE_FULL 5  /* a device overflow list ran out of room             */
 #define GT_EOVERFLOW 6    /* a size exceeds what the encoding supports          */
 #define GT_EBUSY 7        /* admission refused: not enough free memory / slots  */
@@ -321,6 +322,14 @@ gt_status gt_profile_enable(gt_ctx* ctx, int on);
 gt_status gt_profile_reset(gt_ctx* ctx);
 gt_status gt_profile_read(gt_ctx* ctx, const char* phase, double* total_ms, int64_t* spans, int64_t* launches);
 int64_t gt_kernel_launches(void);
+
+/* Self-check of the bounded waits (the decoupled look-backs of the global
+ * sequence count's bucket path and of the inverted index): one warp plays an
+ * item whose predecessor either publishes its prefix (publish != 0: returns
+ * GT_OK, *prefix = 7) or never does (publish == 0: the wait gives up after
+ * `polls` polls, 1..2^24, and the call returns GT_ETIMEOUT with *prefix = -1;
+ * the context stays usable).  No kernel faults or hangs either way. */
+gt_status gt_check_bounded_wait(gt_ctx* ctx, int publish, int64_t polls, int64_t* prefix);
 
 /* Tunable parameters (Section IV-A, parameter selection: results never depend
  * on them, only speed does).  Known names:

@@ -98,6 +98,7 @@ def lib() -> ctypes.CDLL:
             "gt_server_stats": [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                                 ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_uint64)],
             "gt_server_destroy": [_P],
+            "gt_check_bounded_wait": [_P, ctypes.c_int, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)],
             "gt_profile_reset": [_P],
             "gt_profile_read": [_P, ctypes.c_char_p, ctypes.POINTER(ctypes.c_double),
                                 ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)],
@@ -339,6 +340,14 @@ def gt_profile_read(ctx: Context, phase: str):
 
 def gt_kernel_launches() -> int:
     return int(lib().gt_kernel_launches())
+
+
+def gt_check_bounded_wait(ctx: Context, publish: bool, polls: int) -> int:
+    """The bounded look-back wait on one warp: the prefix it obtained (7) when
+    its predecessor publishes; GtError(GT_ETIMEOUT) when it never does."""
+    p = ctypes.c_int64()
+    _check(lib().gt_check_bounded_wait(ctx.handle, int(publish), polls, ctypes.byref(p)), ctx.handle)
+    return int(p.value)
 
 
 def gt_set_param(ctx: Context, name: str, value: int) -> None:

@@ -772,6 +772,44 @@ GT_API gt_status gt_profile_read(gt_ctx* ctx, const char* phase, double* total_m
 
 GT_API int64_t gt_kernel_launches(void) { return gt::g_launches.load(); }
 
+// ============================================================================
+// self-check of the bounded look-back wait
+// ============================================================================
+
+namespace {
+
+// Item 1 looks back at item 0: flags[0] is either never published (the wait
+// runs out after `polls` polls) or published with the prefix `pre`.
+__global__ void wait_check_kernel(unsigned long long* flags, int publish, uint64_t pre, int polls,
+                                  unsigned* status, int64_t* out) {
+  if (publish && threadIdx.x == 0) gt::publish_aggregate(flags, 0, pre);
+  __syncwarp();
+  const int64_t p = gt::warp_look_back(flags, 1, 5, status, polls);
+  if (threadIdx.x == 0) *out = p;
+}
+
+}  // namespace
+
+GT_API gt_status gt_check_bounded_wait(gt_ctx* ctx, int publish, int64_t polls, int64_t* prefix) {
+  if (!ctx || !prefix || polls < 1 || polls > (int64_t(1) << 24)) return GT_EINVAL;
+  return guard(ctx, [&] {
+    use_device(ctx);
+    cudaStream_t s = nullptr;
+    gt::Buf b(ctx, 64, s);
+    GT_CUDA(cudaMemsetAsync(b.p, 0, 64, s));
+    auto* flags = b.as<unsigned long long>();
+    auto* st = reinterpret_cast<unsigned*>(flags + 2);
+    auto* out = reinterpret_cast<int64_t*>(flags + 3);
+    wait_check_kernel<<<1, 32, 0, s>>>(flags, publish, 7, int(polls), st, out);
+    GT_LAUNCH_CHECK();
+    unsigned h_st = 0;
+    GT_CUDA(cudaMemcpyAsync(&h_st, st, 4, cudaMemcpyDeviceToHost, s));
+    GT_CUDA(cudaMemcpyAsync(prefix, out, 8, cudaMemcpyDeviceToHost, s));
+    GT_CUDA(cudaStreamSynchronize(s));
+    if (h_st & gt::ST_TIMEOUT) gt::fail(GT_ETIMEOUT, "look-back wait gave up (as asked)");
+  });
+}
+
 GT_API gt_status gt_set_param(gt_ctx* ctx, const char* name, int64_t value) {
   if (!ctx || !name) return GT_EINVAL;
   static const char* known[] = {"wc_aggregate", "use_graphs", "file_strategy", "wc_slices", "bu_local", "seq_path",

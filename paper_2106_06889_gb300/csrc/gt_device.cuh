@@ -128,4 +128,66 @@ __device__ __forceinline__ uint64_t to_output_key(uint64_t k, int kb) {
   return ((k >> (2 * kb)) << 42) | (((k >> kb) & m) << 21) | (k & m);
 }
 
+// ---- decoupled look-back over items taken in ticket order --------------
+// Flag word per item: state in the top two bits (0 nothing published, 1 the
+// item's own total, 2 the inclusive prefix through the item), value below.
+// An item only waits on items with smaller tickets, i.e. ones already
+// running, so every wait ends; each is bounded anyway.
+constexpr uint64_t kFlagAgg = 1ull << 62, kFlagIncl = 2ull << 62, kFlagVal = (1ull << 62) - 1;
+constexpr int kSpinLimit = 1 << 22;  // look-back polls before giving up (>= 0.25 s)
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// The item's own total, published as soon as it is known (one thread); item
+// 0 publishes its inclusive prefix directly.
+__device__ __forceinline__ void publish_aggregate(unsigned long long* flags, int64_t item, uint64_t agg) {
+  atomicExch(&flags[item], (item == 0 ? kFlagIncl : kFlagAgg) | agg);
+}
+
+// By one warp: reads the flags of the 32 preceding items at once, adds their
+// values up to the nearest one with a published prefix, and moves 32 items
+// further back while there is none; then publishes the item's inclusive
+// prefix.  Returns the exclusive prefix (to every lane); after kSpinLimit
+// polls of an item that published nothing it sets ST_TIMEOUT in *status,
+// still publishes (so that later items are not held up) and returns -1.
+__device__ __forceinline__ int64_t warp_look_back(unsigned long long* flags, int64_t item, uint64_t agg,
+                                                  unsigned* status, int spin_limit = kSpinLimit) {
+  const int lane = threadIdx.x & 31;
+  if (item == 0) return 0;
+  uint64_t excl = 0;
+  int64_t top = item - 1;  // the window is flags[top - 31 .. top], lane l reads top - l
+  int spins = 0;
+  bool ok = true;
+  while (true) {
+    const int64_t j = top - lane;
+    const unsigned long long v = j >= 0 ? ld_acquire_u64(&flags[j]) : kFlagIncl;
+    const uint64_t st = v & ~kFlagVal;
+    if (__any_sync(0xffffffffu, st == 0)) {
+      if (++spins > spin_limit) {
+        ok = false;
+        break;
+      }
+      __nanosleep(32);
+      continue;
+    }
+    const unsigned incl = __ballot_sync(0xffffffffu, st == kFlagIncl);
+    const int stop = incl ? __ffs(incl) - 1 : 31;  // nearest item with a prefix, else the whole window
+    uint64_t part = lane <= stop ? (v & kFlagVal) : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    excl += part;
+    if (incl) break;
+    top -= 32;  // flags[0] always holds a prefix, so the walk ends
+  }
+  if (lane == 0) {
+    if (!ok && status) atomicOr(status, ST_TIMEOUT);
+    atomicExch(&flags[item], kFlagIncl | (excl + agg));
+  }
+  return ok ? int64_t(excl) : -1;
+}
+
 }  // namespace gt

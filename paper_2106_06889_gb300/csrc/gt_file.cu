@@ -639,6 +639,23 @@ __global__ void chunk_pairs_kernel(const int64_t* __restrict__ start, const int3
   }
 }
 
+// At load: the rule-word entries of each chunk narrowed to 32 bits, the
+// pair made relative to the chunk's first pair (a chunk holds at most
+// kChunk + 1 pairs, every one with a word) above the 14-bit index.
+constexpr int kRelShift = 14;
+__global__ void narrow_entries_kernel(const uint64_t* __restrict__ wide, const int64_t* __restrict__ start,
+                                      const int32_t* __restrict__ len, const int64_t* __restrict__ count,
+                                      const int64_t* __restrict__ p0, uint32_t* __restrict__ out) {
+  const int64_t nch = *count;
+  for (int64_t c = blockIdx.x; c < nch; c += gridDim.x) {
+    const int64_t b = start[c], q0 = p0[c];
+    for (int i = threadIdx.x; i < len[c]; i += blockDim.x) {
+      const uint64_t e = wide[b + i];
+      out[b + i] = (uint32_t(int64_t(e >> 16) - q0) << kRelShift) | uint32_t(e & (kFBucket - 1));
+    }
+  }
+}
+
 // Per pair, what the rule-word chunks read: the first own word of its rule
 // and its first word in the stream as uint32 (both below N < 2^32).
 __global__ void pair_records_kernel(const uint64_t* __restrict__ keys, const int64_t* __restrict__ pos, int64_t n,
@@ -656,15 +673,19 @@ __global__ void pair_records_kernel(const uint64_t* __restrict__ keys, const int
 // a dependent global load.
 constexpr int kTvBatch = kTvThreads;
 
-// Root entries (uint16) add 1; rule-word entries (uint64) carry their
-// (file, rule) pair above the 16-bit index and add that pair's weight: the
-// entries of a run come from one chunk, a run of consecutive pairs, so the
-// gathers fall in a small window of the weights.
-template <typename E>
+// Root entries (uint16) add 1; rule-word entries (uint32) carry their
+// (file, rule) pair, relative to their chunk's first pair p0, above the
+// 14-bit index, and add that pair's weight: the entries of a run come from
+// one chunk, a run of consecutive pairs, so the gathers fall in a small
+// window of the weights.
+template <bool kRule>
 __device__ __forceinline__ void tv_runs(uint32_t* hist, int64_t c0, int64_t c1, int nb, int b,
                                         const int64_t* __restrict__ rs, const int32_t* __restrict__ rl,
-                                        const E* __restrict__ ent, const uint32_t* __restrict__ wts,
-                                        int64_t* s_start, int32_t* s_len) {
+                                        const void* __restrict__ entv, const int64_t* __restrict__ p0,
+                                        const uint32_t* __restrict__ wts, int64_t* s_start, int32_t* s_len,
+                                        uint32_t* s_p0) {
+  using E = typename std::conditional<kRule, uint32_t, uint16_t>::type;
+  const E* __restrict__ ent = static_cast<const E*>(entv);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int64_t cb = c0; cb < c1; cb += kTvBatch) {
     const int nbatch = int(min(int64_t(kTvBatch), c1 - cb));
@@ -672,27 +693,29 @@ __device__ __forceinline__ void tv_runs(uint32_t* hist, int64_t c0, int64_t c1, 
     if (tid < nbatch) {
       s_start[tid] = rs[(cb + tid) * nb + b];
       s_len[tid] = rl[(cb + tid) * nb + b];
+      if (kRule) s_p0[tid] = uint32_t(p0[cb + tid]);  // pairs < 2^32 (checked at load)
     }
     __syncthreads();
     for (int q = warp; q < nbatch; q += kTvThreads / 32) {
       const int64_t s0 = s_start[q];
       const int32_t n = s_len[q];
+      const uint32_t* wq = kRule ? wts + s_p0[q] : nullptr;
       // 4 independent loads per lane in flight, then their weights
       for (int i0 = 0; i0 < n; i0 += 128) {
-        E e[4];
+        uint32_t e[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           const int i = i0 + k * 32 + lane;
-          e[k] = i < n ? ent[s0 + i] : E(0);
+          e[k] = i < n ? uint32_t(ent[s0 + i]) : 0u;
         }
         uint32_t x[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k)
-          x[k] = sizeof(E) == 2 ? 1u : (i0 + k * 32 + lane < n ? __ldg(wts + uint32_t(uint64_t(e[k]) >> 16)) : 0u);
+          x[k] = !kRule ? 1u : (i0 + k * 32 + lane < n ? __ldg(wq + (e[k] >> 14)) : 0u);
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           if (i0 + k * 32 + lane >= n) break;
-          atomicAdd(&hist[uint32_t(e[k]) & (kFBucket - 1)], x[k]);
+          atomicAdd(&hist[e[k] & (kFBucket - 1)], x[k]);
         }
       }
     }
@@ -704,20 +727,21 @@ __global__ void __launch_bounds__(kTvThreads) tv_hist_kernel(int32_t F, int nb, 
                                                              const uint16_t* __restrict__ rent, Chunks xc,
                                                              const int64_t* __restrict__ xrs,
                                                              const int32_t* __restrict__ xrl,
-                                                             const uint64_t* __restrict__ xent,
+                                                             const uint32_t* __restrict__ xent,
                                                              const uint32_t* __restrict__ xw,
                                                              const int32_t* __restrict__ order, TvSlots out) {
   __shared__ uint32_t hist[kFBucket];
   __shared__ int64_t warp_tot[kTvThreads / 32 + 1];
   __shared__ int64_t s_start[kTvBatch];
   __shared__ int32_t s_len[kTvBatch];
+  __shared__ uint32_t s_p0[kTvBatch];
   // pieces of the longest files first (order: files by length, descending)
   const int f = order[blockIdx.x / nb], b = blockIdx.x % nb;
   const int64_t piece = int64_t(f) * nb + b;
   const int tid = threadIdx.x;
   for (int i = tid; i < kFBucket; i += kTvThreads) hist[i] = 0;
-  tv_runs<uint16_t>(hist, rc.foff[f], rc.foff[f + 1], nb, b, rrs, rrl, rent, nullptr, s_start, s_len);
-  tv_runs<uint64_t>(hist, xc.foff[f], xc.foff[f + 1], nb, b, xrs, xrl, xent, xw, s_start, s_len);
+  tv_runs<false>(hist, rc.foff[f], rc.foff[f + 1], nb, b, rrs, rrl, rent, nullptr, nullptr, s_start, s_len, s_p0);
+  tv_runs<true>(hist, xc.foff[f], xc.foff[f + 1], nb, b, xrs, xrl, xent, xc.p0, xw, s_start, s_len, s_p0);
   __syncthreads();
   // compaction in word order: warp w owns bins [1024 w, 1024 w + 1024), read
   // 32 consecutive bins per round (no bank conflicts); the round masks are the
@@ -834,6 +858,74 @@ __global__ void ii_fill_kernel(const uint32_t* __restrict__ bits, int nb, int32_
       if ((a >> lane) & 1u) files[o + __popc(a & below)] = lane;
       if ((c >> lane) & 1u) files[o + __popc(a) + __popc(c & below)] = lane + 32;
     }
+  }
+}
+
+// The inverted index in one pass: CTAs take blocks of kIiWords words in
+// ticket order; each counts the files of its words (one ballot per bit, as
+// above), scans the counts, gets the block's first posting by a bounded
+// decoupled look-back over the preceding blocks, writes the words' offsets
+// and fills their postings.
+constexpr int kIiThreads = 256;
+constexpr int kIiWords = kIiThreads;  // a warp per 32 words
+
+__global__ void __launch_bounds__(kIiThreads) ii_build_kernel(const uint32_t* __restrict__ bits, int nb, int32_t F,
+                                                              int32_t V, unsigned long long* __restrict__ flags,
+                                                              unsigned long long* __restrict__ ticket,
+                                                              int64_t* __restrict__ off, int32_t* __restrict__ files,
+                                                              unsigned* __restrict__ status) {
+  __shared__ int64_t s_item, s_prefix;
+  __shared__ int s_wsum[kIiThreads / 32 + 1];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) s_item = int64_t(atomicAdd(ticket, 1ull));
+  __syncthreads();
+  const int64_t item = s_item;
+  const int64_t w0 = item * kIiWords + warp * 32;
+  uint32_t lo = 0, hi = 0;
+  if (w0 < V) ii_masks(bits, nb, F, w0, lane, lo, hi);
+  int mine = 0;
+#pragma unroll
+  for (int l = 0; l < 32; ++l) {
+    const int c = __popc(__ballot_sync(0xffffffffu, (lo >> l) & 1u)) + __popc(__ballot_sync(0xffffffffu, (hi >> l) & 1u));
+    if (lane == l) mine = c;
+  }
+  if (w0 + lane >= V) mine = 0;
+  // exclusive prefix of the counts over the block
+  int incl = mine;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int u = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += u;
+  }
+  if (lane == 31) s_wsum[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    const int x = lane < kIiThreads / 32 ? s_wsum[lane] : 0;
+    int wi = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int u = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += u;
+    }
+    if (lane < kIiThreads / 32) s_wsum[lane] = wi - x;
+    if (lane == kIiThreads / 32 - 1) s_wsum[kIiThreads / 32] = wi;
+    const uint64_t total = uint64_t(__shfl_sync(0xffffffffu, wi, kIiThreads / 32 - 1));
+    if (lane == 0) publish_aggregate(flags, item, total);
+    __syncwarp();
+    const int64_t p = warp_look_back(flags, item, total, status);
+    if (lane == 0) s_prefix = p < 0 ? 0 : p;
+  }
+  __syncthreads();
+  const int64_t my_off = s_prefix + s_wsum[warp] + incl - mine;
+  if (w0 + lane < V) off[w0 + lane] = my_off;
+  if (w0 + lane == V - 1) off[V] = my_off + mine;
+  const unsigned below = (1u << lane) - 1u;
+  for (int l = 0; l < 32 && w0 + l < V; ++l) {
+    const unsigned a = __ballot_sync(0xffffffffu, (lo >> l) & 1u);
+    const unsigned c = __ballot_sync(0xffffffffu, (hi >> l) & 1u);
+    const int64_t o = __shfl_sync(0xffffffffu, my_off, l);
+    if ((a >> lane) & 1u) files[o + __popc(a & below)] = lane;
+    if ((c >> lane) & 1u) files[o + __popc(a) + __popc(c & below)] = lane + 32;
   }
 }
 
@@ -1148,25 +1240,29 @@ void file_sizes(gt_grammar* g, cudaStream_t s) {
   g->xch_p0 = xp0;
   g->xch_p1 = xp1;
   GT_CUDA(cudaStreamSynchronize(s));
-  // the rule words of every file sorted by 16k-word bucket, each entry the
-  // index of its (file, rule) pair above its 16-bit index (structure: a query
-  // gathers its weights by pair)
+  // the rule words of every file sorted by 16k-word bucket, each entry its
+  // (file, rule) pair relative to the chunk's first pair above its 14-bit
+  // index, in 32 bits (structure: a query gathers its weights by pair)
   {
     const int nb = int((d.V + kFBucket - 1) / kFBucket);
     const int64_t nxc2 = g->rule_chunks;
-    void* px = grammar_alloc(g, size_t(g->fword_bound) * 8 + 16 + size_t(nxc2) * nb * 12 + 64, s);
-    auto* xent = static_cast<uint64_t*>(px);
-    auto* xrs = reinterpret_cast<int64_t*>(xent + g->fword_bound + 2);
+    void* px = grammar_alloc(g, size_t(g->fword_bound) * 4 + 16 + size_t(nxc2) * nb * 12 + 64, s);
+    auto* xrs = static_cast<int64_t*>(px);
     auto* xrl = reinterpret_cast<int32_t*>(xrs + nxc2 * nb);
+    auto* xent = reinterpret_cast<uint32_t*>(xrl + nxc2 * nb + 4);
     if (nxc2 > 0) {
-      Buf ident(ctx, size_t(EB) * 4 + 16, s);
+      Buf ident(ctx, size_t(EB) * 4 + 16, s), wide(ctx, size_t(g->fword_bound) * 8 + 16, s);
       iota_u32_kernel<<<grid_for(EB, threads, cap), threads, 0, s>>>(ident.as<uint32_t>(), EB);
       GT_LAUNCH_CHECK();
       Chunks xc{xcs, xcl, xcf, xcn, xp0, xp1};
       // "weight" of pair q = ident[ident[q]] = q: every entry carries its pair
       const PairWords pw{g->fe_wbeg, ident.as<uint32_t>(), g->fe_pos32, ident.as<uint32_t>(), g->rule_words};
-      launch_chunk_sort<true>(unsigned(std::min<int64_t>(nxc2, 65535)), s, xc, nullptr, pw, nb, d.V, xent, xrs, xrl);
-      GT_CUDA(cudaStreamSynchronize(s));  // ident is released on return
+      launch_chunk_sort<true>(unsigned(std::min<int64_t>(nxc2, 65535)), s, xc, nullptr, pw, nb, d.V, wide.p, xrs,
+                              xrl);
+      narrow_entries_kernel<<<unsigned(std::min<int64_t>(nxc2, 65535)), 256, 0, s>>>(
+          wide.as<uint64_t>(), xcs, xcl, xcn, xp0, xent);
+      GT_LAUNCH_CHECK();
+      GT_CUDA(cudaStreamSynchronize(s));  // ident and wide are released on return
     }
     g->xent = xent;
     g->xrun_start = xrs;
@@ -1319,15 +1415,17 @@ gt_result* inverted_index_from(gt_grammar* g, FileHist& fh, cudaStream_t s) {
   auto* ii_off = static_cast<int64_t*>(rb.alloc(size_t(V + 1) * 8));
   auto* files = static_cast<int32_t*>(rb.alloc(size_t(fh.bound) * 4));
   int64_t* len = rb.new_len_slot();
-  Buf cnt(ctx, size_t(V + 1) * 8, s), sc(ctx, scan_scratch_bytes(V + 1), s);
-  ii_count_kernel<<<grid_for(V, threads, cap), threads, 0, s>>>(fh.bits.as<uint32_t>(), fh.nb, d.F, d.V,
-                                                                 cnt.as<int64_t>());
-  GT_LAUNCH_CHECK();
-  GT_CUDA(cudaMemsetAsync(cnt.as<int64_t>() + V, 0, 8, s));
-  exclusive_scan_i64(cnt.as<int64_t>(), ii_off, V + 1, sc.p, s);
-  ii_fill_kernel<<<grid_for(V, threads, cap), threads, 0, s>>>(fh.bits.as<uint32_t>(), fh.nb, d.F, d.V, ii_off,
-                                                                files);
-  GT_LAUNCH_CHECK();
+  if (V == 0) {
+    GT_CUDA(cudaMemsetAsync(ii_off, 0, 8, s));
+  } else {
+    const int64_t blocks = (V + kIiWords - 1) / kIiWords;
+    Buf lb(ctx, size_t(blocks + 1) * 8, s);  // look-back words, then the ticket
+    GT_CUDA(cudaMemsetAsync(lb.p, 0, size_t(blocks + 1) * 8, s));
+    auto* fl = lb.as<unsigned long long>();
+    ii_build_kernel<<<unsigned(blocks), kIiThreads, 0, s>>>(fh.bits.as<uint32_t>(), fh.nb, d.F, d.V, fl,
+                                                             fl + blocks, ii_off, files, rb.status());
+    GT_LAUNCH_CHECK();
+  }
   GT_CUDA(cudaMemcpyAsync(len, fh.total.p, 8, cudaMemcpyDeviceToDevice, s));
   rb.field("offsets", ii_off, V + 1);
   rb.field_dyn("file", files, len);

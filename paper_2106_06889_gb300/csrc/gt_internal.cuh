@@ -232,8 +232,8 @@ struct gt_grammar {
   const uint32_t* fe_wbeg = nullptr;
   const uint32_t* fe_pos32 = nullptr;
   // the rule words of each file sorted by 16k-word bucket per rule-word chunk:
-  // entry = pair << 16 | index in bucket, runs per (chunk, bucket)
-  const uint64_t* xent = nullptr;
+  // entry = (pair - chunk's first pair) << 14 | index in bucket, runs per (chunk, bucket)
+  const uint32_t* xent = nullptr;
   const int64_t* xrun_start = nullptr;
   const int32_t* xrun_len = nullptr;
   const int64_t* xch_start = nullptr;

@@ -494,13 +494,10 @@ constexpr int kRdThreads = 512;
 constexpr int kRdWarps = kRdThreads / 32;
 constexpr int kRdSlots = 4096;         // shared-memory hash slots (power of two)
 constexpr int kRdCapMax = 3072;        // distinct keys per bucket kept in shared memory (75% load)
-constexpr int kSpinLimit = 1 << 22;    // look-back polls before giving up (>= 0.25 s)
 constexpr int kSub = 256;              // sub-buckets of the shared-memory sample sort
 constexpr int kThreadBin = 16;         // sub-buckets up to this size: insertion sort by one thread
 constexpr int kWarpBin = 256;          // up to this size: bitonic network by one warp (8 keys per lane)
 constexpr int kMaxBig = kSub;
-// look-back flag word: state in the top two bits, value below
-constexpr uint64_t kFlagAgg = 1ull << 62, kFlagIncl = 2ull << 62, kFlagVal = (1ull << 62) - 1;
 
 struct ReduceShared {
   uint64_t tkey[kRdSlots];  // hash table, then the second sort buffer
@@ -546,57 +543,15 @@ struct ReduceArgs {
   int cap;                     // distinct keys handled in shared memory (<= kRdCapMax)
 };
 
-__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
-  unsigned long long v;
-  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-  return v;
-}
 
 // The bucket's count, published as soon as it is known (one thread); bucket
 // 0 publishes its inclusive prefix directly.
 __device__ __forceinline__ void publish_count(const ReduceArgs& a, int64_t item, uint64_t agg) {
-  atomicExch(&a.flags[item], (item == 0 ? kFlagIncl : kFlagAgg) | agg);
+  publish_aggregate(a.flags, item, agg);
 }
 
-// Decoupled look-back by one warp: reads the flags of the 32 preceding
-// buckets at once, adds their counts up to the nearest one with a published
-// prefix, and moves 32 buckets further back while there is none; then
-// publishes the bucket's inclusive prefix.  Returns the exclusive prefix (to
-// every lane); after kSpinLimit polls of a bucket that published nothing it
-// flags ST_TIMEOUT and returns -1.
 __device__ int64_t look_back(const ReduceArgs& a, int64_t item, uint64_t agg) {
-  const int lane = threadIdx.x & 31;
-  if (item == 0) return 0;
-  uint64_t excl = 0;
-  int64_t top = item - 1;  // the window is flags[top - 31 .. top], lane l reads top - l
-  int spins = 0;
-  bool ok = true;
-  while (true) {
-    const int64_t j = top - lane;
-    const unsigned long long v = j >= 0 ? ld_acquire_u64(&a.flags[j]) : kFlagIncl;
-    const uint64_t st = v & ~kFlagVal;
-    if (__any_sync(0xffffffffu, st == 0)) {
-      if (++spins > kSpinLimit) {
-        ok = false;
-        break;
-      }
-      __nanosleep(32);
-      continue;
-    }
-    const unsigned incl = __ballot_sync(0xffffffffu, st == kFlagIncl);
-    const int stop = incl ? __ffs(incl) - 1 : 31;  // nearest bucket with a prefix, else the whole window
-    uint64_t part = lane <= stop ? (v & kFlagVal) : 0;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-    excl += part;
-    if (incl) break;
-    top -= 32;  // flags[0] always holds a prefix, so the walk ends
-  }
-  if (lane == 0) {
-    if (!ok) atomicOr(a.status, ST_TIMEOUT);
-    atomicExch(&a.flags[item], kFlagIncl | (excl + agg));
-  }
-  return ok ? int64_t(excl) : -1;
+  return warp_look_back(a.flags, item, agg, a.status);
 }
 
 constexpr int kProbeLimit = 128;  // a longer probe sequence sends the bucket to global memory

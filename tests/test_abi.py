@@ -94,6 +94,7 @@ def test_null_arguments_are_rejected_before_any_device_call(so):
         "gt_poll": (null, ctypes.c_uint64(0), 0, null, null),
         "gt_server_stats": (null, null, null, null, null),
         "gt_server_destroy": (null,),
+        "gt_check_bounded_wait": (null, 0, 100, null),
     }
     for name, args in calls.items():
         f = getattr(lib, name)

@@ -9,6 +9,7 @@ are each within 1 ulp, so the values agree to a few ulp: rtol = 1e-15
 (about 4.5 ulp).  Words, offsets and counts are compared exactly."""
 import numpy as np
 import pytest
+import torch
 
 import oracle
 from paper_2106_06889_gb300 import binding as B
@@ -100,3 +101,20 @@ def test_batch_shares_the_term_vector_traversal(ctx):
             B.gt_free_result(r)
     finally:
         B.gt_free_grammar(gh)
+
+
+def test_bounded_wait_gives_up_and_the_context_stays_usable(ctx):
+    """A look-back whose predecessor never publishes gives up after its poll
+    limit with GT_ETIMEOUT (no hang, no fault); with the predecessor's prefix
+    published it returns it; the context keeps working afterwards."""
+    with pytest.raises(B.GtError) as e:
+        B.gt_check_bounded_wait(ctx, False, 2000)
+    assert "GT_ETIMEOUT" in str(e.value)
+    assert B.gt_check_bounded_wait(ctx, True, 2000) == 7
+    g = grammar_from_rules(5, [[0, 6, 1], [2, 3]], [0, 3])  # rule 1 = symbol 6
+    gh = B.gt_load_grammar(ctx, g)
+    out = torch.empty(5, dtype=torch.int64, device="cuda")
+    B.gt_word_count(gh, out)
+    torch.cuda.synchronize()
+    assert np.array_equal(out.cpu().numpy().astype(np.uint64), oracle.word_count(g))
+    B.gt_free_grammar(gh)
