@@ -794,9 +794,10 @@ __global__ void __launch_bounds__(kTvThreads) tv_hist_kernel(int32_t F, int nb, 
 // Copy every (file, bucket) piece to its place in the term vector.
 // Copy every (file, bucket) piece to its place in the term vector; with wc
 // (zeroed), each entry's count is also added to its word's count (the word
-// count as the sum of the files' counts, one reduction per entry).
+// count as the sum of the files' counts, one 32-bit reduction per entry:
+// counts stay below N < 2^32 on this path).
 __global__ void tv_gather_kernel(TvSlots in, const int64_t* __restrict__ off, int32_t* __restrict__ word,
-                                 uint64_t* __restrict__ cnt, unsigned long long* __restrict__ wc) {
+                                 uint64_t* __restrict__ cnt, unsigned* __restrict__ wc) {
   const int64_t slot = int64_t(blockIdx.x) * kFBucket;
   const int64_t n = in.nnz[blockIdx.x], o = off[blockIdx.x];
   for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
@@ -804,7 +805,7 @@ __global__ void tv_gather_kernel(TvSlots in, const int64_t* __restrict__ off, in
     const uint32_t c = in.cnt[slot + i];
     word[o + i] = w;
     cnt[o + i] = c;
-    if (wc) atomicAdd(&wc[w], (unsigned long long)c);
+    if (wc) atomicAdd(&wc[w], c);
   }
 }
 
@@ -1392,10 +1393,16 @@ gt_result* term_vector_from(gt_grammar* g, FileHist& fh, int top_k, cudaStream_t
   auto* word = static_cast<int32_t*>(rb.alloc(size_t(nb_) * 4));
   auto* cnt = static_cast<uint64_t*>(rb.alloc(size_t(nb_) * 8));
   int64_t* len = rb.new_len_slot();
-  if (wc) GT_CUDA(cudaMemsetAsync(wc, 0, size_t(d.V) * 8, s));
+  Buf wc32(ctx, wc ? size_t(d.V) * 4 + 16 : 16, s);
+  if (wc) GT_CUDA(cudaMemsetAsync(wc32.p, 0, size_t(d.V) * 4, s));
   tv_gather_kernel<<<unsigned(pieces), 256, 0, s>>>(ts, fh.off.as<int64_t>(), word, cnt,
-                                                    reinterpret_cast<unsigned long long*>(wc));
+                                                    wc ? wc32.as<unsigned>() : nullptr);
   GT_LAUNCH_CHECK();
+  if (wc) {
+    widen_u32_kernel<<<grid_for(d.V, 256, ctx->num_sms * 8), 256, 0, s>>>(wc32.as<uint32_t>(), d.V,
+                                                                          reinterpret_cast<int64_t*>(wc));
+    GT_LAUNCH_CHECK();
+  }
   tv_file_off_kernel<<<1, 256, 0, s>>>(fh.off.as<int64_t>(), fh.nb, d.F, fh.total.as<int64_t>(), tv_off);
   GT_LAUNCH_CHECK();
   GT_CUDA(cudaMemcpyAsync(len, fh.total.p, 8, cudaMemcpyDeviceToDevice, s));
