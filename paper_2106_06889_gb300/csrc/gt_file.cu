@@ -1005,6 +1005,11 @@ void file_sizes(gt_grammar* g, cudaStream_t s) {
   g->fentry_bound = g->fword_bound = g->fsym_bound = 0;
   if (d.F > 64) return;
   const int threads = 256, cap = ctx->num_sms * 16;
+  // structure used only while the layout is built (released on return)
+  Buf owners, w0b, pairs, words, recs;
+  const int32_t* rule_words = nullptr;
+  const uint32_t* fe_wbeg = nullptr;
+  const uint32_t* fe_pos32 = nullptr;
   // persistent: masks, slot offsets and the pair count (freed with the grammar)
   void* p = grammar_alloc(g, size_t(d.R) * 16 + 16, s);
   auto* M = static_cast<unsigned long long*>(p);
@@ -1051,10 +1056,11 @@ void file_sizes(gt_grammar* g, cudaStream_t s) {
   g->light_slots = hn[0];
   GT_CUDA(cudaMemcpyAsync(nnz, &EB, 8, cudaMemcpyHostToDevice, s));
   // owners of the slots and each level's first light and heavy slot
-  void* po = grammar_alloc(g, size_t(2 * (d.depth + 1)) * 8 + size_t(EB) * 5 + 64, s);
+  void* po = grammar_alloc(g, size_t(2 * (d.depth + 1)) * 8 + 64, s);
   auto* lslot = static_cast<int64_t*>(po);
   auto* lheavy = lslot + d.depth + 1;
-  auto* srule = reinterpret_cast<int32_t*>(lheavy + d.depth + 1);
+  owners = Buf(ctx, size_t(EB) * 5 + 64, s);
+  auto* srule = owners.as<int32_t>();
   auto* sfile = reinterpret_cast<uint8_t*>(srule + EB);
   slot_owner_kernel<<<grid_for(d.R, threads, cap), threads, 0, s>>>(d.lvl_order, sl.as<int64_t>(), sh.as<int64_t>(),
                                                                      nl, M, d.pedge_off, d.R, off, srule, sfile);
@@ -1071,16 +1077,14 @@ void file_sizes(gt_grammar* g, cudaStream_t s) {
     GT_CUDA(cudaMemcpyAsync(g->lvl_heavy.data(), lheavy, size_t(d.depth + 1) * 8, cudaMemcpyDeviceToHost, s));
     GT_CUDA(cudaStreamSynchronize(s));  // loff, EB and lvl_off's host copy are read by now
   }
-  g->slot_rule = srule;
-  g->slot_file = sfile;
   // the root's references in slot layout (every weight's starting value)
   {
-    auto* w0 = static_cast<uint32_t*>(grammar_alloc(g, size_t(EB) * 4 + 16, s));
+    w0b = Buf(ctx, size_t(EB) * 4 + 16, s);
+    auto* w0 = w0b.as<uint32_t>();
     if (EB > 0) GT_CUDA(cudaMemsetAsync(w0, 0, size_t(EB) * 4, s));
     root_slots_kernel<<<grid_for(d.R, threads, cap), threads, 0, s>>>(d.rfile_off, d.rfile_f, d.rfile_m, d.R, off, M,
                                                                        w0);
     GT_LAUNCH_CHECK();
-    g->root_slots = w0;
   }
   // every slot's row of (parent slot, mult): counted, scanned, filled
   {
@@ -1143,10 +1147,10 @@ void file_sizes(gt_grammar* g, cudaStream_t s) {
   g->fmask = M;
   g->foff = off;
   g->fnnz = nnz;
-  // the pairs in file-major order with their word offsets (persistent)
+  // the pairs in file-major order with their word offsets
   const size_t qbytes = size_t(EB) * 8 + size_t(EB) * 4 + size_t(EB + 1) * 8 + size_t(d.F + 1) * 8 + 64;
-  void* q = grammar_alloc(g, qbytes, s);
-  auto* fkeys = static_cast<uint64_t*>(q);
+  pairs = Buf(ctx, qbytes, s);
+  auto* fkeys = pairs.as<uint64_t>();
   auto* fslot = reinterpret_cast<uint32_t*>(fkeys + EB);
   auto* fpos = reinterpret_cast<int64_t*>(reinterpret_cast<char*>(fslot) + (size_t(EB) * 4 + 15) / 16 * 16);
   auto* fxoff = fpos + EB + 1;
@@ -1170,10 +1174,6 @@ void file_sizes(gt_grammar* g, cudaStream_t s) {
   csr_offsets_hi(fkeys, EB, d.F, fstart.as<int64_t>(), s);
   file_starts_kernel<<<1, 128, 0, s>>>(fstart.as<int64_t>(), fpos, wcnt.as<int64_t>(), EB, d.F, fxoff);
   GT_LAUNCH_CHECK();
-  g->fe_keys = fkeys;
-  g->fe_slot = fslot;
-  g->fe_pos = fpos;
-  g->fe_xoff = fxoff;
   // weights by pair: each slot's pair, the root's references by pair, and the
   // rows and pieces re-addressed to pairs
   {
@@ -1182,7 +1182,7 @@ void file_sizes(gt_grammar* g, cudaStream_t s) {
     if (EB > 0) {
       slot_pair_kernel<<<grid_for(EB, threads, cap), threads, 0, s>>>(fslot, EB, sp);
       GT_LAUNCH_CHECK();
-      pair_gather_kernel<<<grid_for(EB, threads, cap), threads, 0, s>>>(g->root_slots, fslot, EB, r0);
+      pair_gather_kernel<<<grid_for(EB, threads, cap), threads, 0, s>>>(w0b.as<uint32_t>(), fslot, EB, r0);
       GT_LAUNCH_CHECK();
     }
     const int64_t ne = g->row_entries_n, np = g->row_pieces_n;
@@ -1220,18 +1220,18 @@ void file_sizes(gt_grammar* g, cudaStream_t s) {
     int64_t nw = 0;
     GT_CUDA(cudaMemcpyAsync(&nw, wo.as<int64_t>() + d.R, 8, cudaMemcpyDeviceToHost, s));
     GT_CUDA(cudaStreamSynchronize(s));
-    void* pwds = grammar_alloc(g, size_t(d.R) * 4 + size_t(nw) * 4 + 64, s);
-    auto* woff = static_cast<uint32_t*>(pwds);
+    words = Buf(ctx, size_t(d.R) * 4 + size_t(nw) * 4 + 64, s);
+    auto* woff = words.as<uint32_t>();
     auto* rw = reinterpret_cast<int32_t*>(woff + d.R + (d.R & 3 ? 4 - (d.R & 3) : 0));
     rule_words_kernel<<<grid_for(d.R, threads, cap), threads, 0, s>>>(d, wo.as<int64_t>(), woff, rw);
     GT_LAUNCH_CHECK();
-    g->rule_woff = woff;
-    g->rule_words = rw;
-    auto* rec = static_cast<uint32_t*>(grammar_alloc(g, size_t(EB) * 8 + 16, s));
+    recs = Buf(ctx, size_t(EB) * 8 + 16, s);
+    auto* rec = recs.as<uint32_t>();
     pair_records_kernel<<<grid_for(EB + 1, threads, cap), threads, 0, s>>>(fkeys, fpos, EB, woff, rec, rec + EB);
     GT_LAUNCH_CHECK();
-    g->fe_wbeg = rec;
-    g->fe_pos32 = rec + EB;
+    rule_words = rw;
+    fe_wbeg = rec;
+    fe_pos32 = rec + EB;
     GT_CUDA(cudaStreamSynchronize(s));  // the scratch above is released on return
   }
   g->xch_start = xcs;
@@ -1257,7 +1257,7 @@ void file_sizes(gt_grammar* g, cudaStream_t s) {
       GT_LAUNCH_CHECK();
       Chunks xc{xcs, xcl, xcf, xcn, xp0, xp1};
       // "weight" of pair q = ident[ident[q]] = q: every entry carries its pair
-      const PairWords pw{g->fe_wbeg, ident.as<uint32_t>(), g->fe_pos32, ident.as<uint32_t>(), g->rule_words};
+      const PairWords pw{fe_wbeg, ident.as<uint32_t>(), fe_pos32, ident.as<uint32_t>(), rule_words};
       launch_chunk_sort<true>(unsigned(std::min<int64_t>(nxc2, 65535)), s, xc, nullptr, pw, nb, d.V, wide.p, xrs,
                               xrl);
       narrow_entries_kernel<<<unsigned(std::min<int64_t>(nxc2, 65535)), 256, 0, s>>>(

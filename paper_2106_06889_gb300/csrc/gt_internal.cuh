@@ -187,50 +187,32 @@ struct gt_grammar {
   // top-down per-file layout (<= 64 files), built at load: the set of files
   // holding each rule (64-bit mask) and each rule's first (rule, file) slot;
   // slots are laid out level by level (rules in level order, files ascending),
-  // level l's are [lvl_slot[l], lvl_slot[l+1]), owned by (slot_rule, slot_file)
+  // light rules (few parents) first: level l's light slots are
+  // [lvl_slot[l], lvl_slot[l+1]), its heavy ones [lvl_heavy[l], lvl_heavy[l+1])
   const unsigned long long* fmask = nullptr;
   const int64_t* foff = nullptr;
   const int64_t* fnnz = nullptr;
-  // light rules (few parents) first, then the heavy ones, each level by
-  // level: level l's heavy slots are [lvl_heavy[l], lvl_heavy[l+1]).  Slot i's
-  // row row_entries[row_off[i], row_off[i+1]) lists (parent slot, mult) over
-  // the rule's non-root parents holding the slot's file
   std::vector<int64_t> lvl_slot;
   std::vector<int64_t> lvl_heavy;
   int64_t light_slots = 0;
-  const int32_t* slot_rule = nullptr;
-  const uint8_t* slot_file = nullptr;
-  const uint32_t* row_off = nullptr;
-  const uint2* row_entries = nullptr;
-  // the heavy slots' rows cut into pieces (slot, first entry, end entry);
-  // level l's are [lvl_piece[l], lvl_piece[l+1])
-  const uint4* row_pieces = nullptr;
-  std::vector<int64_t> lvl_piece;
-  const uint32_t* root_slots = nullptr;  // [slots]: the root's references of each (rule, file)
   // per-file weights of a query are kept in pair order (file-major):
-  // slot_pair[slot] = its pair, root_pairs[pair] = the root's references; the
-  // rows' entries and the pieces hold pairs
+  // slot_pair[slot] = its pair, root_pairs[pair] = the root's references.
+  // Slot i's row row_entries[row_off[i], row_off[i+1]) lists (parent's pair,
+  // mult) over the rule's non-root parents holding the slot's file; heavy
+  // rows are cut into pieces (pair, first entry, end entry), level l's
+  // [lvl_piece[l], lvl_piece[l+1])
   const uint32_t* slot_pair = nullptr;
   const uint32_t* root_pairs = nullptr;
+  const uint32_t* row_off = nullptr;
+  const uint2* row_entries = nullptr;
   int64_t row_entries_n = 0;
+  const uint4* row_pieces = nullptr;
   int64_t row_pieces_n = 0;
-  // the (rule, file) pairs in file-major order: (file << 32 | rule), the
-  // rule-major slot of each, the offset of its rule words, file starts
-  const uint64_t* fe_keys = nullptr;
-  const uint32_t* fe_slot = nullptr;
-  const int64_t* fe_pos = nullptr;
-  const int64_t* fe_xoff = nullptr;
+  std::vector<int64_t> lvl_piece;
   // the rule words (file-major) cut into chunks of at most 4096 words inside
   // each file: chunk c = words [xch_start[c], + xch_len[c]), overlapped by the
   // pairs [xch_p0[c], xch_p1[c]); file f's chunks are [xch_foff[f], xch_foff[f+1])
   int64_t rule_chunks = 0;  // host copy of *xch_count
-  // the rules' own words, rule after rule: rule r's are rule_words[rule_woff[r]], W_r of them
-  const uint32_t* rule_woff = nullptr;
-  const int32_t* rule_words = nullptr;
-  // per pair (file-major): its rule's rule_words offset, and its first word
-  // as uint32 ([pairs + 1], the last entry the total)
-  const uint32_t* fe_wbeg = nullptr;
-  const uint32_t* fe_pos32 = nullptr;
   // the rule words of each file sorted by 16k-word bucket per rule-word chunk:
   // entry = (pair - chunk's first pair) << 14 | index in bucket, runs per (chunk, bucket)
   const uint32_t* xent = nullptr;
