@@ -661,9 +661,11 @@ def sequence_paths(B, ctx, g, stream, reps=3):
     gh = B.gt_load_grammar(ctx, g, stream)
     out = {}
     with torch.cuda.stream(stream):
-        for name, path, items in (("bucketed", 2, 8), ("radix_sort_tile4096", 1, 16), ("radix_sort", 1, 8)):
+        for name, path, items, pf in (("bucketed", 2, 8, 0), ("radix_sort_tile4096", 1, 16, 0),
+                                      ("radix_sort_prefetch", 1, 8, 1), ("radix_sort", 1, 8, 0)):
             B.gt_set_param(ctx, "seq_path", path)
             B.gt_set_param(ctx, "radix_items", items)
+            B.gt_set_param(ctx, "radix_prefetch", pf)
             B.gt_free_result(B.gt_sequence_count(gh, 0, stream))
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             keep = []

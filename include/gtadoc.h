@@ -358,6 +358,10 @@ gt_status gt_check_bounded_wait(gt_ctx* ctx, int publish, int64_t polls, int64_t
  *                   8 (default, tiles of 2048 keys) or 16 (tiles of 4096:
  *                   longer runs per digit in each tile's writes); GT_EINVAL
  *                   otherwise.  Same results.
+ *   "radix_prefetch" 1: the radix sort's scatter passes (2048-key tiles) run
+ *                   as a persistent kernel that copies the next tile into
+ *                   shared memory asynchronously while it ranks the current
+ *                   one; 0 (default): one CTA per tile.  Same results.
  *   "file_strategy" per-file analytics (term vector, inverted index, per-file
  *                   sequence count, ranked index): 0 (default) picks top-down
  *                   for at most 64 files and bottom-up otherwise (the paper's

@@ -813,7 +813,7 @@ GT_API gt_status gt_check_bounded_wait(gt_ctx* ctx, int publish, int64_t polls, 
 GT_API gt_status gt_set_param(gt_ctx* ctx, const char* name, int64_t value) {
   if (!ctx || !name) return GT_EINVAL;
   static const char* known[] = {"wc_aggregate", "use_graphs", "file_strategy", "wc_slices", "bu_local", "seq_path",
-                                "seq_table_cap", "radix_items"};
+                                "seq_table_cap", "radix_items", "radix_prefetch"};
   if (std::strcmp(name, "radix_items") == 0 && value != 8 && value != 16) {
     ctx->last_error = "radix_items must be 8 or 16";
     return GT_EINVAL;

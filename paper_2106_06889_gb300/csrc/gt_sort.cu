@@ -244,9 +244,134 @@ __global__ void __launch_bounds__(kRsThreads, ITEMS == 8 ? 4 : 2) radix_downswee
   }
 }
 
+// The same scatter as a persistent kernel (one CTA per tile slot of the
+// SMs) that copies the next full tile's keys and values into shared memory
+// with asynchronous 16-byte copies while it ranks and scatters the current
+// one; the tile it has just ranked is staged in place.  Same results (the
+// ranking order and the offsets are the same).  Needs 16-byte-aligned key and
+// value arrays; the caller checks.
+template <int VB>
+__global__ void __launch_bounds__(kRsThreads, 3) radix_scatter_pf_kernel(
+    const uint64_t* __restrict__ kin, uint64_t* __restrict__ kout, const void* __restrict__ vin,
+    void* __restrict__ vout, int64_t n, int shift, uint32_t mask, const int64_t* __restrict__ offs, int64_t ntiles) {
+  constexpr int kRsItems = 8, kRsTile = kRsThreads * 8;
+  constexpr int kBuf = kRsTile * (8 + VB);  // bytes of one tile (keys, then values)
+  __shared__ uint32_t wcnt[kRsWarps][256];
+  __shared__ uint32_t dstart[256];
+  __shared__ uint32_t wsum[kRsWarps];
+  __shared__ int64_t goff[256];
+  extern __shared__ __align__(16) unsigned char rs_smem[];  // two tile buffers
+  using VT = typename std::conditional<VB == 8, uint64_t, uint32_t>::type;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  const int64_t nfull = n / kRsTile;  // tiles copied asynchronously; the last partial one is read directly
+  auto prefetch = [&](int64_t t, unsigned char* buf) {
+    if (t >= nfull) return;
+    const unsigned char* gk = reinterpret_cast<const unsigned char*>(kin + t * kRsTile);
+    const unsigned char* gv = static_cast<const unsigned char*>(vin) + t * kRsTile * VB;
+    for (int c = threadIdx.x; c < kBuf / 16; c += kRsThreads) {
+      const unsigned char* src = c < kRsTile * 8 / 16 ? gk + 16 * c : gv + 16 * (c - kRsTile * 8 / 16);
+      const unsigned dst = unsigned(__cvta_generic_to_shared(buf + 16 * c));
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+    }
+  };
+  int b = 0;
+  prefetch(blockIdx.x, rs_smem);
+  asm volatile("cp.async.commit_group;" ::: "memory");
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, b ^= 1) {
+    unsigned char* cur = rs_smem + b * kBuf;
+    prefetch(t + gridDim.x, rs_smem + (b ^ 1) * kBuf);  // into the buffer the previous tile staged in
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    asm volatile("cp.async.wait_group 1;" ::: "memory");  // this tile's copies are done
+    for (int i = threadIdx.x; i < kRsWarps * 256; i += kRsThreads) wcnt[i / 256][i % 256] = 0;
+    goff[threadIdx.x] = offs[t * 256 + threadIdx.x];
+    __syncthreads();
+    const int64_t tbase = t * kRsTile;
+    const bool staged = t < nfull;
+    const uint64_t* sk_in = reinterpret_cast<const uint64_t*>(cur);
+    const VT* sv_in = reinterpret_cast<const VT*>(cur + kRsTile * 8);
+    uint64_t key[kRsItems];
+    uint32_t rank[kRsItems];
+    VT val[kRsItems];
+#pragma unroll
+    for (int it = 0; it < kRsItems; ++it) {
+      const int j = warp * 32 * kRsItems + it * 32 + lane;  // the same item order as the one-tile kernel
+      const bool valid = tbase + j < n;
+      key[it] = staged ? sk_in[j] : (valid ? kin[tbase + j] : 0);
+      val[it] = 0;
+      if (VB != 0 && valid) val[it] = staged ? sv_in[j] : static_cast<const VT*>(vin)[tbase + j];
+      const uint32_t d = uint32_t(key[it] >> shift) & mask;
+      const unsigned peers = warp_digit_peers(d, __ballot_sync(0xffffffffu, valid));
+      const uint32_t before = wcnt[warp][d];
+      const uint32_t r = __popc(peers & lt_mask);
+      rank[it] = before + r;
+      __syncwarp();
+      if (valid && r == 0) wcnt[warp][d] = before + __popc(peers);
+      __syncwarp();
+    }
+    __syncthreads();  // also: the tile's buffer is read, it becomes the staging area
+    const int dd = threadIdx.x;
+    uint32_t run = 0;
+#pragma unroll
+    for (int w = 0; w < kRsWarps; ++w) {
+      const uint32_t c = wcnt[w][dd];
+      wcnt[w][dd] = run;
+      run += c;
+    }
+    uint32_t incl = run;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += u;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    uint32_t wpre = 0;
+#pragma unroll
+    for (int w = 0; w < kRsWarps; ++w) wpre += w < warp ? wsum[w] : 0u;
+    dstart[dd] = wpre + incl - run;
+    __syncthreads();
+    uint64_t* skey = reinterpret_cast<uint64_t*>(cur);
+    VT* sval = reinterpret_cast<VT*>(cur + kRsTile * 8);
+#pragma unroll
+    for (int it = 0; it < kRsItems; ++it) {
+      const int j = warp * 32 * kRsItems + it * 32 + lane;
+      if (tbase + j < n) {
+        const uint32_t d = uint32_t(key[it] >> shift) & mask;
+        const uint32_t lp = dstart[d] + wcnt[warp][d] + rank[it];
+        skey[lp] = key[it];
+        if (VB != 0) sval[lp] = val[it];
+      }
+    }
+    __syncthreads();
+    const int tn = int(n - tbase < kRsTile ? n - tbase : kRsTile);
+    for (int i = threadIdx.x; i < tn; i += kRsThreads) {
+      const uint64_t k = skey[i];
+      const uint32_t d = uint32_t(k >> shift) & mask;
+      const int64_t pos = goff[d] + (i - int64_t(dstart[d]));
+      kout[pos] = k;
+      if (VB != 0) static_cast<VT*>(vout)[pos] = sval[i];
+    }
+    __syncthreads();  // the staging buffer is read before the next prefetch lands in it
+  }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
 template <int VB, int ITEMS>
 void launch_downsweep(const uint64_t* ka, uint64_t* kb, const void* va, void* vb, int64_t n, int shift, uint32_t mask,
                       int64_t ntiles, const int64_t* offs, cudaStream_t s) {
+  const bool aligned = (reinterpret_cast<uintptr_t>(ka) & 15) == 0 && (reinterpret_cast<uintptr_t>(va) & 15) == 0;
+  if (ITEMS == 8 && aligned && t_call_ctx && t_call_ctx->param("radix_prefetch", 0) != 0) {
+    constexpr size_t smem2 = size_t(2) * kRsTile * (8 + VB);
+    GT_CUDA(cudaFuncSetAttribute(radix_scatter_pf_kernel<VB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 int(smem2)));
+    const int64_t grid = std::min<int64_t>(ntiles, int64_t(t_call_ctx->num_sms) * 3);
+    Phase ph(t_call_ctx, "radix_pass", s);
+    radix_scatter_pf_kernel<VB><<<unsigned(grid), kRsThreads, smem2, s>>>(ka, kb, va, vb, n, shift, mask, offs,
+                                                                          ntiles);
+    GT_LAUNCH_CHECK();
+    return;
+  }
   constexpr size_t smem = size_t(kRsThreads) * ITEMS * (8 + VB);
   GT_CUDA(cudaFuncSetAttribute(radix_downsweep_kernel<VB, ITEMS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                int(smem)));

@@ -107,7 +107,8 @@ def test_same_as_sort_path(ctx):
                          ids=["nested2m", "multi500k", "one_key", "steep_root"])
 def test_radix_tile_sizes(name, g):
     """The radix-sort path with tiles of 2048 and of 4096 keys per scatter
-    pass ("radix_items" 8 and 16): the 3-word counts and the word sort equal
+    pass ("radix_items" 8 and 16), and with the persistent prefetching
+    scatter ("radix_prefetch" 1): the 3-word counts and the word sort equal
     the oracle's; an unsupported size is refused."""
     c = B.gt_create(0)
     try:
@@ -117,10 +118,11 @@ def test_radix_tile_sizes(name, g):
         gh = B.gt_load_grammar(c, g)
         want = oracle.sequence_count(g, 0)
         ww, wc = oracle.sort_words(g, 1)
-        for items in (8, 16):
+        for items, prefetch in ((8, 0), (16, 0), (8, 1)):
             B.gt_set_param(c, "radix_items", items)
+            B.gt_set_param(c, "radix_prefetch", prefetch)
             k, n = run(gh)
-            assert np.array_equal(k, want[0]) and np.array_equal(n, want[1]), items
+            assert np.array_equal(k, want[0]) and np.array_equal(n, want[1]), (items, prefetch)
             r = B.gt_sort(gh, 1)
             assert np.array_equal(B.result_numpy(r, "word"), ww) and np.array_equal(B.result_numpy(r, "count"), wc)
             B.gt_free_result(r)
