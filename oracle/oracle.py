@@ -18,8 +18,8 @@ No traversal, no blocking, no reuse of partial results: it is slow on purpose
 and meant to be checked against the paper by eye.  Integer results are exact
 (int64/uint64).  The readings taken where the paper is silent are:
 
-* word count is global over all files (the root "holds the final word counts"
-  in the word-count example of Section II-A);
+* word count is global over all files (in the word-count example of Section
+  II-A the counts of the whole input end up at the root);
 * a 3-word sequence never spans two files (the splitters between files are
   unique symbols and belong to no window);
 * 3-word keys pack as ``w1 << 42 | w2 << 21 | w3``;

@@ -1,23 +1,28 @@
 // Per-file analytics: term vector and inverted index (Section VI), with the
-// top-down traversal of Section IV-A carrying file information from the root
-// to every rule ("a small buffer ... in each rule indicating its file
-// information", the strategy the paper picks when there are few files).
+// top-down traversal of Section IV-A, which carries per-rule file information
+// from the root down (the strategy the paper picks when there are few files).
 //
-// GB300 form, for up to 64 files:
+// GB300 form, for up to 64 files.  At load (structure only):
 //   1. file masks, top-down: mask[r] = files whose expansion contains rule r,
 //      a 64-bit set per rule, ORed over parents level by level;
-//   2. memory pool: popcount(mask) slots per rule, placed by an exclusive scan;
-//   3. per-file weights, top-down: slot (r, f) = occurrences of r in file f,
-//      from the root's per-file references plus mult * parent weight;
-//   4. rule words per file: every (file, rule) pair emits the rule's own words
-//      with that weight, grouped by file (radix sort by file, then a scan);
-//   5. one CTA per (file, 2^14-word bucket) builds a dense shared-memory
-//      histogram from the file's root segment and emitted rule words - the
-//      CTAs of one file run together, so the file's data is read from HBM once
-//      and from L2 by the others - and writes the bucket's nonzero counts in
-//      word order plus a bit per word for the inverted index;
-//   6. the (file, bucket) pieces are concatenated into the term vector and
-//      the bits are turned into ascending file lists for the inverted index.
+//   2. memory pool: popcount(mask) slots per rule, level by level, each slot's
+//      (file, rule) pair in file-major order, the root's references by pair,
+//      and each slot's row of (parent's pair, mult);
+//   3. every file's rule words, bucket-sorted per chunk, each entry naming its
+//      pair.
+// Per query:
+//   4. per-file weights, level by level: weight (r, f) = occurrences of r in
+//      file f = the root's references plus the row's mult * parent weight;
+//   5. the root's chunks sorted by 2^14-word bucket; one CTA per (file,
+//      bucket) builds a dense shared-memory histogram from the file's root
+//      runs and weighted rule-word runs - the CTAs of one file run together,
+//      so the file's data is read from HBM once and from L2 by the others -
+//      and writes the bucket's nonzero counts in word order plus a bit per
+//      word for the inverted index;
+//   6. the (file, bucket) pieces are copied into the term vector (adding the
+//      word count on the way when it is asked for) and the bits become
+//      ascending file lists for the inverted index (one pass, bounded
+//      look-back for the offsets).
 #include <algorithm>
 
 #include <vector>
