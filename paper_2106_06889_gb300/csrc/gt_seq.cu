@@ -67,12 +67,18 @@ __global__ void __launch_bounds__(kWinThreads) win_emit_kernel(DevGrammar d, con
                                                                unsigned* __restrict__ status) {
   TileWin t;
   const int c = tile_windows(d, head, tail, kb, int64_t(blockIdx.x) * kTile + threadIdx.x * 4, t);
+  // the tile's first row and the owners' weights are requested before the
+  // scan's barriers, so they arrive while the CTA ranks its windows
+  const int64_t first = tile_off[blockIdx.x];
+  uint32_t wv[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) wv[i] = t.n[i] ? uint32_t(wt[t.r[i]]) : 0u;
   int total;
-  int64_t pos = tile_off[blockIdx.x] + cta_excl_scan(c, &total);
+  int64_t pos = first + cta_excl_scan(c, &total);
   bool over = false;
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    const uint32_t w = t.n[i] ? uint32_t(wt[t.r[i]]) : 0u;
+    const uint32_t w = wv[i];
 #pragma unroll
     for (int q = 0; q < 2; ++q)
       if (q < t.n[i]) {
@@ -288,13 +294,13 @@ __global__ void __launch_bounds__(kRedThreads) red_write_kernel(const uint64_t* 
   __shared__ uint32_t sf[kRedTile];  // files fit 32 bits
   const int64_t base = int64_t(blockIdx.x) * kRedTile;
   const int len = int(min(n - base, int64_t(kRedTile)));
+  int64_t o0 = toff[blockIdx.x];  // requested with the tile, before the barrier
   for (int r = threadIdx.x; r < len; r += kRedThreads) {
     sk[r] = keys[base + r];
     sv[r] = vals[base + r];
     if (fkeys) sf[r] = uint32_t(fkeys[base + r]);
   }
   __syncthreads();
-  int64_t o0 = toff[blockIdx.x];
   for (int k = 0; k < kRedItems; ++k) {  // one 256-row step at a time, in row order
     const int r = k * kRedThreads + threadIdx.x;
     const int64_t i = base + r;

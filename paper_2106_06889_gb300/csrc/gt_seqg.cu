@@ -232,10 +232,15 @@ __global__ void __launch_bounds__(kSgThreads) sg_emit_kernel(const __grid_consta
     TileWin t;
     uint32_t total;
     const uint32_t mine = tile_windows(a.d, a.head, a.tail, a.kb, tl * kTile + threadIdx.x * 4, t);
-    int64_t pos = a.tile_off[tl] + block_scan_u32<kSgThreads>(mine, &total);
+    // first row and weights requested before the scan's barriers
+    const int64_t first = a.tile_off[tl];
+    uint64_t wv[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) wv[i] = t.n[i] ? a.wt[t.r[i]] : 0;
+    int64_t pos = first + block_scan_u32<kSgThreads>(mine, &total);
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      const uint64_t w64 = t.n[i] ? a.wt[t.r[i]] : 0;
+      const uint64_t w64 = wv[i];
 #pragma unroll
       for (int q = 0; q < 2; ++q)
         if (q < t.n[i]) {

@@ -103,15 +103,15 @@ __global__ void __launch_bounds__(kRsThreads) radix_upsweep_kernel(const uint64_
   constexpr int kRsItems = ITEMS, kRsTile = kRsThreads * ITEMS;
   __shared__ uint32_t h[kRsWarps][256];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int i = threadIdx.x; i < kRsWarps * 256; i += kRsThreads) h[i / 256][i % 256] = 0;
-  __syncthreads();
   const int64_t wbase = int64_t(blockIdx.x) * kRsTile + int64_t(warp) * 32 * kRsItems;
-  uint64_t key[kRsItems];  // every load issued before the first update
+  uint64_t key[kRsItems];  // every load issued before the counters are cleared
 #pragma unroll
   for (int it = 0; it < kRsItems; ++it) {
     const int64_t idx = wbase + it * 32 + lane;
     key[it] = idx < n ? keys[idx] : 0;
   }
+  for (int i = threadIdx.x; i < kRsWarps * 256; i += kRsThreads) h[i / 256][i % 256] = 0;
+  __syncthreads();
   // counting only: one shared atomic per key into the warp's own counters
   // (measured faster than ballot multisplit, also when all keys share a digit)
 #pragma unroll
@@ -174,9 +174,6 @@ __global__ void __launch_bounds__(kRsThreads, ITEMS == 8 ? 4 : 2) radix_downswee
   uint64_t* skey = reinterpret_cast<uint64_t*>(rs_smem);
   unsigned char* sval = rs_smem + kRsTile * 8;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int i = threadIdx.x; i < kRsWarps * 256; i += kRsThreads) wcnt[i / 256][i % 256] = 0;
-  goff[threadIdx.x] = offs[int64_t(blockIdx.x) * 256 + threadIdx.x];
-  __syncthreads();
   const unsigned lt_mask = (1u << lane) - 1u;
   const int64_t tbase = int64_t(blockIdx.x) * kRsTile;
   const int64_t wbase = tbase + int64_t(warp) * 32 * kRsItems;
@@ -184,6 +181,8 @@ __global__ void __launch_bounds__(kRsThreads, ITEMS == 8 ? 4 : 2) radix_downswee
   uint64_t key[kRsItems];
   uint32_t rank[kRsItems];
   VT val[kRsItems];
+  // the tile's keys and values and this digit's output offset are all
+  // requested before the first barrier, so one memory round trip starts a tile
 #pragma unroll
   for (int it = 0; it < kRsItems; ++it) {
     const int64_t idx = wbase + it * 32 + lane;
@@ -191,6 +190,14 @@ __global__ void __launch_bounds__(kRsThreads, ITEMS == 8 ? 4 : 2) radix_downswee
     key[it] = valid ? kin[idx] : 0;
     val[it] = 0;
     if (VB != 0 && valid) val[it] = static_cast<const VT*>(vin)[idx];
+  }
+  goff[threadIdx.x] = offs[int64_t(blockIdx.x) * 256 + threadIdx.x];
+  for (int i = threadIdx.x; i < kRsWarps * 256; i += kRsThreads) wcnt[i / 256][i % 256] = 0;
+  __syncthreads();
+#pragma unroll
+  for (int it = 0; it < kRsItems; ++it) {
+    const int64_t idx = wbase + it * 32 + lane;
+    const bool valid = idx < n;
     const uint32_t d = uint32_t(key[it] >> shift) & mask;
     const unsigned peers = warp_digit_peers(d, __ballot_sync(0xffffffffu, valid));
     const uint32_t before = wcnt[warp][d];
