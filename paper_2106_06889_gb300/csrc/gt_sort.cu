@@ -242,12 +242,16 @@ __global__ void __launch_bounds__(kRsThreads, ITEMS == 8 ? 4 : 2) radix_downswee
   }
   __syncthreads();
   const int tn = int(n - tbase < kRsTile ? n - tbase : kRsTile);
-  for (int i = threadIdx.x; i < tn; i += kRsThreads) {
-    const uint64_t k = skey[i];
-    const uint32_t d = uint32_t(k >> shift) & mask;
-    const int64_t pos = goff[d] + (i - int64_t(dstart[d]));
-    kout[pos] = k;
-    if (VB != 0) static_cast<VT*>(vout)[pos] = reinterpret_cast<const VT*>(sval)[i];
+#pragma unroll
+  for (int it = 0; it < kRsItems; ++it) {
+    const int i = it * kRsThreads + threadIdx.x;
+    if (i < tn) {
+      const uint64_t k = skey[i];
+      const uint32_t d = uint32_t(k >> shift) & mask;
+      const int64_t pos = goff[d] + (i - int64_t(dstart[d]));
+      kout[pos] = k;
+      if (VB != 0) static_cast<VT*>(vout)[pos] = reinterpret_cast<const VT*>(sval)[i];
+    }
   }
 }
 
